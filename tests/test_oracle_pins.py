@@ -1,0 +1,339 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Each test would fail for a plausible slip in the oracle: a wrong Jacobi
+parameter or index (basis vs the printed formula, printed 2D relations,
+orthogonality/norms), a transposed or mis-signed operand in the curl or the
+fluxes (skew-adjointness, exact curl of polynomial fields), a wrong mass scaling
+(flat-element closed form), a dropped facet term (consistency, energy).
+"""
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import sympy as sp
+
+from oracle.basis import phi3, psi2, index3, index2, legendre
+from oracle.quadrature import tet_rule, tri_rule
+from oracle.dg import OracleDG
+from oracle.project import project, l2_error
+from workloads.mesh import kuhn_cube_mesh
+from workloads.fields import te110_fields
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- basis
+def _sympy_phi3(i, j, k):
+    X, Y, Z = sp.symbols("x y z")
+    phi = ((1 - X - Y) ** i * (1 - X) ** j * sp.legendre(i, 2 * Z / (1 - X - Y) - 1)
+           * sp.jacobi(j, 2 * i + 1, 0, 2 * Y / (1 - X) - 1)
+           * sp.jacobi(k, 2 * i + 2 * j + 2, 0, 2 * X - 1))
+    return (X, Y, Z), phi
+
+
+def test_phi3_matches_printed_formula_sympy():
+    """Sec. 4.2.2 definition, evaluated exactly by sympy at rational points."""
+    p = 3
+    rng = np.random.default_rng(11)
+    pts = []
+    for _ in range(4):
+        a, b, c = rng.integers(1, 20, size=3)
+        s = a + b + c + rng.integers(1, 10)
+        pts.append((Fraction(int(a), int(s)), Fraction(int(b), int(s)), Fraction(int(c), int(s))))
+    P = np.array([[float(v) for v in q] for q in pts])
+    val, grad = phi3(p, P)
+    for r, (i, j, k) in enumerate(index3(p)):
+        (X, Y, Z), phi = _sympy_phi3(i, j, k)
+        dphi = [sp.diff(phi, v) for v in (X, Y, Z)]
+        for q, pt in enumerate(pts):
+            sub = {X: sp.Rational(pt[0].numerator, pt[0].denominator),
+                   Y: sp.Rational(pt[1].numerator, pt[1].denominator),
+                   Z: sp.Rational(pt[2].numerator, pt[2].denominator)}
+            assert val[r, q] == pytest.approx(float(phi.subs(sub)), abs=1e-13)
+            for d in range(3):
+                assert grad[r, q, d] == pytest.approx(float(dphi[d].subs(sub)), abs=1e-12)
+
+
+def test_psi2_matches_eq4_sympy():
+    X, Y = sp.symbols("x y")
+    pts = [(sp.Rational(1, 7), sp.Rational(2, 5)), (sp.Rational(3, 8), sp.Rational(1, 9))]
+    P = np.array([[float(a), float(b)] for a, b in pts])
+    val, grad = psi2(3, P, grad=True)
+    for r, (i, j) in enumerate(index2(3)):
+        psi = sp.legendre(i, 2 * Y / (1 - X) - 1) * (1 - X) ** i * sp.jacobi(j, 2 * i + 1, 0, 2 * X - 1)
+        for q, (a, b) in enumerate(pts):
+            assert val[r, q] == pytest.approx(float(psi.subs({X: a, Y: b})), abs=1e-13)
+            assert grad[r, q, 0] == pytest.approx(float(sp.diff(psi, X).subs({X: a, Y: b})), abs=1e-12)
+            assert grad[r, q, 1] == pytest.approx(float(sp.diff(psi, Y).subs({X: a, Y: b})), abs=1e-12)
+
+
+def test_quadrature_exact_on_monomials():
+    """int_T x^a y^b z^c = a! b! c! / (a+b+c+3)!  (exact for total degree <= 2q-1)."""
+    q = 4
+    x, w = tet_rule(q)
+    for a in range(8):
+        for b in range(8 - a):
+            for c in range(8 - a - b):
+                exact = math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
+                got = np.sum(w * x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c)
+                assert got == pytest.approx(exact, rel=1e-13, abs=1e-16)
+    s, ws = tri_rule(q)
+    for a in range(8):
+        for b in range(8 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert np.sum(ws * s[:, 0] ** a * s[:, 1] ** b) == pytest.approx(exact, rel=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_orthogonality_and_closed_form_norms(p):
+    """L2-orthogonality (Sec. 3.1, Sec. 4.2.2) with
+    ||phi_ijk||^2 = 1/(2(2i+1)(i+j+1)(2i+2j+2k+3)), ||psi_ij||^2 = 1/(2(2i+1)(i+j+1))."""
+    x, w = tet_rule(p + 2)
+    v, _ = phi3(p, x)
+    M = (v * w) @ v.T
+    d = np.array([1.0 / (2 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3))
+                  for i, j, k in index3(p)])
+    assert np.abs(M - np.diag(d)).max() < 1e-15 * max(1, p)
+    assert d[0] == pytest.approx(1.0 / 6.0)
+    s, ws = tri_rule(p + 2)
+    pv = psi2(p, s)
+    M2 = (pv * ws) @ pv.T
+    d2 = np.array([1.0 / (2 * (2 * i + 1) * (i + j + 1)) for i, j in index2(p)])
+    assert np.abs(M2 - np.diag(d2)).max() < 1e-15 * max(1, p)
+
+
+def _read_relations(name):
+    rel = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = [t.strip() for t in line.split("|")]
+            rel.setdefault(parts[0], []).append(parts[1:])
+    return rel
+
+
+def test_printed_2d_relations_hold():
+    """The two printed 2D FindRelation outputs of Sec. 4.2.1 annihilate phi_ij of Eq. (4)."""
+    rel = _read_relations("relations_2d.txt")
+    pmax = 12
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(0.05, 0.45, size=(7, 2))
+    val, grad = psi2(pmax, pts, grad=True)
+    pos = {ij: r for r, ij in enumerate(index2(pmax))}
+    I, J = sp.symbols("i j")
+    for name, dcomp in (("dx", 0), ("dy", 1)):
+        terms = [(sp.sympify(c, locals={"i": I, "j": J}), int(si), int(sj), int(d))
+                 for c, si, sj, d in rel[name]]
+        for i in range(4):
+            for j in range(4):
+                total = np.zeros(len(pts))
+                scale = 0.0
+                for coef, si, sj, d in terms:
+                    c = float(coef.subs({I: i, J: j}))
+                    r = pos[(i + si, j + sj)]
+                    f = grad[r, :, dcomp] if d else val[r]
+                    total += c * f
+                    scale = max(scale, np.abs(c * f).max())
+                assert np.abs(total).max() <= 1e-12 * scale, (name, i, j)
+
+
+def test_printed_relations_are_not_vacuous():
+    """Changing one printed coefficient breaks the dx relation (guards the test above)."""
+    rel = _read_relations("relations_2d.txt")
+    pts = np.array([[0.2, 0.3], [0.1, 0.15]])
+    val, grad = psi2(8, pts, grad=True)
+    pos = {ij: r for r, ij in enumerate(index2(8))}
+    I, J = sp.symbols("i j")
+    terms = [(sp.sympify(c, locals={"i": I, "j": J}), int(si), int(sj), int(d)) for c, si, sj, d in rel["dx"]]
+    i, j = 1, 1
+    total = 0.0
+    for n, (coef, si, sj, d) in enumerate(terms):
+        c = float(coef.subs({I: i, J: j})) * (1.01 if n == 0 else 1.0)
+        r = pos[(i + si, j + sj)]
+        total = total + c * (grad[r, :, 0] if d else val[r])
+    assert np.abs(total).max() > 1e-6
+
+
+def test_legendre_worked_example():
+    """Eq. (5) and the ansatz solution of Sec. 4.1, plus the backward sweep of Sec. 3.2.2
+    reproducing exact differentiation of a random Legendre series."""
+    rel = _read_relations("legendre_relation.txt")["term"]
+    x = np.linspace(-0.95, 0.95, 9)
+    N = 12
+    P = legendre(N + 2, x)
+    h = 1e-6
+    dP = (legendre(N + 2, x + h) - legendre(N + 2, x - h)) / (2 * h)
+    nsym = sp.Symbol("n")
+    for n in range(N):
+        s = sum(float(sp.sympify(c, locals={"n": nsym}).subs(nsym, n)) * (dP if int(d) else P)[n + int(sh)]
+                for c, sh, d in rel)
+        assert np.abs(s).max() < 1e-7
+    # backward sweep: v' = sum w_i P_i
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(N + 1)
+    vt = v.copy()
+    wv = np.zeros(N)
+    for n in range(N, 0, -1):
+        wv[n - 1] = (2 * n - 1) * vt[n]
+        if n - 2 >= 0:
+            vt[n - 2] += vt[n]
+    lhs = v @ dP[: N + 1]
+    rhs = wv @ P[:N]
+    assert np.abs(lhs - rhs).max() < 1e-6 * np.abs(lhs).max()
+
+
+# -------------------------------------------------------------- operator
+def _mesh(kind):
+    if kind == "jitter":
+        return kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    if kind == "periodic":
+        return kuhn_cube_mesh(3, periodic=True, shuffle_local=True, seed=2)
+    return kuhn_cube_mesh(2)
+
+
+@pytest.mark.parametrize("kind", ["plain", "jitter", "periodic"])
+@pytest.mark.parametrize("flux", ["central", "stabilized"])
+def test_skew_adjointness(kind, flux):
+    """Eq. (2): the evolution matrix is antisymmetric, r_E = -C^T H (and -S^T K)."""
+    m = _mesh(kind)
+    eps = np.random.default_rng(1).uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, 2, eps, 1.0, vertex_key=m.vertex_key, flux=flux)
+    A = dg.assemble()
+    CH, CE = A["CH"].toarray(), A["CE"].toarray()
+    assert np.abs(CE + CH.T).max() <= 1e-14 * np.abs(CH).max()
+    if flux == "stabilized":
+        S, CEK = A["S"].toarray(), A["CEK"].toarray()
+        assert np.abs(CEK + S.T).max() <= 1e-14 * np.abs(S).max()
+
+
+def test_mesh_topology_counts():
+    m = kuhn_cube_mesh(3)
+    dg = OracleDG(m.xyz, m.tets, 1, 1.0, 1.0)
+    assert (dg.geo.nbr < 0).sum() == 12 * 9           # 6 sides x n^2 squares x 2 triangles
+    mp = kuhn_cube_mesh(3, periodic=True)
+    dgp = OracleDG(mp.xyz, mp.tets, 1, 1.0, 1.0, vertex_key=mp.vertex_key)
+    assert (dgp.geo.nbr < 0).sum() == 0
+    assert dgp.nfaces == 2 * dgp.nt
+    # neighbour relation is an involution
+    g = dgp.geo
+    t = np.arange(g.nt)
+    for f in range(4):
+        assert np.all(g.nbr[g.nbr[t, f], g.nbr_face[t, f]] == t)
+
+
+def _poly_fields():
+    def E(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        o = np.zeros(x.shape)
+        o[..., 0] = Y * (1 - Y) * Z * (1 - Z)
+        o[..., 2] = X * (1 - X) * Y * (1 - Y)
+        return o
+
+    def curlE(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        o = np.zeros(x.shape)
+        o[..., 0] = X * (1 - X) * (1 - 2 * Y)
+        o[..., 1] = Y * (1 - Y) * (1 - 2 * Z) - (1 - 2 * X) * Y * (1 - Y)
+        o[..., 2] = -(1 - 2 * Y) * Z * (1 - Z)
+        return o
+
+    def H(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack([Y ** 2 * Z, X * Z ** 2, X ** 3], -1)
+
+    def curlH(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack([-2 * X * Z, Y ** 2 - 3 * X ** 2, Z ** 2 - 2 * Y * Z], -1)
+    return E, curlE, H, curlH
+
+
+def test_exact_curl_of_polynomial_fields():
+    """Sec. 3.2.2: the modal curl is exact for polynomials of the space; a continuous
+    field with vanishing tangential trace on the PEC boundary has no jumps, so one
+    H-kick gives exactly -curl E and one E-kick exactly curl H (consistency).
+    A flipped facet sign or a dropped facet term fails this."""
+    p = 4
+    m = kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    dg = OracleDG(m.xyz, m.tets, p, 1.0, 1.0)
+    E, curlE, H, curlH = _poly_fields()
+    A = dg.assemble()
+    Ec = project(dg, E, p)
+    dH = dg._blockmul(A["MHinv"], A["CH"] @ Ec)
+    c = project(dg, curlE, p - 1)
+    assert np.abs(dH + c).max() < 1e-12 * np.abs(c).max()
+    Hc = project(dg, H, p - 1)
+    dE = dg._blockmul(A["MEinv"], A["CE"] @ Hc)
+    ce = project(dg, curlH, p)
+    assert np.abs(dE - ce).max() < 1e-11 * np.abs(ce).max()
+
+
+def test_flat_mass_closed_form():
+    """Sec. 3.3.1: flat elements, constant eps: M = |det F| eps (F^{-1} F^{-T}) (x) diag(||phi||^2)."""
+    p = 3
+    m = kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    eps = np.random.default_rng(2).uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+    ts = np.arange(dg.nt)
+    M = dg.mass_blocks(ts, "E")
+    d = np.array([1.0 / (2 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3)) for i, j, k in index3(p)])
+    for t in ts:
+        G = abs(dg.geo.detF[t]) * eps[t] * dg.geo.Finv[t] @ dg.geo.Finv[t].T
+        ref = np.kron(G, np.diag(d))
+        assert np.abs(M[t] - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_geometry_free_reference_integrals():
+    """Sec. 3.2.1: (H, curl e)_T and the facet integrals equal the reference-element
+    ones up to sign, so the physical blocks of every element are sign(det F) times
+    those of the reference tetrahedron."""
+    p = 3
+    m = kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    dg = OracleDG(m.xyz, m.tets, p, 1.0, 1.0)
+    ref_xyz = np.array([[0., 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    dgr = OracleDG(ref_xyz, np.array([[0, 1, 2, 3]]), p, 1.0, 1.0)
+    VHr, VEr = dgr.volume_blocks(np.array([0]))
+    ts = np.arange(dg.nt)
+    VH, VE = dg.volume_blocks(ts)
+    s = np.sign(dg.geo.detF)
+    assert np.abs(VH - s[:, None, None] * VHr).max() < 1e-12 * np.abs(VHr).max()
+    for f in range(4):
+        fr = dgr.face_blocks(np.array([0]), f)["AH_own"]      # PEC on the lone tet: c = 1
+        fb = dg.face_blocks(ts, f)
+        own = fb["AH_own"] * np.where(fb["nbr"] >= 0, 2.0, 1.0)[:, None, None]
+        assert np.abs(own - s[:, None, None] * fr).max() < 1e-12 * np.abs(fr).max()
+
+
+@pytest.mark.parametrize("flux", ["central", "stabilized"])
+def test_energy_conserved(flux):
+    """Sec. 2.1 / Sec. 3: antisymmetric evolution + symplectic Euler conserve the
+    modified discrete energy to round-off."""
+    m = kuhn_cube_mesh(2, jitter=0.1, seed=7)
+    eps = np.random.default_rng(4).uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, 3, eps, 1.0, flux=flux)
+    rng = np.random.default_rng(0)
+    E0 = rng.standard_normal(dg.sizeE)
+    H0 = rng.standard_normal(dg.sizeH)
+    _, _, _, W = dg.run(E0, H0, 0.2 * 0.5 / 9, 40)
+    assert np.abs(W - W[0]).max() < 1e-13 * W[0]
+
+
+def test_te110_cavity_convergence():
+    """Analytic PEC cavity mode: errors shrink under h-refinement at p=3."""
+    errs = []
+    for n in (2, 4):
+        m = kuhn_cube_mesh(n)
+        dg = OracleDG(m.xyz, m.tets, 3, 1.0, 1.0)
+        E0 = project(dg, lambda x: te110_fields(x, 0.0)[0], 3)
+        H0 = project(dg, lambda x: te110_fields(x, 0.0)[1], 2)
+        dt = 0.2 / n / 9
+        N = int(round(0.25 / dt))
+        E, H, _, _ = dg.run(E0, H0, dt, N)
+        e, r = l2_error(dg, E, lambda x: te110_fields(x, N * dt)[0], 3)
+        errs.append(e / r)
+    assert errs[1] < 0.05
+    assert errs[0] / errs[1] > 4.0
