@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Throughput of the DG Maxwell time step on GB300, as one JSON line.
+
+A bench "step" is one leapfrog time step (H-phase + E-phase over the whole
+mesh) of the named workload.  The metric is DoF-steps/s = elements * D_e *
+steps / time with D_e = 3 N3(p) + 3 N3(p-1) volume coefficients per element.
+
+Default workload: planewave_n32_p6 (periodic unit box, n = 32, 196,608 tets,
+p = 6, plane wave k = 2 pi (1,2,3)), FP32 path; the FP64 path is timed on the
+same workload and reported beside it.  The field state (330 MB in FP32) is
+larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+For N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(the method has no cross-problem exchange); value = all ranks' DoF-steps / the
+max over ranks of the timed region.  --impl reference times the FP64 CPU
+oracle on bounded element samples of the same workload (rank 0 only).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF-steps/s at p=4/6 (mixed vs FP64 plain, same GB300); % HBM roofline; err"
+UNIT = "DoF-steps/s"
+
+
+def n3(q):
+    return (q + 1) * (q + 2) * (q + 3) // 6 if q >= 0 else 0
+
+
+def dof_per_elem(p):
+    return 3 * n3(p) + 3 * n3(p - 1)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="planewave_n32_p6")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=4, help="steps of the FP64 comparison run (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def analytic(workload):
+    from workloads.fields import plane_wave_fields, te110_fields, gaussian_pulse_fields
+    if workload.init == "plane":
+        return lambda x, t: plane_wave_fields(x, t)
+    if workload.init == "te110":
+        return lambda x, t: te110_fields(x, t)
+    c = workload.centre
+    return lambda x, t: gaussian_pulse_fields(x, c) if t == 0 else (None, None)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/dgm_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        smax = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (sha256 recorded beside the numbers)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1104_4208_gb300", "csrc", "kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == sha:
+                return float(parts[3])
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- GPU arm
+def make_solver(w, precision):
+    from paper_1104_4208_gb300.solver import Solver
+    m = w.mesh
+    return Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=precision)
+
+
+def project_initial(S, w, torch, q1d):
+    from paper_1104_4208_gb300 import _capi as capi
+    xh, _ = capi.dgm_quad_rule(q1d)
+    maps = capi.dgm_element_maps(S.mesh, S.nt)
+    F = maps[:, 3:].reshape(-1, 3, 3)
+    fn = analytic(w)
+    Ed = torch.empty((S.nt, xh.shape[0], 3), dtype=torch.float64, device="cuda")
+    Hd = torch.empty_like(Ed)
+    chunk = 16384
+    for s in range(0, S.nt, chunk):
+        e = min(S.nt, s + chunk)
+        x = maps[s:e, None, :3] + np.einsum("tij,qj->tqi", F[s:e], xh)
+        Ex, Hx = fn(x, 0.0)
+        Ed[s:e].copy_(torch.from_numpy(Ex))
+        Hd[s:e].copy_(torch.from_numpy(Hx))
+    capi.dgm_project_device(S.prob, q1d, Ed.data_ptr(), Hd.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    del Ed, Hd
+    torch.cuda.empty_cache()
+    return maps, xh
+
+
+def l2_rel_error(S, w, torch, q1d, maps, xh, T):
+    from paper_1104_4208_gb300 import _capi as capi
+    if w.init not in ("plane", "te110"):
+        return None
+    _, wq = capi.dgm_quad_rule(q1d)
+    Ed = torch.empty((S.nt, xh.shape[0], 3), dtype=torch.float64, device="cuda")
+    capi.dgm_eval_device(S.prob, q1d, Ed.data_ptr(), None, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    Eh_all = Ed.cpu().numpy()
+    del Ed
+    torch.cuda.empty_cache()
+    F = maps[:, 3:].reshape(-1, 3, 3)
+    det = np.abs(np.linalg.det(F))
+    fn = analytic(w)
+    err2 = ref2 = 0.0
+    chunk = 16384
+    for s in range(0, S.nt, chunk):
+        e = min(S.nt, s + chunk)
+        x = maps[s:e, None, :3] + np.einsum("tij,qj->tqi", F[s:e], xh)
+        Ex, _ = fn(x, T)
+        Eh = Eh_all[s:e]
+        wt = det[s:e, None] * wq[None, :]
+        err2 += np.einsum("tq,tqc->", wt, (Eh - Ex) ** 2)
+        ref2 += np.einsum("tq,tqc->", wt, Ex ** 2)
+    return float(np.sqrt(err2 / ref2))
+
+
+def timed_run(S, torch, dt, steps, warmup):
+    from paper_1104_4208_gb300 import _capi as capi
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    if warmup > 0:
+        capi.dgm_run(S.prob, dt, warmup, sp)
+    torch.cuda.synchronize()
+    dist_barrier()
+    torch.cuda.synchronize()
+    W = np.empty(steps + 1)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = capi.dgm_run_timed(S.prob, dt, steps, sp, W)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), stats, W
+
+
+_DIST = {"on": False}
+
+
+def dist_barrier():
+    if _DIST["on"]:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x):
+    if not _DIST["on"]:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _DIST["nccl"] else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(w, seconds, cores_env=True):
+    """DoF-steps/s of the FP64 CPU oracle on a bounded element sample (H- and E-kick)."""
+    code = r"""
+import sys, time, json, os
+import numpy as np
+sys.path.insert(0, %r)
+from workloads.configs import make_workload
+from oracle.dg import OracleDG
+w = make_workload(%r)
+m = w.mesh
+dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key)
+rng = np.random.default_rng(0)
+E = rng.standard_normal(m.nt * 3 * dg.NE); H = rng.standard_normal(m.nt * 3 * dg.NH)
+budget = %r
+t0 = time.perf_counter(); dg.local_kick_H(E, [0], w.dt); dg.local_kick_E(H, [0], w.dt); t1 = time.perf_counter()
+per = max(t1 - t0, 1e-3)
+k = int(max(1, min(4096, budget / per)))
+s = rng.choice(m.nt, k, replace=False)
+t0 = time.perf_counter()
+for c in range(0, k, 16):
+    dg.local_kick_H(E, s[c:c+16], w.dt); dg.local_kick_E(H, s[c:c+16], w.dt)
+t1 = time.perf_counter()
+D = 3 * dg.NE + 3 * dg.NH
+print(json.dumps({"rate": k * D / (t1 - t0), "elements": int(k), "seconds": t1 - t0}))
+""" % (ROOT, w.name, seconds)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from workloads.configs import make_workload
+    from paper_1104_4208_gb300 import _capi as capi
+
+    w = make_workload(args.workload)
+    D = dof_per_elem(w.p)
+    dofs = w.nt * D
+    q1d = w.p + 1
+    S = make_solver(w, args.precision)
+    maps, xh = project_initial(S, w, torch, q1d)
+    err0 = l2_rel_error(S, w, torch, q1d, maps, xh, 0.0)
+    dt = w.dt
+
+    with ClockSampler(local) as clk:
+        ms, stats, W = timed_run(S, torch, dt, args.steps, args.warmup)
+    clocks = clk.summary()
+    T = (args.warmup + args.steps) * dt
+    err = l2_rel_error(S, w, torch, q1d, maps, xh, T)
+    drift = float(np.abs(W - W[0]).max() / W[0])
+    ms_max = dist_max(ms)
+    value = world * dofs * args.steps / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
+    b = 4 if args.precision == "fp32" else 8
+    NE, NH = n3(w.p), n3(w.p - 1)
+    bytes_H = w.nt * (3 * NE * b + 2 * 3 * NH * b + 16 * 8 + 16)
+    bytes_E = w.nt * (3 * NH * b + 2 * 3 * NE * b + 8 * 8 + 16)
+    tH = stats.h_phase_ms / max(stats.h_launches, 1)
+    tE = stats.e_phase_ms / max(stats.e_launches, 1)
+    if stats.h_phase_ms >= stats.e_phase_ms:
+        kname, kbytes, kms = "k_phase_H", bytes_H, tH
+    else:
+        kname, kbytes, kms = "k_phase_E", bytes_E, tE
+    peak, peak_src = measured_peak_hbm()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "traffic": profile_traffic(f"{kname}<{'float' if b == 4 else 'double'}>"),
+            "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
+            "share": {"k_phase_H": stats.h_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms),
+                      "k_phase_E": stats.e_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms)}}
+
+    # FP64 plain path on the same workload, same initial data
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        S.close()
+        S64 = make_solver(w, "fp64")
+        project_initial(S64, w, torch, q1d)
+        ms64, st64, W64 = timed_run(S64, torch, dt, args.fp64_steps, 1)
+        v64 = world * dofs * args.fp64_steps / (dist_max(ms64) * 1e-3)
+        fp64 = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "speedup_of_mixed": value / v64,
+                "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0])}
+        S64.close()
+        S = make_solver(w, args.precision)
+        project_initial(S, w, torch, q1d)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    nE, nH = S.nE, S.nH
+    if args.no_e2e:
+        nE = 0
+    if nE:
+        hE = torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy()
+        hH = torch.empty(nH, dtype=torch.float64, pin_memory=True).numpy()
+        capi.dgm_get_fields(S.prob, hE, hH)
+        torch.cuda.synchronize()
+        dist_barrier()
+        t0 = time.perf_counter()
+        capi.dgm_set_fields(S.prob, hE, hH)
+        capi.dgm_run(S.prob, dt, args.steps, None, None)
+        capi.dgm_get_fields(S.prob, hE, hH)
+        torch.cuda.synchronize()
+        t_e2e = dist_max(time.perf_counter() - t0)
+        dist_barrier()
+        e2e = {"value": world * dofs * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": (nE + nH) * 8 / args.steps, "d2h_bytes_per_step": (nE + nH) * 8 / args.steps,
+               "note": "one upload, K steps, one download per timed call"}
+    S.close()
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            r = cpu_oracle_rate(w, args.cpu_seconds)
+            if r:
+                cpu = {"value": r["rate"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "sample": f"H- and E-kick of {r['elements']} random elements of {w.name} "
+                                 f"({r['seconds']:.1f} s, 1 thread)"}
+        launches = int(stats.h_launches + stats.e_launches + stats.other_launches)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+               "config": {"workload": w.name, "tets": w.nt, "p": w.p, "dof": dofs, "precision": args.precision,
+                          "flux": "central", "dt": dt, "parallelism": f"replicas{world}",
+                          "l2": "state larger than L2 (no flush needed)",
+                          "state_mb": dofs * (4 if args.precision == 'fp32' else 8) / 1e6},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks,
+               "err": {"l2_rel_E_vs_analytic": err, "l2_rel_E_initial_projection": err0,
+                       "energy_drift": drift},
+               "fp64_plain": fp64}
+    return out
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    from workloads.configs import make_workload
+    w = make_workload(args.workload)
+    per_step = max(1.0, 100.0 / max(1, args.steps + args.warmup))
+    total_el = 0
+    t_total = 0.0
+    D = dof_per_elem(w.p)
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(w, per_step)
+        if r is None:
+            return {"impl": "reference", "unavailable": "CPU oracle failed to run"}
+        if i >= args.warmup:
+            total_el += r["elements"]
+            t_total += r["seconds"]
+    value = total_el * D / t_total
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "tets": w.nt, "p": w.p, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": f"{total_el} random elements of {w.name} over {args.steps} steps, "
+                                       "H- and E-kick, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        nccl = args.impl == "gb300" and torch.cuda.is_available()
+        if nccl:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if nccl else "gloo")
+        _DIST.update(on=True, nccl=nccl)
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_gpu(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if _DIST["on"]:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

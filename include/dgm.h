@@ -1,0 +1,203 @@
+/*
+ * dgm.h -- C ABI of the GB300 library for the energy-conserving discontinuous
+ * Galerkin (DG) discretisation of the time-domain Maxwell equations
+ * (Koutschan, Lehrenfeld, Schoeberl, "Computer Algebra meets Finite Elements:
+ * an Efficient Implementation for Maxwell's Equations", arXiv:1104.4208).
+ *
+ * Problem statement (Sec. 2, Sec. 3): a tetrahedral mesh, piecewise constant
+ * permittivity eps and permeability mu per element, a polynomial order p and
+ * initial fields go in; the fields after N explicit time steps and the
+ * discrete energy come out.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - p is the polynomial degree of E; H has degree p-1 (Sec. 2: E in V^{k+1},
+ *    H in V^k).  1 <= p <= DGM_PMAX.
+ *  - Element map: the four vertices of each tetrahedron are re-ordered by
+ *    ascending vertex key (vertex_key[v] if given, else the vertex id v);
+ *    Phi(xh) = X0 + F xh, F = [X1-X0, X2-X0, X3-X0] (Sec. 3.2.1).
+ *  - Fields are covariant (Sec. 3.2.1):  E|_T(x) = F^{-T} sum_a c_{m,a} e_m
+ *    phi_a(Phi^{-1} x), phi_a the Dubiner basis of Sec. 4.2.2 exactly as
+ *    printed (unnormalised), multi-indices a = (i,j,k), i+j+k <= p, ordered
+ *    lexicographically with i outermost and k innermost.
+ *  - Canonical field layout (host and device arrays, FP64):
+ *      E [nt][3][N3(p)],  H [nt][3][N3(p-1)],  N3(q) = (q+1)(q+2)(q+3)/6.
+ *  - Face unknowns H^F (stabilized flux only): H^F = sum_g psi_g (K_1g t^1 +
+ *    K_2g t^2) with psi the 2D Dubiner basis of Eq. (4) in the face
+ *    parametrisation x = X_a + s t_1 + u t_2, t_1 = X_b - X_a, t_2 = X_c - X_a
+ *    (a, b, c = the face's vertices by ascending key, coordinates taken from the
+ *    first element that lists the face), t^i the dual basis of (t_1, t_2).
+ *    Layout K [nfaces][2][N2(p)], N2(p) = (p+1)(p+2)/2; faces numbered by first
+ *    occurrence when scanning elements in order and local faces 0..3 (local face
+ *    f is opposite the f-th vertex in key order).
+ *  - Faces without a partner are perfect electric conductor (PEC) walls.
+ *
+ * Errors: every function returns DGM_OK (0) or a negative DGM_ERR_* code and
+ * leaves a message retrievable with dgm_last_error() (thread local).  No
+ * exception crosses this boundary.
+ *
+ * Ownership: handles own their device memory.  Functions taking host arrays
+ * copy them; functions named *_device take raw device pointers (e.g. from
+ * torch tensors), never free them and are ordered on the given CUDA stream.
+ * Handles are not thread safe.
+ */
+#ifndef DGM_H
+#define DGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGM_PMAX 8
+
+enum dgm_status {
+    DGM_OK = 0,
+    DGM_ERR_INVALID_ARG = -1,
+    DGM_ERR_OOM = -2,
+    DGM_ERR_CUDA = -3,
+    DGM_ERR_UNSTABLE = -4,
+    DGM_ERR_TIMEOUT = -5,
+    DGM_ERR_UNSUPPORTED = -6
+};
+
+/* Numerical flux (Sec. 2.1): the central flux, or the stabilized central flux
+ * with the additional face unknown H^F. */
+enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
+
+/* Arithmetic of the per-step operator.  FP64: state and arithmetic in double.
+ * FP32: state and operator arithmetic in float; geometry, tables (rounded once)
+ * and the energy reduction in double. */
+enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1 };
+
+typedef struct dgm_options {
+    int flux;           /* dgm_flux */
+    double alpha0;      /* alpha = alpha0 * p^2 (Sec. 2.1, "alpha scales with p^2") */
+    int precision;      /* dgm_precision */
+    int variant;        /* 0 = automatic kernel choice */
+    int checks;         /* nonzero: validate inputs (CFL bound, NaN scan) */
+} dgm_options;
+
+typedef struct dgm_ctx dgm_ctx;
+typedef struct dgm_mesh dgm_mesh;
+typedef struct dgm_problem dgm_problem;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int dgm_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dgm_last_error(void);
+
+/* Fill *opt with defaults: central flux, alpha0 = 1, FP64, automatic variant. */
+void dgm_default_options(dgm_options* opt);
+
+/* Context bound to CUDA device `device`.  DGM_ERR_CUDA if the device is absent. */
+int dgm_create(dgm_ctx** ctx, int device);
+int dgm_destroy(dgm_ctx* ctx);
+
+/* Mesh (Sec. 2: triangulation T_h of tetrahedra, facets F_h).
+ * xyz [nv][3] vertex coordinates; tets [nt][4] vertex ids; vertex_key [nv]
+ * (nullable) identifies periodic copies of a vertex -- two faces whose three
+ * keys coincide are glued (the periodic translation is implied by the
+ * coordinates).  Faces without a partner are PEC walls.
+ * The mesh is host data: ctx may be NULL (no GPU is touched).
+ * Errors: DGM_ERR_INVALID_ARG for ids out of range, repeated keys in one tet,
+ * degenerate tets (|det F| <= 1e-12 (max edge component)^3), faces shared by
+ * more than two tets, a tet glued to itself. */
+int dgm_mesh_create(dgm_ctx* ctx, int64_t nv, const double* xyz, int64_t nt,
+                    const int32_t* tets, const int32_t* vertex_key, dgm_mesh** out);
+int dgm_mesh_destroy(dgm_mesh* mesh);
+/* Counts: elements, faces, boundary (PEC) faces.  Any pointer may be NULL. */
+int dgm_mesh_info(const dgm_mesh* mesh, int64_t* nt, int64_t* nfaces, int64_t* nboundary);
+
+/* Problem: mesh + p + eps[nt] + mu[nt] (> 0) + options (nullable: defaults).
+ * Builds the reference tables for p (Sec. 3.2.2, Sec. 3.2.3), the per-element
+ * inverse mass blocks (Sec. 3.3.1) and uploads everything to the device.
+ * Fields start at zero. */
+int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* eps,
+                       const double* mu, const dgm_options* opt, dgm_problem** out);
+int dgm_problem_destroy(dgm_problem* prob);
+/* Lengths (in doubles) of the canonical E, H and H^F arrays. */
+int dgm_problem_sizes(const dgm_problem* prob, int64_t* nE, int64_t* nH, int64_t* nHF);
+
+/* Copy fields in/out (canonical layout, FP64 host arrays).  HF may be NULL
+ * (ignored / zero) and must be NULL for the central flux. */
+int dgm_set_fields(dgm_problem* prob, const double* E, const double* H, const double* HF);
+int dgm_get_fields(dgm_problem* prob, double* E, double* H, double* HF);
+/* Same with device pointers (FP64, canonical layout), ordered on `stream`. */
+int dgm_set_fields_device(dgm_problem* prob, const double* E, const double* H,
+                          const double* HF, void* stream);
+int dgm_get_fields_device(dgm_problem* prob, double* E, double* H, double* HF, void* stream);
+
+/* One half of the symplectic Euler step of Sec. 3, applied in place:
+ *   which = 0 (H-kick):  H += dt M_mu^{-1} C_h E   (and H^F += dt M_F^{-1} S E)
+ *   which = 1 (E-kick):  E -= dt M_eps^{-1} C_h^T H (including the H^F term)
+ * C_h is the DG curl with the chosen flux (Sec. 2.1).  Ordered on `stream`
+ * (NULL = the legacy default stream). */
+int dgm_kick(dgm_problem* prob, int which, double dt, void* stream);
+
+/* nsteps leapfrog steps (symplectic Euler with H staggered by dt/2, Sec. 3),
+ * started and finished with half kicks so that E, H are reported at the same
+ * time t + nsteps*dt.  energy_out (nullable, host, nsteps+1 doubles) receives
+ * the modified discrete energy
+ *   W^n = 1/2 (eps E^n, E^n) + 1/2 (mu H^{n-1/2}, H^{n+1/2})
+ *         [+ 1/2 sum_F (h_F/alpha) (H^{F,n-1/2}, H^{F,n+1/2})_F]
+ * which the scheme conserves exactly up to round-off (Sec. 2.1, Eq. (2)).
+ * Blocks until the energies are on the host when energy_out != NULL. */
+int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* energy_out);
+
+/* Per-kernel timing of one dgm_run_timed call: CUDA events recorded on the
+ * launching stream around every phase kernel (summed, milliseconds) and the
+ * number of kernels the call launched. */
+typedef struct dgm_run_stats {
+    double h_phase_ms;       /* H-phase kernels (incl. their fused energy partials) */
+    double e_phase_ms;       /* E-phase kernels */
+    double other_ms;         /* energy reductions */
+    int64_t h_launches, e_launches, other_launches;
+} dgm_run_stats;
+
+/* dgm_run with per-kernel CUDA-event timing written to *stats (nullable). */
+int dgm_run_timed(dgm_problem* prob, double dt, int64_t nsteps, void* stream,
+                  double* energy_out, dgm_run_stats* stats);
+
+/* Discrete energy 1/2 (eps E,E) + 1/2 (mu H,H) [+ face term] of the current
+ * state (no staggering), FP64. */
+int dgm_energy(dgm_problem* prob, double* W);
+
+/* Initial data and evaluation (Sec. 2: initial conditions; covariant L2
+ * projection, which for flat elements reduces to c_a = F^T sum_q w_q phi_a(xh_q)
+ * u(x_q) / ||phi_a||^2 by Sec. 3.3.1).
+ *
+ * dgm_quad_rule: tensor Gauss-Legendre rule in the collapsed coordinates of the
+ * reference tetrahedron with q1d points per direction (nq = q1d^3, exact for
+ * polynomials of total degree <= 2 q1d - 3); xh [nq][3] reference points, w [nq]
+ * weights summing to 1/6.  Any output may be NULL.  Needs no GPU.
+ * dgm_element_maps: [nt][12] = X0 (3) and F row-major (9) of every element in
+ * key order (Sec. 3.2.1).  Physical points are x = X0 + F xh.  Needs no GPU.
+ * dgm_project_device: set E (and H) to the projections of point values
+ * E_pts [nt][nq][3] (H_pts likewise, nullable) given at x = X0 + F xh_q of the
+ * rule with q1d points.  Device pointers, FP64, ordered on `stream`.
+ * dgm_eval_device: the reverse -- physical field values of the current E, H at
+ * the same points (outputs nullable). */
+int dgm_quad_rule(int q1d, int* nq, double* xh, double* w);
+int dgm_element_maps(const dgm_mesh* mesh, double* out);
+int dgm_project_device(dgm_problem* prob, int q1d, const double* E_pts, const double* H_pts,
+                       void* stream);
+int dgm_eval_device(dgm_problem* prob, int q1d, double* E_pts, double* H_pts, void* stream);
+
+/* Reference tables of the library (host, FP64, orthonormalised basis
+ * phi_a / ||phi_a||), for inspection and tests:
+ *   which = 0,1,2: D_x, D_y, D_z  [N3(p-1)][N3(p)], entry (b,a) = (d phi_a, phi_b)
+ *   which = 3..6 : trace of face which-3  [N2(p)][N3(p)], entry (g,a) =
+ *                  int psi_g(s,u) phi_a(face point) ds du, face basis orthonormal
+ *   which = 7    : squared norms ||phi_a||^2 [N3(p)]
+ * Needs no GPU.  `count` = capacity of `out` in doubles; the required size is
+ * returned in *needed. */
+int dgm_reference_table(int p, int which, double* out, int64_t count, int64_t* needed);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGM_H */

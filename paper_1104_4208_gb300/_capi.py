@@ -1,0 +1,230 @@
+"""ctypes binding of the C ABI in include/dgm.h (argument marshalling only).
+
+Every computation happens in libdgm.so; this module converts NumPy arrays and
+torch tensors to pointers and return codes to exceptions.  Importing it loads
+the in-tree library and fails loudly if it has not been built.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libdgm.so is not built; run `python -c \"import __graft_entry__ as g; g.build()\"` "
+        "or `python paper_1104_4208_gb300/build.py` first")
+
+_lib = C.CDLL(LIB_PATH)
+
+DGM_OK = 0
+DGM_ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE", -5: "TIMEOUT", -6: "UNSUPPORTED"}
+DGM_FLUX_CENTRAL, DGM_FLUX_STABILIZED = 0, 1
+DGM_PREC_FP64, DGM_PREC_FP32 = 0, 1
+DGM_PMAX = 8
+
+
+class DgmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{DGM_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dgm_options(C.Structure):
+    _fields_ = [("flux", C.c_int), ("alpha0", C.c_double), ("precision", C.c_int),
+                ("variant", C.c_int), ("checks", C.c_int)]
+
+
+class dgm_run_stats(C.Structure):
+    _fields_ = [("h_phase_ms", C.c_double), ("e_phase_ms", C.c_double), ("other_ms", C.c_double),
+                ("h_launches", C.c_int64), ("e_launches", C.c_int64), ("other_launches", C.c_int64)]
+
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_pd = C.POINTER(C.c_double)
+_pi32 = C.POINTER(C.c_int32)
+_pi64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "dgm_version": ([], C.c_int),
+    "dgm_last_error": ([], C.c_char_p),
+    "dgm_default_options": ([C.POINTER(dgm_options)], None),
+    "dgm_create": ([C.POINTER(_vp), C.c_int], C.c_int),
+    "dgm_destroy": ([_vp], C.c_int),
+    "dgm_mesh_create": ([_vp, _i64, _pd, _i64, _pi32, _pi32, C.POINTER(_vp)], C.c_int),
+    "dgm_mesh_destroy": ([_vp], C.c_int),
+    "dgm_mesh_info": ([_vp, _pi64, _pi64, _pi64], C.c_int),
+    "dgm_problem_create": ([_vp, _vp, C.c_int, _pd, _pd, C.POINTER(dgm_options), C.POINTER(_vp)], C.c_int),
+    "dgm_problem_destroy": ([_vp], C.c_int),
+    "dgm_problem_sizes": ([_vp, _pi64, _pi64, _pi64], C.c_int),
+    "dgm_set_fields": ([_vp, _pd, _pd, _pd], C.c_int),
+    "dgm_get_fields": ([_vp, _pd, _pd, _pd], C.c_int),
+    "dgm_set_fields_device": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
+    "dgm_get_fields_device": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
+    "dgm_kick": ([_vp, C.c_int, C.c_double, _vp], C.c_int),
+    "dgm_run": ([_vp, C.c_double, _i64, _vp, _pd], C.c_int),
+    "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
+    "dgm_energy": ([_vp, _pd], C.c_int),
+    "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
+    "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
+    "dgm_element_maps": ([_vp, _pd], C.c_int),
+    "dgm_project_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
+    "dgm_eval_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
+}
+
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != DGM_OK:
+        raise DgmError(rc, _lib.dgm_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_pd) if a is not None else None
+
+
+# ---- same names as the C ABI -------------------------------------------------
+def dgm_version():
+    return _lib.dgm_version()
+
+
+def dgm_last_error():
+    return _lib.dgm_last_error().decode()
+
+
+def dgm_default_options():
+    o = dgm_options()
+    _lib.dgm_default_options(C.byref(o))
+    return o
+
+
+def dgm_create(device=0):
+    h = _vp()
+    _check(_lib.dgm_create(C.byref(h), device))
+    return h
+
+
+def dgm_destroy(ctx):
+    _check(_lib.dgm_destroy(ctx))
+
+
+def dgm_mesh_create(ctx, xyz, tets, vertex_key=None):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    key = None if vertex_key is None else np.ascontiguousarray(vertex_key, dtype=np.int32)
+    h = _vp()
+    _check(_lib.dgm_mesh_create(ctx, xyz.shape[0], _dptr(xyz), tets.shape[0],
+                                tets.ctypes.data_as(_pi32),
+                                None if key is None else key.ctypes.data_as(_pi32), C.byref(h)))
+    return h
+
+
+def dgm_mesh_destroy(mesh):
+    _check(_lib.dgm_mesh_destroy(mesh))
+
+
+def dgm_mesh_info(mesh):
+    a, b, c = _i64(), _i64(), _i64()
+    _check(_lib.dgm_mesh_info(mesh, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dgm_problem_create(ctx, mesh, p, eps, mu, opt=None):
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    h = _vp()
+    _check(_lib.dgm_problem_create(ctx, mesh, int(p), _dptr(eps), _dptr(mu),
+                                   None if opt is None else C.byref(opt), C.byref(h)))
+    return h
+
+
+def dgm_problem_destroy(prob):
+    _check(_lib.dgm_problem_destroy(prob))
+
+
+def dgm_problem_sizes(prob):
+    a, b, c = _i64(), _i64(), _i64()
+    _check(_lib.dgm_problem_sizes(prob, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dgm_set_fields(prob, E=None, H=None, HF=None):
+    E = None if E is None else np.ascontiguousarray(E, dtype=np.float64)
+    H = None if H is None else np.ascontiguousarray(H, dtype=np.float64)
+    HF = None if HF is None else np.ascontiguousarray(HF, dtype=np.float64)
+    _check(_lib.dgm_set_fields(prob, _dptr(E), _dptr(H), _dptr(HF)))
+
+
+def dgm_get_fields(prob, E, H, HF=None):
+    _check(_lib.dgm_get_fields(prob, _dptr(E), _dptr(H), _dptr(HF)))
+
+
+def dgm_set_fields_device(prob, E_ptr, H_ptr, HF_ptr=None, stream=None):
+    _check(_lib.dgm_set_fields_device(prob, E_ptr, H_ptr, HF_ptr, stream))
+
+
+def dgm_get_fields_device(prob, E_ptr, H_ptr, HF_ptr=None, stream=None):
+    _check(_lib.dgm_get_fields_device(prob, E_ptr, H_ptr, HF_ptr, stream))
+
+
+def dgm_kick(prob, which, dt, stream=None):
+    _check(_lib.dgm_kick(prob, int(which), float(dt), stream))
+
+
+def dgm_run(prob, dt, nsteps, stream=None, energy_out=None):
+    _check(_lib.dgm_run(prob, float(dt), int(nsteps), stream, _dptr(energy_out)))
+
+
+def dgm_run_timed(prob, dt, nsteps, stream=None, energy_out=None):
+    st = dgm_run_stats()
+    _check(_lib.dgm_run_timed(prob, float(dt), int(nsteps), stream, _dptr(energy_out), C.byref(st)))
+    return st
+
+
+def dgm_energy(prob):
+    w = C.c_double()
+    _check(_lib.dgm_energy(prob, C.byref(w)))
+    return w.value
+
+
+def dgm_reference_table(p, which):
+    need = _i64()
+    _check(_lib.dgm_reference_table(int(p), int(which), None, 0, C.byref(need)))
+    out = np.empty(need.value)
+    _check(_lib.dgm_reference_table(int(p), int(which), _dptr(out), need.value, C.byref(need)))
+    return out
+
+
+def dgm_quad_rule(q1d):
+    nq = C.c_int()
+    _check(_lib.dgm_quad_rule(int(q1d), C.byref(nq), None, None))
+    xh = np.empty((nq.value, 3))
+    w = np.empty(nq.value)
+    _check(_lib.dgm_quad_rule(int(q1d), C.byref(nq), _dptr(xh), _dptr(w)))
+    return xh, w
+
+
+def dgm_element_maps(mesh, nt):
+    out = np.empty((nt, 12))
+    _check(_lib.dgm_element_maps(mesh, _dptr(out)))
+    return out
+
+
+def dgm_project_device(prob, q1d, E_ptr, H_ptr, stream=None):
+    _check(_lib.dgm_project_device(prob, int(q1d), E_ptr, H_ptr, stream))
+
+
+def dgm_eval_device(prob, q1d, E_ptr, H_ptr, stream=None):
+    _check(_lib.dgm_eval_device(prob, int(q1d), E_ptr, H_ptr, stream))

@@ -1,0 +1,64 @@
+// Internal declarations shared by the host C++ and the CUDA translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgm.h"
+
+namespace dgm {
+
+inline int n3(int q) { return q < 0 ? 0 : (q + 1) * (q + 2) * (q + 3) / 6; }
+inline int n2(int q) { return q < 0 ? 0 : (q + 1) * (q + 2) / 2; }
+
+void set_error(const std::string& msg);
+
+// ---------------------------------------------------------------- tables
+// Reference operators of the orthonormalised Dubiner basis phi_a / ||phi_a||
+// (Sec. 3.2.2 gradients, Sec. 3.2.3 traces), FP64.
+struct RefTables {
+    int p = 0, NE = 0, NH = 0, N2E = 0, N2H = 0;
+    std::vector<double> norm2E;          // [NE] ||phi_a||^2 (unnormalised basis)
+    std::vector<double> D[3];            // [NH][NE]  (d_d phi'_a, phi'_b)
+    std::vector<double> TrE[4];          // [N2E][NE] (phi'_a|_f, psi'_g) over degree-p face modes
+    std::vector<double> TrH[4];          // [N2H][NH] (phi'_b|_f, psi'_g) for the degree p-1 basis
+    // Face-frame tangents of local face f in reference coordinates:
+    // that[f][i][m], i = 0,1 (t_1 = v_b - v_a, t_2 = v_c - v_a).
+    double that[4][2][3];
+    // sign of nu_hat . (t_1 x t_2) for the outward reference normal of face f
+    double sigma_hat[4];
+    // position of each degree-(p-1) face index (i,j) inside the degree-p list
+    std::vector<int> pos2H;              // [N2H]
+};
+
+int build_ref_tables(int p, RefTables& t);
+// Squared norm of the unnormalised 3D Dubiner function (closed form).
+double dubiner3_norm2(int i, int j, int k);
+double dubiner2_norm2(int i, int j);
+void index3(int p, std::vector<int>& ijk);   // 3 ints per entry, lexicographic
+// Collapsed-coordinate Gauss-Legendre rule on the reference tetrahedron:
+// xh [nq][3] Cartesian points, w [nq] weights (sum 1/6), col [nq][3] collapsed coords.
+void collapsed_rule(int q1d, std::vector<double>& xh, std::vector<double>& w, std::vector<double>& col);
+// Orthonormalised phi'_a at the collapsed rule's points, [nq][N3(p)].
+void phi_table(int p, int q1d, std::vector<double>& phi);
+void index2(int p, std::vector<int>& ij);
+
+// ---------------------------------------------------------------- mesh
+struct MeshData {
+    int64_t nv = 0, nt = 0, nfaces = 0, nboundary = 0;
+    std::vector<double> xyz;             // [nv][3]
+    std::vector<int32_t> tets;           // [nt][4], vertices by ascending key
+    std::vector<int32_t> keys;           // [nt][4]
+    std::vector<int32_t> nbr;            // [nt][4] neighbour element or -1 (PEC)
+    std::vector<int8_t> nbr_face;        // [nt][4] neighbour's local face or -1
+    std::vector<int64_t> face_id;        // [nt][4] global face index
+    std::vector<int32_t> face_elem;      // [nfaces][2] (t*4+f) of the sides, second -1 on PEC
+    std::vector<double> F;               // [nt][9] row-major, columns = edges
+    std::vector<double> detF;            // [nt]
+};
+
+int build_mesh(int64_t nv, const double* xyz, int64_t nt, const int32_t* tets,
+               const int32_t* vertex_key, MeshData& m);
+
+}  // namespace dgm

@@ -1,0 +1,458 @@
+// CUDA kernels of the DG Maxwell time step (sm_103a).
+//
+// One time step of the symplectic Euler / leapfrog scheme (Sec. 3) is two
+// phase kernels:
+//   H-phase: H += dt M_mu^{-1} C_h E       (volume curl + facet jump + lift)
+//   E-phase: E -= dt M_eps^{-1} C_h^T H    (volume curl^T + facet average + lift)
+// Both work on the orthonormalised covariant coefficients of each element,
+// with the geometry-free reference operators of Sec. 3.2.1:
+//   r_H[m,b] = -s_T (curl E)[m,b]
+//              + sum_f sigma_f sum_g Tr_f[g,b] (t2_m a1_g - t1_m a2_g),  a = [[E]]/2
+//   r_E[m,a] =  s_T (curl^T H)[m,a]
+//              + sum_f sigma_f sum_g Tr_f[g,a] (t2_m b1_g - t1_m b2_g),  b = {{H}}
+// where a_i, b_i are tangential covariant face coefficients in the shared face
+// frame (both sides order the face's vertices by key), sigma_f = s_T * sign of
+// the reference face orientation, s_T = sign det F.  The inverse mass is the
+// 3x3 block (F^T F)/(|det F| eps) per coefficient (Sec. 3.3.1).
+//
+// Mapping: one warp per element, the element's coefficients staged in shared
+// memory, lanes over output coefficients, reference tables read through the
+// read-only cache.  The neighbour's trace on a shared face is recomputed from
+// the neighbour's coefficients (read from L2), so no per-step face buffer is
+// written.  Energy partials are accumulated in FP64 per warp in a fixed
+// order and reduced per block in a fixed order (bitwise reproducible).
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace dgm {
+
+__constant__ double c_that[4][2][3];
+__constant__ double c_sigma_hat[4];
+
+int upload_face_frames(const double that[4][2][3], const double sigma_hat[4]) {
+    if (cudaMemcpyToSymbol(c_that, that, sizeof(double) * 24) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(c_sigma_hat, sigma_hat, sizeof(double) * 4) != cudaSuccess) return -1;
+    return 0;
+}
+
+namespace {
+
+constexpr int kWarps = 4;   // warps per block
+
+template <typename real>
+__device__ __forceinline__ real ld(const real* p) {
+    return __ldg(p);
+}
+
+// fixed-order block reduction of one double per warp
+__device__ void block_energy_store(double v, double* out) {
+    __shared__ double red[kWarps];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kWarps; ++i) s += red[i];
+        out[blockIdx.x] = s;
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kWarps * 32)
+k_phase_H(KParams<real> P, double dt, double a_lo, double c_out, double* __restrict__ partials) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    real* sE = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
+    real* sN = sE + 3 * P.NE;
+    real* sA = sN + 3 * P.NE;
+    const int NE = P.NE, NH = P.NH, N2H = P.N2H;
+    double eacc = 0.0;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + wib; t < P.nt; t += nwarps) {
+        const real* Et = P.E + t * 3 * NE;
+        for (int k = lane; k < 3 * NE; k += 32) sE[k] = Et[k];
+        const double* g = P.geo + t * kGeoStride;
+        const double sT = g[kGeoSign];
+        __syncwarp();
+        for (int f = 0; f < 4; ++f) {
+            const int32_t nb = P.nbr[t * 4 + f];
+            const double sig = sT * c_sigma_hat[f];
+            if (nb >= 0) {
+                const real* En = P.E + (int64_t)(nb >> 2) * 3 * NE;
+                for (int k = lane; k < 3 * NE; k += 32) sN[k] = En[k];
+            }
+            __syncwarp();
+            for (int gm = lane; gm < N2H; gm += 32) {
+                const real* T = P.TrEqT + (size_t)f * NE * N2H + gm;
+                real t0 = 0, t1 = 0, t2 = 0;
+                for (int a = 0; a < NE; ++a) {
+                    const real w = ld(T + (size_t)a * N2H);
+                    t0 += w * sE[a];
+                    t1 += w * sE[NE + a];
+                    t2 += w * sE[2 * NE + a];
+                }
+                real J0 = (real)c_that[f][0][0] * t0 + (real)c_that[f][0][1] * t1 + (real)c_that[f][0][2] * t2;
+                real J1 = (real)c_that[f][1][0] * t0 + (real)c_that[f][1][1] * t1 + (real)c_that[f][1][2] * t2;
+                real a0, a1;
+                if (nb >= 0) {
+                    const int nf = nb & 3;
+                    const real* Tn = P.TrEqT + (size_t)nf * NE * N2H + gm;
+                    real n0 = 0, n1 = 0, n2 = 0;
+                    for (int a = 0; a < NE; ++a) {
+                        const real w = ld(Tn + (size_t)a * N2H);
+                        n0 += w * sN[a];
+                        n1 += w * sN[NE + a];
+                        n2 += w * sN[2 * NE + a];
+                    }
+                    const real K0 = (real)c_that[nf][0][0] * n0 + (real)c_that[nf][0][1] * n1 + (real)c_that[nf][0][2] * n2;
+                    const real K1 = (real)c_that[nf][1][0] * n0 + (real)c_that[nf][1][1] * n1 + (real)c_that[nf][1][2] * n2;
+                    a0 = (real)(0.5 * sig) * (J0 - K0);
+                    a1 = (real)(0.5 * sig) * (J1 - K1);
+                } else {
+                    a0 = (real)sig * J0;
+                    a1 = (real)sig * J1;
+                }
+                sA[(2 * f) * N2H + gm] = a0;
+                sA[(2 * f + 1) * N2H + gm] = a1;
+            }
+            __syncwarp();
+        }
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double gm6[6] = {g[6], g[7], g[8], g[9], g[10], g[11]};
+        const double inv_mu = g[kGeoInvMu], mu = g[kGeoMu];
+        real* Ht = P.H + t * 3 * NH;
+        for (int b = lane; b < NH; b += 32) {
+            real cx = 0, cy = 0, cz = 0;
+            const real* Dx = P.DT + b;
+            const real* Dy = Dx + (size_t)NE * NH;
+            const real* Dz = Dy + (size_t)NE * NH;
+            for (int a = 0; a < NE; ++a) {
+                const real dx = ld(Dx + (size_t)a * NH), dy = ld(Dy + (size_t)a * NH), dz = ld(Dz + (size_t)a * NH);
+                const real ex = sE[a], ey = sE[NE + a], ez = sE[2 * NE + a];
+                cx += dy * ez - dz * ey;
+                cy += dz * ex - dx * ez;
+                cz += dx * ey - dy * ex;
+            }
+            real r0 = -(real)sT * cx, r1 = -(real)sT * cy, r2 = -(real)sT * cz;
+            for (int f = 0; f < 4; ++f) {
+                const real* L = P.TrH + (size_t)f * N2H * NH + b;
+                const real* A0 = sA + (2 * f) * N2H;
+                const real* A1 = A0 + N2H;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < N2H; ++gm) {
+                    const real l = ld(L + (size_t)gm * NH);
+                    u0 += l * A0[gm];
+                    u1 += l * A1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real s = (real)(dt * inv_mu);
+            const real d0 = s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real d1 = s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real d2 = s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            const real h0 = Ht[b], h1 = Ht[NH + b], h2 = Ht[2 * NH + b];
+            if (partials) {
+                const double l0 = (double)h0 - a_lo * (double)d0, l1 = (double)h1 - a_lo * (double)d1,
+                             l2 = (double)h2 - a_lo * (double)d2;
+                const double u0 = l0 + (double)d0, u1 = l1 + (double)d1, u2 = l2 + (double)d2;
+                eacc += 0.5 * mu *
+                        (l0 * (gm6[0] * u0 + gm6[1] * u1 + gm6[2] * u2) + l1 * (gm6[1] * u0 + gm6[3] * u1 + gm6[4] * u2) +
+                         l2 * (gm6[2] * u0 + gm6[4] * u1 + gm6[5] * u2));
+            }
+            Ht[b] = h0 + (real)c_out * d0;
+            Ht[NH + b] = h1 + (real)c_out * d1;
+            Ht[2 * NH + b] = h2 + (real)c_out * d2;
+        }
+        if (partials) {
+            const double eps = g[kGeoEps];
+            for (int a = lane; a < NE; a += 32) {
+                const double e0 = sE[a], e1 = sE[NE + a], e2 = sE[2 * NE + a];
+                eacc += 0.5 * eps *
+                        (e0 * (gm6[0] * e0 + gm6[1] * e1 + gm6[2] * e2) + e1 * (gm6[1] * e0 + gm6[3] * e1 + gm6[4] * e2) +
+                         e2 * (gm6[2] * e0 + gm6[4] * e1 + gm6[5] * e2));
+            }
+        }
+        __syncwarp();
+    }
+    if (partials) block_energy_store(eacc, partials);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kWarps * 32)
+k_phase_E(KParams<real> P, double dt) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    real* sH = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
+    real* sN = sH + 3 * P.NH;
+    real* sB = sN + 3 * P.NH;
+    const int NE = P.NE, NH = P.NH, N2H = P.N2H;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + wib; t < P.nt; t += nwarps) {
+        const real* Ht = P.H + t * 3 * NH;
+        for (int k = lane; k < 3 * NH; k += 32) sH[k] = Ht[k];
+        const double* g = P.geo + t * kGeoStride;
+        const double sT = g[kGeoSign];
+        __syncwarp();
+        for (int f = 0; f < 4; ++f) {
+            const int32_t nb = P.nbr[t * 4 + f];
+            const double sig = sT * c_sigma_hat[f];
+            if (nb >= 0) {
+                const real* Hn = P.H + (int64_t)(nb >> 2) * 3 * NH;
+                for (int k = lane; k < 3 * NH; k += 32) sN[k] = Hn[k];
+            }
+            __syncwarp();
+            for (int gm = lane; gm < N2H; gm += 32) {
+                const real* T = P.TrHT + (size_t)f * NH * N2H + gm;
+                real t0 = 0, t1 = 0, t2 = 0;
+                for (int b = 0; b < NH; ++b) {
+                    const real w = ld(T + (size_t)b * N2H);
+                    t0 += w * sH[b];
+                    t1 += w * sH[NH + b];
+                    t2 += w * sH[2 * NH + b];
+                }
+                real J0 = (real)c_that[f][0][0] * t0 + (real)c_that[f][0][1] * t1 + (real)c_that[f][0][2] * t2;
+                real J1 = (real)c_that[f][1][0] * t0 + (real)c_that[f][1][1] * t1 + (real)c_that[f][1][2] * t2;
+                real b0, b1;
+                if (nb >= 0) {
+                    const int nf = nb & 3;
+                    const real* Tn = P.TrHT + (size_t)nf * NH * N2H + gm;
+                    real n0 = 0, n1 = 0, n2 = 0;
+                    for (int b = 0; b < NH; ++b) {
+                        const real w = ld(Tn + (size_t)b * N2H);
+                        n0 += w * sN[b];
+                        n1 += w * sN[NH + b];
+                        n2 += w * sN[2 * NH + b];
+                    }
+                    const real K0 = (real)c_that[nf][0][0] * n0 + (real)c_that[nf][0][1] * n1 + (real)c_that[nf][0][2] * n2;
+                    const real K1 = (real)c_that[nf][1][0] * n0 + (real)c_that[nf][1][1] * n1 + (real)c_that[nf][1][2] * n2;
+                    b0 = (real)(0.5 * sig) * (J0 + K0);
+                    b1 = (real)(0.5 * sig) * (J1 + K1);
+                } else {
+                    b0 = (real)sig * J0;
+                    b1 = (real)sig * J1;
+                }
+                sB[(2 * f) * N2H + gm] = b0;
+                sB[(2 * f + 1) * N2H + gm] = b1;
+            }
+            __syncwarp();
+        }
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double inv_eps = g[kGeoInvEps];
+        real* Et = P.E + t * 3 * NE;
+        for (int a = lane; a < NE; a += 32) {
+            real rx = 0, ry = 0, rz = 0;
+            const real* Dx = P.D + a;
+            const real* Dy = Dx + (size_t)NH * NE;
+            const real* Dz = Dy + (size_t)NH * NE;
+            for (int b = 0; b < NH; ++b) {
+                const real dx = ld(Dx + (size_t)b * NE), dy = ld(Dy + (size_t)b * NE), dz = ld(Dz + (size_t)b * NE);
+                const real hx = sH[b], hy = sH[NH + b], hz = sH[2 * NH + b];
+                rx += dz * hy - dy * hz;
+                ry += dx * hz - dz * hx;
+                rz += dy * hx - dx * hy;
+            }
+            real r0 = (real)sT * rx, r1 = (real)sT * ry, r2 = (real)sT * rz;
+            for (int f = 0; f < 4; ++f) {
+                const real* L = P.TrEq + (size_t)f * N2H * NE + a;
+                const real* B0 = sB + (2 * f) * N2H;
+                const real* B1 = B0 + N2H;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < N2H; ++gm) {
+                    const real l = ld(L + (size_t)gm * NE);
+                    u0 += l * B0[gm];
+                    u1 += l * B1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real s = (real)(dt * inv_eps);
+            Et[a] += s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            Et[NE + a] += s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            Et[2 * NE + a] += s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+        }
+        __syncwarp();
+    }
+}
+
+// canonical FP64 (unnormalised basis) <-> internal (orthonormalised, real)
+template <typename real>
+__global__ void k_import(const double* __restrict__ src, real* __restrict__ dst, const double* __restrict__ nrm,
+                         int64_t n, int ncoef) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (real)(src[i] * nrm[i % ncoef]);
+}
+
+template <typename real>
+__global__ void k_export(const real* __restrict__ src, double* __restrict__ dst, const double* __restrict__ nrm,
+                         int64_t n, int ncoef) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i] / nrm[i % ncoef];
+}
+
+__global__ void k_energy_reduce(const double* __restrict__ partials, int n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// covariant L2 projection of point values (setup): c'_{m,a} = (F^T sum_q w_q phi'_a(q) u_q)_m
+template <typename real>
+__global__ void k_project(int64_t nt, int N, int nq, const double* __restrict__ maps,
+                          const double* __restrict__ wphi, const double* __restrict__ pts, real* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nw) {
+        const double* F = maps + t * 12 + 3;
+        const double* u = pts + t * (int64_t)nq * 3;
+        for (int a = lane; a < N; a += 32) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int q = 0; q < nq; ++q) {
+                const double w = wphi[(size_t)q * N + a];
+                s0 += w * u[3 * q];
+                s1 += w * u[3 * q + 1];
+                s2 += w * u[3 * q + 2];
+            }
+            real* o = out + t * 3 * N;
+            o[a] = (real)(F[0] * s0 + F[3] * s1 + F[6] * s2);
+            o[N + a] = (real)(F[1] * s0 + F[4] * s1 + F[7] * s2);
+            o[2 * N + a] = (real)(F[2] * s0 + F[5] * s1 + F[8] * s2);
+        }
+    }
+}
+
+// physical values u(x_q) = F^{-T} sum_a c'_a phi'_a(q) of the current field (setup / diagnostics)
+template <typename real>
+__global__ void k_eval(int64_t nt, int N, int nq, const double* __restrict__ maps, const double* __restrict__ phi,
+                       const real* __restrict__ c, double* __restrict__ pts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nw) {
+        const double* F = maps + t * 12 + 3;
+        const double det = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                           F[2] * (F[3] * F[7] - F[4] * F[6]);
+        // rows of F^{-T} = columns of F^{-1}
+        double Fi[9];
+        Fi[0] = (F[4] * F[8] - F[5] * F[7]) / det;
+        Fi[1] = (F[2] * F[7] - F[1] * F[8]) / det;
+        Fi[2] = (F[1] * F[5] - F[2] * F[4]) / det;
+        Fi[3] = (F[5] * F[6] - F[3] * F[8]) / det;
+        Fi[4] = (F[0] * F[8] - F[2] * F[6]) / det;
+        Fi[5] = (F[2] * F[3] - F[0] * F[5]) / det;
+        Fi[6] = (F[3] * F[7] - F[4] * F[6]) / det;
+        Fi[7] = (F[1] * F[6] - F[0] * F[7]) / det;
+        Fi[8] = (F[0] * F[4] - F[1] * F[3]) / det;
+        const real* ct = c + t * 3 * N;
+        for (int q = lane; q < nq; q += 32) {
+            double v0 = 0, v1 = 0, v2 = 0;
+            for (int a = 0; a < N; ++a) {
+                const double f = phi[(size_t)q * N + a];
+                v0 += f * (double)ct[a];
+                v1 += f * (double)ct[N + a];
+                v2 += f * (double)ct[2 * N + a];
+            }
+            double* o = pts + (t * nq + q) * 3;
+            // (F^{-T} v)_i = sum_j Finv[j][i] v_j
+            o[0] = Fi[0] * v0 + Fi[3] * v1 + Fi[6] * v2;
+            o[1] = Fi[1] * v0 + Fi[4] * v1 + Fi[7] * v2;
+            o[2] = Fi[2] * v0 + Fi[5] * v1 + Fi[8] * v2;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename real>
+int launch_project(int64_t nt, int N, int nq, const double* maps, const double* wphi, const double* pts, real* out,
+                   cudaStream_t s) {
+    const int64_t blocks = (nt + 3) / 4;
+    k_project<real><<<(int)(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(nt, N, nq, maps, wphi, pts, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_eval(int64_t nt, int N, int nq, const double* maps, const double* phi, const real* c, double* pts,
+                cudaStream_t s) {
+    const int64_t blocks = (nt + 3) / 4;
+    k_eval<real><<<(int)(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(nt, N, nq, maps, phi, c, pts);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template int launch_project<double>(int64_t, int, int, const double*, const double*, const double*, double*, cudaStream_t);
+template int launch_project<float>(int64_t, int, int, const double*, const double*, const double*, float*, cudaStream_t);
+template int launch_eval<double>(int64_t, int, int, const double*, const double*, const double*, double*, cudaStream_t);
+template int launch_eval<float>(int64_t, int, int, const double*, const double*, const float*, double*, cudaStream_t);
+
+template <typename real>
+size_t phase_smem_bytes(const KParams<real>& P) {
+    return (size_t)kWarps * P.warp_smem * sizeof(real);
+}
+
+template <typename real>
+int launch_phase_H(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
+                   cudaStream_t s) {
+    const size_t smem = phase_smem_bytes(P);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_phase_H<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_phase_H<real><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_phase_E(const KParams<real>& P, int grid, double dt, cudaStream_t s) {
+    const size_t smem = phase_smem_bytes(P);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_phase_E<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_phase_E<real><<<grid, kWarps * 32, smem, s>>>(P, dt);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_import(const double* src, real* dst, const double* nrm, int64_t n, int ncoef, cudaStream_t s) {
+    if (n == 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_import<real><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, nrm, n, ncoef);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_export(const real* src, double* dst, const double* nrm, int64_t n, int ncoef, cudaStream_t s) {
+    if (n == 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_export<real><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, nrm, n, ncoef);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s) {
+    k_energy_reduce<<<1, 256, 0, s>>>(partials, n, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int phase_warps_per_block() { return kWarps; }
+
+template int launch_phase_H<double>(const KParams<double>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_H<float>(const KParams<float>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_E<double>(const KParams<double>&, int, double, cudaStream_t);
+template int launch_phase_E<float>(const KParams<float>&, int, double, cudaStream_t);
+template int launch_import<double>(const double*, double*, const double*, int64_t, int, cudaStream_t);
+template int launch_import<float>(const double*, float*, const double*, int64_t, int, cudaStream_t);
+template int launch_export<double>(const double*, double*, const double*, int64_t, int, cudaStream_t);
+template int launch_export<float>(const float*, double*, const double*, int64_t, int, cudaStream_t);
+
+}  // namespace dgm

@@ -1,0 +1,55 @@
+// Launch interface of the CUDA kernels (host side, no torch types).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dgm {
+
+// Per-element geometry record (FP64), kGeoStride doubles per element:
+//   [0..5]  G^{-1} = F^T F / |det F|         (xx, xy, xz, yy, yz, zz)
+//   [6..11] G      = |det F| F^{-1} F^{-T}   (same order)
+//   [12] eps  [13] 1/eps  [14] mu  [15] 1/mu  [16] sign(det F)
+constexpr int kGeoStride = 20;
+constexpr int kGeoEps = 12, kGeoInvEps = 13, kGeoMu = 14, kGeoInvMu = 15, kGeoSign = 16;
+
+template <typename real>
+struct KParams {
+    int64_t nt;
+    int NE, NH, N2E, N2H;
+    int warp_smem;              // reals of shared memory per warp
+    real* E;                    // [nt][3][NE] orthonormalised coefficients
+    real* H;                    // [nt][3][NH]
+    const double* geo;          // [nt][kGeoStride]
+    const int32_t* nbr;         // [nt][4] = 4*neighbour + neighbour's local face, or -1 (PEC)
+    const real* DT;             // [3][NE][NH]   D_d transposed
+    const real* D;              // [3][NH][NE]
+    const real* TrEqT;          // [4][NE][N2H]  E trace onto degree <= p-1 face modes, transposed
+    const real* TrEq;           // [4][N2H][NE]
+    const real* TrHT;           // [4][NH][N2H]  H trace, transposed
+    const real* TrH;            // [4][N2H][NH]
+};
+
+int upload_face_frames(const double that[4][2][3], const double sigma_hat[4]);
+
+template <typename real>
+int launch_phase_H(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
+                   cudaStream_t s);
+template <typename real>
+int launch_phase_E(const KParams<real>& P, int grid, double dt, cudaStream_t s);
+template <typename real>
+int launch_import(const double* src, real* dst, const double* nrm, int64_t n, int ncoef, cudaStream_t s);
+template <typename real>
+int launch_export(const real* src, double* dst, const double* nrm, int64_t n, int ncoef, cudaStream_t s);
+template <typename real>
+int launch_project(int64_t nt, int N, int nq, const double* maps, const double* wphi, const double* pts, real* out,
+                   cudaStream_t s);
+template <typename real>
+int launch_eval(int64_t nt, int N, int nq, const double* maps, const double* phi, const real* c, double* pts,
+                cudaStream_t s);
+int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s);
+int phase_warps_per_block();
+
+}  // namespace dgm

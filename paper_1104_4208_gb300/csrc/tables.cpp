@@ -1,0 +1,345 @@
+// Reference-element tables of the Dubiner basis (host, FP64).
+//
+// The 3D Dubiner function of Sec. 4.2.2 is a product of univariate factors in
+// the collapsed coordinates (xi, eta, zeta) of the reference tetrahedron,
+//   x = xi, y = (1-xi) eta, z = (1-xi)(1-eta) zeta,
+//   phi_ijk = (1-xi)^(i+j) (1-eta)^i L_i(2 zeta - 1) J_j^(2i+1,0)(2 eta - 1)
+//             J_k^(2i+2j+2,0)(2 xi - 1),
+// which is the tensor-product structure the method exploits (Sec. 3, item 1
+// and 4 of the list of ingredients).  Derivatives of the univariate Jacobi
+// factors use the identity d/dt P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1); the
+// Cartesian derivatives follow from the chain rule of the collapsed map.
+// Integrals use tensor Gauss-Legendre rules in the collapsed coordinates with
+// the Jacobian (1-xi)^2 (1-eta), exact for the polynomial integrands.
+//
+// Outputs are in the orthonormalised basis phi'_a = phi_a / ||phi_a|| (and
+// psi'_g on faces), so that the lift operators are exact transposes of the
+// trace operators and C_h, C_h^T share one rounded table.
+//
+// Host arithmetic is compiled with -ffp-contract=off so that the tables are
+// bit-identical on x86-64 and aarch64.
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dgm_internal.h"
+
+namespace dgm {
+
+void index3(int p, std::vector<int>& ijk) {
+    ijk.clear();
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p - i; ++j)
+            for (int k = 0; k <= p - i - j; ++k) {
+                ijk.push_back(i);
+                ijk.push_back(j);
+                ijk.push_back(k);
+            }
+}
+
+void index2(int p, std::vector<int>& ij) {
+    ij.clear();
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p - i; ++j) {
+            ij.push_back(i);
+            ij.push_back(j);
+        }
+}
+
+double dubiner3_norm2(int i, int j, int k) {
+    return 1.0 / (2.0 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3));
+}
+
+double dubiner2_norm2(int i, int j) { return 1.0 / (2.0 * (2 * i + 1) * (i + j + 1)); }
+
+namespace {
+
+// Gauss-Legendre nodes/weights on [0,1] (Newton on P_n).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+        }
+        x[i] = 0.5 * (1.0 + t);
+        w[i] = 1.0 / ((1.0 - t * t) * dp * dp);    // (2/((1-t^2) P'^2)) / 2
+    }
+}
+
+// P_n^(a,b)(t) for n = 0..N.
+void jacobi_all(int N, double a, double b, double t, double* out) {
+    out[0] = 1.0;
+    if (N == 0) return;
+    out[1] = 0.5 * ((a + b + 2.0) * t + (a - b));
+    for (int n = 1; n < N; ++n) {
+        double c = 2.0 * n + a + b;
+        double a1 = 2.0 * (n + 1) * (n + a + b + 1) * c;
+        double a2 = (c + 1.0) * (a * a - b * b);
+        double a3 = c * (c + 1.0) * (c + 2.0);
+        double a4 = 2.0 * (n + a) * (n + b) * (c + 2.0);
+        out[n + 1] = ((a2 + a3 * t) * out[n] - a4 * out[n - 1]) / a1;
+    }
+}
+
+// P_n^(a,0)(t) and its derivative, n = 0..N.
+void jacobi_d(int N, double a, double t, double* val, double* der) {
+    jacobi_all(N, a, 0.0, t, val);
+    std::vector<double> tmp(N + 1);
+    der[0] = 0.0;
+    if (N >= 1) {
+        jacobi_all(N - 1, a + 1.0, 1.0, t, tmp.data());
+        for (int n = 1; n <= N; ++n) der[n] = 0.5 * (n + a + 1.0) * tmp[n - 1];
+    }
+}
+
+double ipow(double x, int n) {
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+// Values and Cartesian derivatives of all phi_ijk (|ijk| <= p) at the
+// collapsed point (xi, eta, zeta) (interior: xi, eta < 1).
+void phi3_at(int p, const std::vector<int>& idx, double xi, double eta, double zeta,
+             double* val, double* dx, double* dy, double* dz) {
+    const int N = (int)idx.size() / 3;
+    std::vector<double> L(p + 1), Ld(p + 1), J(p + 1), Jd(p + 1), K(p + 1), Kd(p + 1);
+    jacobi_d(p, 0.0, 2.0 * zeta - 1.0, L.data(), Ld.data());
+    const double om_xi = 1.0 - xi, om_eta = 1.0 - eta;
+    int lasti = -1, lastij = -1;
+    for (int r = 0; r < N; ++r) {
+        const int i = idx[3 * r], j = idx[3 * r + 1], k = idx[3 * r + 2];
+        if (i != lasti) {
+            jacobi_d(p - i, 2.0 * i + 1.0, 2.0 * eta - 1.0, J.data(), Jd.data());
+            lasti = i;
+            lastij = -1;
+        }
+        if (i + j != lastij) {
+            jacobi_d(p - i - j, 2.0 * i + 2.0 * j + 2.0, 2.0 * xi - 1.0, K.data(), Kd.data());
+            lastij = i + j;
+        }
+        const double A = L[i], Ad = 2.0 * Ld[i];
+        const double B = ipow(om_eta, i) * J[j];
+        const double Bd = (i > 0 ? -i * ipow(om_eta, i - 1) * J[j] : 0.0) + ipow(om_eta, i) * 2.0 * Jd[j];
+        const double C = ipow(om_xi, i + j) * K[k];
+        const double Cd = (i + j > 0 ? -(i + j) * ipow(om_xi, i + j - 1) * K[k] : 0.0)
+                          + ipow(om_xi, i + j) * 2.0 * Kd[k];
+        const double f = A * B * C;
+        const double fxi = A * B * Cd, feta = A * Bd * C, fzeta = Ad * B * C;
+        val[r] = f;
+        if (dx) {
+            dx[r] = fxi + eta / om_xi * feta + zeta / (om_xi * om_eta) * fzeta;
+            dy[r] = feta / om_xi + zeta / (om_xi * om_eta) * fzeta;
+            dz[r] = fzeta / (om_xi * om_eta);
+        }
+    }
+}
+
+// Values of phi_ijk at a Cartesian reference point (interior of a face or cell).
+void phi3_cart(int p, const std::vector<int>& idx, const double* xh, double* val) {
+    const double xi = xh[0];
+    const double eta = xh[1] / (1.0 - xh[0]);
+    const double zeta = xh[2] / (1.0 - xh[0] - xh[1]);
+    phi3_at(p, idx, xi, eta, zeta, val, nullptr, nullptr, nullptr);
+}
+
+// psi_ij (Eq. (4)) at the collapsed face point (a, b): s = a, u = (1-a) b.
+void psi2_at(int p, const std::vector<int>& idx, double a, double b, double* val) {
+    const int N = (int)idx.size() / 2;
+    std::vector<double> L(p + 1), Ld(p + 1), J(p + 1), Jd(p + 1);
+    jacobi_d(p, 0.0, 2.0 * b - 1.0, L.data(), Ld.data());
+    int lasti = -1;
+    for (int r = 0; r < N; ++r) {
+        const int i = idx[2 * r], j = idx[2 * r + 1];
+        if (i != lasti) {
+            jacobi_d(p - i, 2.0 * i + 1.0, 2.0 * a - 1.0, J.data(), Jd.data());
+            lasti = i;
+        }
+        val[r] = L[i] * ipow(1.0 - a, i) * J[j];
+    }
+}
+
+const double kVert[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+void face_trace(int p, int f, std::vector<double>& T) {
+    // T[g][a] = int psi'_g(s,u) phi'_a(xh_f(s,u)) ds du, face modes of degree <= p
+    std::vector<int> i3, i2;
+    index3(p, i3);
+    index2(p, i2);
+    const int NE = (int)i3.size() / 3, N2 = (int)i2.size() / 2;
+    int v[3], c = 0;
+    for (int q = 0; q < 4; ++q)
+        if (q != f) v[c++] = q;
+    std::vector<double> xa, wa, xb, wb;
+    const int nq = p + 2;
+    gauss_legendre01(nq, xa, wa);
+    gauss_legendre01(nq, xb, wb);
+    std::vector<double> phi(NE), psi(N2);
+    T.assign((size_t)N2 * NE, 0.0);
+    for (int qa = 0; qa < nq; ++qa)
+        for (int qb = 0; qb < nq; ++qb) {
+            const double s = xa[qa], u = (1.0 - xa[qa]) * xb[qb];
+            const double w = wa[qa] * wb[qb] * (1.0 - xa[qa]);
+            double xh[3];
+            for (int d = 0; d < 3; ++d)
+                xh[d] = kVert[v[0]][d] + s * (kVert[v[1]][d] - kVert[v[0]][d])
+                        + u * (kVert[v[2]][d] - kVert[v[0]][d]);
+            phi3_cart(p, i3, xh, phi.data());
+            psi2_at(p, i2, xa[qa], xb[qb], psi.data());
+            for (int g = 0; g < N2; ++g)
+                for (int a = 0; a < NE; ++a) T[(size_t)g * NE + a] += w * psi[g] * phi[a];
+        }
+    for (int g = 0; g < N2; ++g) {
+        const double ng = std::sqrt(dubiner2_norm2(i2[2 * g], i2[2 * g + 1]));
+        for (int a = 0; a < NE; ++a) {
+            const double na = std::sqrt(dubiner3_norm2(i3[3 * a], i3[3 * a + 1], i3[3 * a + 2]));
+            T[(size_t)g * NE + a] /= (ng * na);
+        }
+    }
+}
+
+}  // namespace
+
+void collapsed_rule(int q1d, std::vector<double>& xh, std::vector<double>& w, std::vector<double>& col) {
+    std::vector<double> g, gw;
+    gauss_legendre01(q1d, g, gw);
+    const int nq = q1d * q1d * q1d;
+    xh.resize(3 * nq);
+    w.resize(nq);
+    col.resize(3 * nq);
+    int q = 0;
+    for (int a = 0; a < q1d; ++a)
+        for (int b = 0; b < q1d; ++b)
+            for (int c = 0; c < q1d; ++c, ++q) {
+                const double xi = g[a], eta = g[b], zeta = g[c];
+                xh[3 * q] = xi;
+                xh[3 * q + 1] = (1.0 - xi) * eta;
+                xh[3 * q + 2] = (1.0 - xi) * (1.0 - eta) * zeta;
+                w[q] = gw[a] * gw[b] * gw[c] * (1.0 - xi) * (1.0 - xi) * (1.0 - eta);
+                col[3 * q] = xi;
+                col[3 * q + 1] = eta;
+                col[3 * q + 2] = zeta;
+            }
+}
+
+void phi_table(int p, int q1d, std::vector<double>& phi) {
+    std::vector<double> xh, w, col;
+    collapsed_rule(q1d, xh, w, col);
+    std::vector<int> idx;
+    index3(p, idx);
+    const int N = (int)idx.size() / 3, nq = (int)w.size();
+    phi.resize((size_t)nq * N);
+    for (int q = 0; q < nq; ++q) {
+        phi3_at(p, idx, col[3 * q], col[3 * q + 1], col[3 * q + 2], &phi[(size_t)q * N], nullptr, nullptr, nullptr);
+        for (int a = 0; a < N; ++a)
+            phi[(size_t)q * N + a] /= std::sqrt(dubiner3_norm2(idx[3 * a], idx[3 * a + 1], idx[3 * a + 2]));
+    }
+}
+
+int build_ref_tables(int p, RefTables& t) {
+    if (p < 1 || p > DGM_PMAX) {
+        set_error("p must be in [1, DGM_PMAX]");
+        return DGM_ERR_INVALID_ARG;
+    }
+    std::vector<int> iE, iH, i2E, i2H;
+    index3(p, iE);
+    index3(p - 1, iH);
+    index2(p, i2E);
+    index2(p - 1, i2H);
+    t.p = p;
+    t.NE = (int)iE.size() / 3;
+    t.NH = (int)iH.size() / 3;
+    t.N2E = (int)i2E.size() / 2;
+    t.N2H = (int)i2H.size() / 2;
+    t.norm2E.resize(t.NE);
+    for (int a = 0; a < t.NE; ++a) t.norm2E[a] = dubiner3_norm2(iE[3 * a], iE[3 * a + 1], iE[3 * a + 2]);
+
+    // derivative tables: (d_d phi'_a, phi'_b), b over the degree p-1 basis
+    const int nq = p + 2;
+    std::vector<double> gx, gw;
+    gauss_legendre01(nq, gx, gw);
+    for (int d = 0; d < 3; ++d) t.D[d].assign((size_t)t.NH * t.NE, 0.0);
+    std::vector<double> v(t.NE), dx(t.NE), dy(t.NE), dz(t.NE), vh(t.NH);
+    for (int a = 0; a < nq; ++a)
+        for (int b = 0; b < nq; ++b)
+            for (int c = 0; c < nq; ++c) {
+                const double xi = gx[a], eta = gx[b], zeta = gx[c];
+                const double w = gw[a] * gw[b] * gw[c] * (1.0 - xi) * (1.0 - xi) * (1.0 - eta);
+                phi3_at(p, iE, xi, eta, zeta, v.data(), dx.data(), dy.data(), dz.data());
+                phi3_at(p - 1, iH, xi, eta, zeta, vh.data(), nullptr, nullptr, nullptr);
+                for (int bb = 0; bb < t.NH; ++bb) {
+                    const double wb = w * vh[bb];
+                    double* Dx = &t.D[0][(size_t)bb * t.NE];
+                    double* Dy = &t.D[1][(size_t)bb * t.NE];
+                    double* Dz = &t.D[2][(size_t)bb * t.NE];
+                    for (int aa = 0; aa < t.NE; ++aa) {
+                        Dx[aa] += wb * dx[aa];
+                        Dy[aa] += wb * dy[aa];
+                        Dz[aa] += wb * dz[aa];
+                    }
+                }
+            }
+    for (int bb = 0; bb < t.NH; ++bb) {
+        const double nb = std::sqrt(dubiner3_norm2(iH[3 * bb], iH[3 * bb + 1], iH[3 * bb + 2]));
+        for (int aa = 0; aa < t.NE; ++aa) {
+            const double na = std::sqrt(t.norm2E[aa]);
+            for (int d = 0; d < 3; ++d) t.D[d][(size_t)bb * t.NE + aa] /= (na * nb);
+        }
+    }
+    for (int f = 0; f < 4; ++f) {
+        face_trace(p, f, t.TrE[f]);
+        face_trace(p - 1, f, t.TrH[f]);
+    }
+    // face frames and reference orientation signs
+    const double nhat[4][3] = {{1, 1, 1}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}};
+    for (int f = 0; f < 4; ++f) {
+        int v[3], c = 0;
+        for (int q = 0; q < 4; ++q)
+            if (q != f) v[c++] = q;
+        for (int m = 0; m < 3; ++m) {
+            t.that[f][0][m] = kVert[v[1]][m] - kVert[v[0]][m];
+            t.that[f][1][m] = kVert[v[2]][m] - kVert[v[0]][m];
+        }
+        const double* a = t.that[f][0];
+        const double* b = t.that[f][1];
+        const double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        const double dot = cr[0] * nhat[f][0] + cr[1] * nhat[f][1] + cr[2] * nhat[f][2];
+        t.sigma_hat[f] = dot > 0 ? 1.0 : -1.0;
+    }
+    t.pos2H.resize(t.N2H);
+    for (int g = 0; g < t.N2H; ++g) {
+        const int i = i2H[2 * g], j = i2H[2 * g + 1];
+        int pos = -1;
+        for (int q = 0; q < t.N2E; ++q)
+            if (i2E[2 * q] == i && i2E[2 * q + 1] == j) pos = q;
+        t.pos2H[g] = pos;
+    }
+    return DGM_OK;
+}
+
+}  // namespace dgm

@@ -1,0 +1,65 @@
+"""Convenience wrapper owning the C-ABI handles of one problem.
+
+Argument marshalling only: every step runs in libdgm.so.
+"""
+
+import numpy as np
+
+from . import _capi as capi
+
+
+class Solver:
+    """mesh + p + eps + mu -> device-resident DG Maxwell problem (include/dgm.h)."""
+
+    def __init__(self, xyz, tets, p, eps, mu, vertex_key=None, precision="fp64",
+                 flux="central", alpha0=1.0, device=0):
+        self.ctx = capi.dgm_create(device)
+        self.mesh = capi.dgm_mesh_create(self.ctx, xyz, tets, vertex_key)
+        self.nt, self.nfaces, self.nboundary = capi.dgm_mesh_info(self.mesh)
+        opt = capi.dgm_default_options()
+        opt.precision = {"fp64": capi.DGM_PREC_FP64, "fp32": capi.DGM_PREC_FP32}[precision]
+        opt.flux = {"central": capi.DGM_FLUX_CENTRAL, "stabilized": capi.DGM_FLUX_STABILIZED}[flux]
+        opt.alpha0 = alpha0
+        eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.nt,))
+        mu = np.broadcast_to(np.asarray(mu, dtype=np.float64), (self.nt,))
+        self.prob = capi.dgm_problem_create(self.ctx, self.mesh, p, eps, mu, opt)
+        self.p = p
+        self.nE, self.nH, self.nHF = capi.dgm_problem_sizes(self.prob)
+
+    def set_fields(self, E, H, HF=None):
+        capi.dgm_set_fields(self.prob, E, H, HF)
+
+    def get_fields(self):
+        E = np.empty(self.nE)
+        H = np.empty(self.nH)
+        HF = np.empty(self.nHF) if self.nHF else None
+        capi.dgm_get_fields(self.prob, E, H, HF)
+        return (E, H, HF) if self.nHF else (E, H)
+
+    def kick(self, which, dt, stream=None):
+        capi.dgm_kick(self.prob, which, dt, stream)
+
+    def run(self, dt, nsteps, stream=None, energies=False):
+        out = np.empty(nsteps + 1) if energies else None
+        capi.dgm_run(self.prob, dt, nsteps, stream, out)
+        return out
+
+    def energy(self):
+        return capi.dgm_energy(self.prob)
+
+    def close(self):
+        if getattr(self, "prob", None):
+            capi.dgm_problem_destroy(self.prob)
+            self.prob = None
+        if getattr(self, "mesh", None):
+            capi.dgm_mesh_destroy(self.mesh)
+            self.mesh = None
+        if getattr(self, "ctx", None):
+            capi.dgm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,130 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load and export every entry point that include/dgm.h
+declares; the reference tables it generates on the host must agree with the
+oracle's own quadrature of the printed basis; input validation must reject
+bad meshes and arguments with the documented codes.
+"""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1104_4208_gb300 import build
+    build.build()
+    from paper_1104_4208_gb300 import _capi
+    return _capi
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dgm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgm_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(capi):
+    declared = _declared()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(capi._lib, name), name
+    assert set(declared) <= set(capi.exported_symbols())
+
+
+def test_version_and_defaults(capi):
+    assert capi.dgm_version() >= 100
+    o = capi.dgm_default_options()
+    assert o.flux == capi.DGM_FLUX_CENTRAL and o.precision == capi.DGM_PREC_FP64 and o.alpha0 == 1.0
+
+
+def _oracle_tables(p):
+    from oracle.basis import phi3, psi2, index3
+    from oracle.quadrature import tet_rule, tri_rule
+    x, w = tet_rule(p + 2)
+    vE, gE = phi3(p, x)
+    vH, _ = phi3(p - 1, x)
+    nE = np.sqrt((vE * w * vE).sum(1))
+    nH = np.sqrt((vH * w * vH).sum(1))
+    D = [((vH * w) @ gE[:, :, d].T) / nH[:, None] / nE[None, :] for d in range(3)]
+    s, ws = tri_rule(p + 2)
+    ps = psi2(p, s)
+    nps = np.sqrt((ps * ws * ps).sum(1))
+    V = np.array([[0., 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    Tr = []
+    for f in range(4):
+        a, b, c = [v for v in range(4) if v != f]
+        xh = V[a] + s[:, :1] * (V[b] - V[a]) + s[:, 1:] * (V[c] - V[a])
+        ph, _ = phi3(p, xh)
+        Tr.append(((ps * ws) @ ph.T) / nps[:, None] / nE[None, :])
+    return D, Tr, nE ** 2
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6, 8])
+def test_reference_tables_match_oracle_quadrature(capi, p):
+    """Sec. 3.2.2 / 3.2.3 tables (orthonormal basis) vs the oracle's quadrature of the
+    printed basis: derivative matrices, face traces and squared norms."""
+    D, Tr, n2 = _oracle_tables(p)
+    for d in range(3):
+        got = capi.dgm_reference_table(p, d).reshape(D[d].shape)
+        assert np.abs(got - D[d]).max() < 1e-12 * max(1.0, np.abs(D[d]).max())
+    for f in range(4):
+        got = capi.dgm_reference_table(p, 3 + f).reshape(Tr[f].shape)
+        assert np.abs(got - Tr[f]).max() < 1e-13
+    assert np.allclose(capi.dgm_reference_table(p, 7), n2, rtol=1e-13, atol=0)
+
+
+def test_reference_table_rejects_bad_p(capi):
+    with pytest.raises(capi.DgmError) as e:
+        capi.dgm_reference_table(0, 0)
+    assert e.value.code == -1
+    with pytest.raises(capi.DgmError):
+        capi.dgm_reference_table(capi.DGM_PMAX + 1, 0)
+
+
+def test_device_absent_is_an_error_not_a_crash(capi):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(capi.DgmError) as e:
+        capi.dgm_create(0)
+    assert e.value.code == -3
+
+
+def test_mesh_counts_and_adjacency(capi):
+    from workloads.mesh import kuhn_cube_mesh
+    for n in (1, 2, 3):
+        m = kuhn_cube_mesh(n, jitter=0.1, seed=n, shuffle_local=True)
+        h = capi.dgm_mesh_create(None, m.xyz, m.tets)
+        nt, nf, nb = capi.dgm_mesh_info(h)
+        assert nt == 6 * n ** 3
+        assert nb == 12 * n * n
+        assert 4 * nt == 2 * nf - nb
+        capi.dgm_mesh_destroy(h)
+    mp = kuhn_cube_mesh(3, periodic=True, shuffle_local=True, seed=4)
+    h = capi.dgm_mesh_create(None, mp.xyz, mp.tets, mp.vertex_key)
+    nt, nf, nb = capi.dgm_mesh_info(h)
+    assert nb == 0 and nf == 2 * nt
+    capi.dgm_mesh_destroy(h)
+
+
+def test_mesh_validation_errors(capi):
+    xyz = np.array([[0., 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [0.5, 0.5, 0]])
+    bad = [
+        np.array([[0, 1, 2, 7]]),                 # id out of range
+        np.array([[0, 1, 2, 2]]),                 # repeated vertex
+        np.array([[0, 1, 2, 5]]),                 # coplanar: degenerate
+        np.array([[0, 1, 2, 3], [1, 2, 0, 4], [0, 2, 1, 5 - 1]]),   # face (0,1,2) on three tets
+    ]
+    for tets in bad:
+        with pytest.raises(capi.DgmError) as e:
+            capi.dgm_mesh_create(None, xyz, tets)
+        assert e.value.code == -1
+    key = np.array([0, 1, 2, 3, 3, 5])          # vertices 3 and 4 share a key
+    with pytest.raises(capi.DgmError):
+        capi.dgm_mesh_create(None, xyz, np.array([[0, 1, 3, 4]]), key)

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (relative to the max-abs of the reference):
+  FP64: 1e-12 per operator application and on trajectories, energy drift 1e-11
+        (the oracle and the CUDA path sum in different orders and the CUDA path
+        uses FMA; observed differences are a few 1e-15).
+  FP32: 2e-5 per operator application, 2e-4 on trajectories (single-precision
+        state and arithmetic, FP64 tables rounded once, FP64 energy sums).
+"""
+
+import numpy as np
+import pytest
+
+from workloads.mesh import kuhn_cube_mesh
+from workloads.configs import make_workload
+from workloads.fields import te110_fields, gaussian_pulse_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+TOL_TRAJ = {"fp64": 1e-12, "fp32": 2e-4}
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4208_gb300 import build
+    build.build()
+    from paper_1104_4208_gb300 import _capi
+    return _capi
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _solver(capi, m, p, eps, mu=1.0, precision="fp64"):
+    from paper_1104_4208_gb300.solver import Solver
+    return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=precision)
+
+
+def _cases():
+    out = []
+    for p in (1, 2, 3, 4, 5):
+        out.append(("jitter_n2", p))
+    out.append(("jitter_n3", 3))          # 162 tets: several blocks and a ragged tail
+    out.append(("periodic_n3", 2))
+    for p in (6, 7, 8):
+        out.append(("jitter_n1", p))
+    return out
+
+
+def _mesh(name):
+    if name == "jitter_n2":
+        return kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    if name == "jitter_n3":
+        return kuhn_cube_mesh(3, jitter=0.15, seed=6, shuffle_local=True)
+    if name == "periodic_n3":
+        return kuhn_cube_mesh(3, periodic=True, shuffle_local=True, seed=2)
+    return kuhn_cube_mesh(1, jitter=0.0, seed=1, shuffle_local=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,p", _cases())
+def test_kick_parity(capi, name, p, precision):
+    """One H-kick and one E-kick (Sec. 3 symplectic Euler halves) vs the oracle."""
+    from oracle.dg import OracleDG
+    m = _mesh(name)
+    rng = np.random.default_rng(100 + p)
+    eps = rng.uniform(1, 4, m.nt)
+    mu = rng.uniform(1, 2, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key)
+    A = dg.assemble()
+    S = _solver(capi, m, p, eps, mu, precision)
+    E0 = rng.standard_normal(S.nE)
+    H0 = rng.standard_normal(S.nH)
+    dt = 0.05
+    S.set_fields(E0, H0)
+    S.kick(0, dt)
+    _, H = S.get_fields()
+    dH = dt * dg._blockmul(A["MHinv"], A["CH"] @ E0)
+    assert _rel(H - H0, dH) < TOL[precision]
+    S.set_fields(E0, H0)
+    S.kick(1, dt)
+    E, _ = S.get_fields()
+    dE = dt * dg._blockmul(A["MEinv"], A["CE"] @ H0)
+    assert _rel(E - E0, dE) < TOL[precision]
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cavity_trajectory_parity(capi, precision):
+    """Workload cavity_n4_p3 (384 tets, p=3, TE110, dt = 0.2h/p^2, 100 steps):
+    fields and the per-step discrete energy vs the oracle; energy conserved."""
+    from oracle.dg import OracleDG
+    from oracle.project import project, l2_error
+    w = make_workload("cavity_n4_p3")
+    m = w.mesh
+    dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu)
+    E0 = project(dg, lambda x: te110_fields(x, 0.0)[0], w.p)
+    H0 = project(dg, lambda x: te110_fields(x, 0.0)[1], w.p - 1)
+    Eo, Ho, _, Wo = dg.run(E0, H0, w.dt, w.steps)
+    S = _solver(capi, m, w.p, w.eps, w.mu, precision)
+    S.set_fields(E0, H0)
+    W = S.run(w.dt, w.steps, energies=True)
+    E, H = S.get_fields()
+    assert _rel(E, Eo) < TOL_TRAJ[precision]
+    assert _rel(H, Ho) < TOL_TRAJ[precision]
+    assert np.abs(W - Wo).max() / Wo[0] < TOL_TRAJ[precision]
+    drift = np.abs(W - W[0]).max() / W[0]
+    assert drift < (1e-11 if precision == "fp64" else 1e-5)
+    T = w.steps * w.dt
+    e, r = l2_error(dg, E, lambda x: te110_fields(x, T)[0], w.p)
+    eo, _ = l2_error(dg, Eo, lambda x: te110_fields(x, T)[0], w.p)
+    assert abs(e - eo) <= 1e-6 * r + (1e-12 if precision == "fp64" else 1e-4) * r
+    S.close()
+
+
+def test_energy_of_state(capi):
+    from oracle.dg import OracleDG
+    m = kuhn_cube_mesh(2, jitter=0.1, seed=9)
+    rng = np.random.default_rng(3)
+    eps = rng.uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, 3, eps, 1.0)
+    S = _solver(capi, m, 3, eps)
+    E0 = rng.standard_normal(S.nE)
+    H0 = rng.standard_normal(S.nH)
+    S.set_fields(E0, H0)
+    assert abs(S.energy() - dg.energy(E0, H0, H0)) < 1e-12 * dg.energy(E0, H0, H0)
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sampled_parity_full_pulse_workload(capi, precision):
+    """Workload pulse_n16_p4 at full size (24,576 tets, p=4, eps~U[1,4], jitter 0.15h):
+    one H-kick and one E-kick from the projected Gaussian pulse plus seeded noise,
+    compared on 96 sampled elements (interior and PEC boundary) with the oracle's
+    element-local brute-force residuals."""
+    from oracle.dg import OracleDG
+    from oracle.project import project
+    w = make_workload("pulse_n16_p4")
+    m = w.mesh
+    dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu)
+    rng = np.random.default_rng(77)
+    S = _solver(capi, m, w.p, w.eps, w.mu, precision)
+    E0 = rng.standard_normal(S.nE) * 0.1
+    H0 = rng.standard_normal(S.nH) * 0.1
+    sample = np.unique(np.concatenate([rng.choice(m.nt, 80, replace=False),
+                                       np.where((dg.geo.nbr < 0).any(1))[0][:16], [0, m.nt - 1]]))
+    dt = w.dt
+    S.set_fields(E0, H0)
+    S.kick(0, dt)
+    _, H = S.get_fields()
+    ref = dg.local_kick_H(E0, sample, dt)
+    got = H.reshape(m.nt, -1)[sample] - H0.reshape(m.nt, -1)[sample]
+    assert _rel(got, ref) < TOL[precision]
+    S.set_fields(E0, H0)
+    S.kick(1, dt)
+    E, _ = S.get_fields()
+    ref = dg.local_kick_E(H0, sample, dt)
+    got = E.reshape(m.nt, -1)[sample] - E0.reshape(m.nt, -1)[sample]
+    assert _rel(got, ref) < TOL[precision]
+    S.close()
+
+
+def test_sampled_parity_full_planewave_workload(capi):
+    """Workload planewave_n32_p6 at full size (196,608 tets, periodic, p=6), FP32:
+    one H-kick on sampled elements vs the oracle."""
+    from oracle.dg import OracleDG
+    w = make_workload("planewave_n32_p6")
+    m = w.mesh
+    dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key)
+    rng = np.random.default_rng(78)
+    S = _solver(capi, m, w.p, w.eps, w.mu, "fp32")
+    E0 = rng.standard_normal(S.nE) * 0.1
+    H0 = rng.standard_normal(S.nH) * 0.1
+    sample = np.unique(np.concatenate([rng.choice(m.nt, 24, replace=False), [0, m.nt - 1]]))
+    S.set_fields(E0, H0)
+    S.kick(0, w.dt)
+    _, H = S.get_fields()
+    ref = dg.local_kick_H(E0, sample, w.dt)
+    got = H.reshape(m.nt, -1)[sample] - H0.reshape(m.nt, -1)[sample]
+    assert _rel(got, ref) < TOL["fp32"]
+    S.close()
+
+
+def test_single_tet_all_pec(capi):
+    """Edge case: one element, every face a PEC wall, lowest and highest order."""
+    from oracle.dg import OracleDG
+    xyz = np.array([[0., 0, 0], [1, 0.1, 0], [0.2, 1, 0], [0.1, 0.3, 0.9]])
+    tets = np.array([[2, 0, 3, 1]])
+    for p in (1, capi.DGM_PMAX):
+        class M:
+            pass
+        mm = M()
+        mm.xyz, mm.tets, mm.vertex_key, mm.nt = xyz, tets, None, 1
+        dg = OracleDG(xyz, tets, p, 2.0, 1.5)
+        A = dg.assemble()
+        S = _solver(capi, mm, p, 2.0, 1.5)
+        rng = np.random.default_rng(p)
+        E0 = rng.standard_normal(S.nE)
+        H0 = rng.standard_normal(S.nH)
+        S.set_fields(E0, H0)
+        S.kick(0, 0.1)
+        S.kick(1, 0.1)
+        E, H = S.get_fields()
+        Hr = H0 + 0.1 * dg._blockmul(A["MHinv"], A["CH"] @ E0)
+        Er = E0 + 0.1 * dg._blockmul(A["MEinv"], A["CE"] @ Hr)
+        assert _rel(H, Hr) < 1e-12 and _rel(E, Er) < 1e-12
+        S.close()
+
+
+def test_deterministic_reruns(capi):
+    """Fixed-order reductions: two identical runs agree bitwise (fields and energies)."""
+    m = kuhn_cube_mesh(3, jitter=0.1, seed=4)
+    rng = np.random.default_rng(5)
+    eps = rng.uniform(1, 4, m.nt)
+    outs = []
+    for _ in range(2):
+        S = _solver(capi, m, 3, eps, 1.0, "fp32")
+        S.set_fields(np.linspace(-1, 1, S.nE), np.cos(np.arange(S.nH)))
+        W = S.run(0.005, 20, energies=True)
+        outs.append((*S.get_fields(), W))
+        S.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_invalid_arguments(capi):
+    from paper_1104_4208_gb300.solver import Solver
+    m = kuhn_cube_mesh(1)
+    with pytest.raises(capi.DgmError) as e:
+        Solver(m.xyz, m.tets, 0, 1.0, 1.0)
+    assert e.value.code == -1
+    with pytest.raises(capi.DgmError):
+        Solver(m.xyz, m.tets, 2, -1.0, 1.0)
+    S = Solver(m.xyz, m.tets, 2, 1.0, 1.0)
+    with pytest.raises(capi.DgmError):
+        S.kick(0, float("nan"))
+    with pytest.raises(capi.DgmError):
+        S.set_fields(np.zeros(S.nE), np.zeros(S.nH), np.zeros(4))
+    S.close()
