@@ -165,6 +165,18 @@ int dgm_run_timed(dgm_problem* prob, double dt, int64_t nsteps, void* stream,
  * state (no staggering), FP64. */
 int dgm_energy(dgm_problem* prob, double* W);
 
+/* The value of dgm_energy, written to *W_device (one double in device memory,
+ * on the problem's device) and ordered on `stream`, without allocating any
+ * device memory.  The paper has no counterpart; this serves callers that may
+ * not call cudaMalloc/cudaFree (for example applications that hand all device
+ * memory to their own pool at start-up).  The partial sums live in a fixed
+ * device array of 4096 doubles per device, shared by every call: calls whose
+ * kernels overlap on the GPU race on it.  The first call on a device looks up
+ * that array's address; make it before any stream capture.  Problems needing
+ * more than 4096 partial sums are rejected with DGM_ERR_INVALID_ARG (on GB300
+ * a problem uses at most 16 per SM). */
+int dgm_energy_noalloc(dgm_problem* prob, double* W_device, void* stream);
+
 /* Initial data and evaluation (Sec. 2: initial conditions; covariant L2
  * projection, which for flat elements reduces to c_a = F^T sum_q w_q phi_a(xh_q)
  * u(x_q) / ||phi_a||^2 by Sec. 3.3.1).

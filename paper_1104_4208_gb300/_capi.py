@@ -69,6 +69,7 @@ _SIGS = {
     "dgm_run": ([_vp, C.c_double, _i64, _vp, _pd], C.c_int),
     "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
     "dgm_energy": ([_vp, _pd], C.c_int),
+    "dgm_energy_noalloc": ([_vp, _vp, _vp], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
     "dgm_element_maps": ([_vp, _pd], C.c_int),
@@ -197,6 +198,10 @@ def dgm_energy(prob):
     w = C.c_double()
     _check(_lib.dgm_energy(prob, C.byref(w)))
     return w.value
+
+
+def dgm_energy_noalloc(prob, W_device_ptr, stream=None):
+    _check(_lib.dgm_energy_noalloc(prob, W_device_ptr, stream))
 
 
 def dgm_reference_table(p, which):
