@@ -303,8 +303,10 @@ def run_gpu(args, rank, world, local):
     # roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
     b = 4 if args.precision == "fp32" else 8
     NE, NH = n3(w.p), n3(w.p - 1)
-    bytes_H = w.nt * (3 * NE * b + 2 * 3 * NH * b + 16 * 8 + 16)
-    bytes_E = w.nt * (3 * NH * b + 2 * 3 * NE * b + 8 * 8 + 16)
+    # algorithmic bytes per element and phase (g = 64 B geometry, c = 20 B topology):
+    # H-phase reads E, H and writes H; E-phase reads H, E and writes E
+    bytes_H = w.nt * (b * (3 * NE + 6 * NH) + 64 + 20)
+    bytes_E = w.nt * (b * (6 * NE + 3 * NH) + 64 + 20)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
     if stats.h_phase_ms >= stats.e_phase_ms:
