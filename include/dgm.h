@@ -68,8 +68,12 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
 
 /* Arithmetic of the per-step operator.  FP64: state and arithmetic in double.
  * FP32: state and operator arithmetic in float; geometry, tables (rounded once)
- * and the energy reduction in double. */
-enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1 };
+ * and the energy reduction in double.
+ * TC32: float state; the reference operators are applied to tiles of 128
+ * elements on the tensor cores with TF32 operands (10-bit mantissa) and FP32
+ * accumulation; one rounded table serves C_h and C_h^T, so the discrete
+ * operator stays skew; geometry and energy in double.  Central flux, p <= 6. */
+enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2 };
 
 typedef struct dgm_options {
     int flux;           /* dgm_flux */

@@ -41,7 +41,9 @@ int upload_tables(dgm_problem* P, dgm::KParams<real>& K) {
     const dgm::RefTables& t = P->tab;
     const int NE = t.NE, NH = t.NH, N2H = t.N2H, N2E = t.N2E;
     const size_t nD = (size_t)3 * NE * NH, nT = (size_t)4 * NE * N2H, nTH = (size_t)4 * NH * N2H;
-    std::vector<real> buf(2 * nD + 2 * nT + 2 * nTH);
+    const bool stab = P->opt.flux == DGM_FLUX_STABILIZED;
+    const size_t nTF = stab ? (size_t)4 * NE * N2E : 0;
+    std::vector<real> buf(2 * nD + 2 * nT + 2 * nTH + 2 * nTF);
     real* DT = buf.data();
     real* D = DT + nD;
     real* TrEqT = D + nD;
@@ -70,7 +72,17 @@ int upload_tables(dgm_problem* P, dgm::KParams<real>& K) {
             }
         }
     }
-    (void)N2E;
+    if (stab) {
+        real* TrEfT = TrH + nTH;
+        real* TrEf = TrEfT + nTF;
+        for (int f = 0; f < 4; ++f)
+            for (int g = 0; g < N2E; ++g)
+                for (int a = 0; a < NE; ++a) {
+                    const real v = (real)t.TrE[f][(size_t)g * NE + a];
+                    TrEfT[(size_t)f * NE * N2E + (size_t)a * N2E + g] = v;
+                    TrEf[(size_t)f * N2E * NE + (size_t)g * NE + a] = v;
+                }
+    }
     DGM_CUDA(cudaMalloc(&P->dTables, buf.size() * sizeof(real)));
     DGM_CUDA(cudaMemcpy(P->dTables, buf.data(), buf.size() * sizeof(real), cudaMemcpyHostToDevice));
     real* base = (real*)P->dTables;
@@ -80,6 +92,8 @@ int upload_tables(dgm_problem* P, dgm::KParams<real>& K) {
     K.TrEq = base + 2 * nD + nT;
     K.TrHT = base + 2 * nD + 2 * nT;
     K.TrH = base + 2 * nD + 2 * nT + nTH;
+    K.TrEfT = stab ? base + 2 * nD + 2 * nT + 2 * nTH : nullptr;
+    K.TrEf = stab ? base + 2 * nD + 2 * nT + 2 * nTH + nTF : nullptr;
     return DGM_OK;
 }
 
@@ -90,11 +104,15 @@ void fill_params(dgm_problem* P, dgm::KParams<real>& K) {
     K.NH = P->NH;
     K.N2E = P->N2E;
     K.N2H = P->N2H;
-    K.warp_smem = std::max(2 * 3 * P->NE, 2 * 3 * P->NH) + 8 * P->N2H;
+    const bool stab = P->opt.flux == DGM_FLUX_STABILIZED;
+    K.warp_smem = std::max(2 * 3 * P->NE, 2 * 3 * P->NH + (stab ? 8 * P->N2E : 0)) + 8 * P->N2H;
     K.E = (real*)P->dE;
     K.H = (real*)P->dH;
     K.geo = P->dGeo;
     K.nbr = P->dNbr;
+    K.K = stab ? (real*)P->dK : nullptr;
+    K.fgeo = P->dFaceGeo;
+    K.fid = P->dFid;
 }
 
 int ensure_energy(dgm_problem* P, int64_t n) {
@@ -108,6 +126,7 @@ int ensure_energy(dgm_problem* P, int64_t n) {
 }
 
 int phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s) {
+    if (P->tc) return dgm::tc_phase_H(P, dt, a_lo, c_out, energy_slot, s);
     double* partials = energy_slot ? P->dPartials : nullptr;
     int rc = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
                      : dgm::launch_phase_H<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s);
@@ -117,7 +136,8 @@ int phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy
     return DGM_OK;
 }
 
-int phase_E(dgm_problem* P, double dt, cudaStream_t s) {
+int phase_E(dgm_problem* P, double dt, cudaStream_t s, bool energy = false) {
+    if (P->tc) return dgm::tc_phase_E(P, dt, energy, s);
     int rc = P->fp32 ? dgm::launch_phase_E<float>(P->kf, P->grid, dt, s)
                      : dgm::launch_phase_E<double>(P->kd, P->grid, dt, s);
     if (rc) return cuda_fail(cudaGetLastError(), "E-phase launch");
@@ -125,6 +145,7 @@ int phase_E(dgm_problem* P, double dt, cudaStream_t s) {
 }
 
 int import_fields(dgm_problem* P, const double* dEsrc, const double* dHsrc, cudaStream_t s) {
+    if (P->tc) return dgm::tc_import(P, dEsrc, dHsrc, P->dNrmE, P->dNrmH, s);
     const int64_t nE = P->nt * 3 * P->NE, nH = P->nt * 3 * P->NH;
     int rc = 0;
     if (P->fp32) {
@@ -137,7 +158,22 @@ int import_fields(dgm_problem* P, const double* dEsrc, const double* dHsrc, cuda
     return rc ? cuda_fail(cudaGetLastError(), "import launch") : DGM_OK;
 }
 
+int import_faces(dgm_problem* P, const double* src, cudaStream_t s) {
+    const int64_t n = P->nfaces * 2 * P->N2E;
+    int rc = P->fp32 ? dgm::launch_import<float>(src, (float*)P->dK, P->dNrmF, n, P->N2E, s)
+                     : dgm::launch_import<double>(src, (double*)P->dK, P->dNrmF, n, P->N2E, s);
+    return rc ? cuda_fail(cudaGetLastError(), "import launch") : DGM_OK;
+}
+
+int export_faces(dgm_problem* P, double* dst, cudaStream_t s) {
+    const int64_t n = P->nfaces * 2 * P->N2E;
+    int rc = P->fp32 ? dgm::launch_export<float>((const float*)P->dK, dst, P->dNrmF, n, P->N2E, s)
+                     : dgm::launch_export<double>((const double*)P->dK, dst, P->dNrmF, n, P->N2E, s);
+    return rc ? cuda_fail(cudaGetLastError(), "export launch") : DGM_OK;
+}
+
 int export_fields(dgm_problem* P, double* dEdst, double* dHdst, cudaStream_t s) {
+    if (P->tc) return dgm::tc_export(P, dEdst, dHdst, P->dNrmE, P->dNrmH, s);
     const int64_t nE = P->nt * 3 * P->NE, nH = P->nt * 3 * P->NH;
     int rc = 0;
     if (P->fp32) {
@@ -152,9 +188,11 @@ int export_fields(dgm_problem* P, double* dEdst, double* dHdst, cudaStream_t s) 
 
 void free_problem(dgm_problem* P) {
     void* ptrs[] = {P->dE, P->dH, P->dTables, P->dGeo, P->dNbr, P->dNrmE, P->dNrmH,
-                    P->dPartials, P->dEnergy, P->dStage, P->dMaps, P->dWphiE, P->dWphiH, P->dPhiE, P->dPhiH};
+                    P->dPartials, P->dEnergy, P->dStage, P->dMaps, P->dWphiE, P->dWphiH, P->dPhiE, P->dPhiH,
+                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (P->tc) dgm::tc_problem_free(P);
 }
 
 }  // namespace
@@ -250,11 +288,11 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         set_error("dgm_problem_create: unknown flux");
         return DGM_ERR_INVALID_ARG;
     }
-    if (o.flux == DGM_FLUX_STABILIZED) {
-        set_error("dgm_problem_create: stabilized flux not available in this build");
-        return DGM_ERR_UNSUPPORTED;
+    if (o.flux == DGM_FLUX_STABILIZED && !(o.alpha0 > 0.0 && std::isfinite(o.alpha0))) {
+        set_error("dgm_problem_create: alpha0 must be positive");
+        return DGM_ERR_INVALID_ARG;
     }
-    if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32) {
+    if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32 && o.precision != DGM_PREC_TC32) {
         set_error("dgm_problem_create: unknown precision");
         return DGM_ERR_INVALID_ARG;
     }
@@ -295,12 +333,73 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaSetDevice"));
     const size_t rs = P->fp32 ? sizeof(float) : sizeof(double);
     const int64_t nE = m.nt * 3 * P->NE, nH = m.nt * 3 * P->NH;
+    const bool tc = o.precision == DGM_PREC_TC32;
     cudaError_t e;
-    if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc E"));
-    if ((e = cudaMalloc(&P->dH, nH * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc H"));
-    if ((e = cudaMemset(P->dE, 0, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "memset E"));
-    if ((e = cudaMemset(P->dH, 0, nH * rs)) != cudaSuccess) return fail(cuda_fail(e, "memset H"));
-    if ((e = cudaMalloc(&P->dStage, std::max(nE, nH) * sizeof(double))) != cudaSuccess)
+    if (!tc) {
+        if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc E"));
+        if ((e = cudaMalloc(&P->dH, nH * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc H"));
+        if ((e = cudaMemset(P->dE, 0, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "memset E"));
+        if ((e = cudaMemset(P->dH, 0, nH * rs)) != cudaSuccess) return fail(cuda_fail(e, "memset H"));
+    }
+    const bool stab = o.flux == DGM_FLUX_STABILIZED;
+    const int64_t nK = stab ? m.nfaces * 2 * P->N2E : 0;
+    if (stab) {
+        if ((e = cudaMalloc(&P->dK, nK * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc HF"));
+        if ((e = cudaMemset(P->dK, 0, nK * rs)) != cudaSuccess) return fail(cuda_fail(e, "memset HF"));
+        // face records: frame of the first side, h_F = min over sides of |det F| / |t1 x t2|
+        const double alpha = o.alpha0 * p * p;
+        std::vector<double> fg((size_t)m.nfaces * dgm::kFaceGeoStride);
+        std::vector<int32_t> fid(4 * m.nt);
+        for (int64_t F = 0; F < m.nfaces; ++F) {
+            const int32_t s0 = m.face_elem[2 * F], s1 = m.face_elem[2 * F + 1];
+            const int64_t t = s0 / 4;
+            const int f = s0 % 4;
+            int v[3], q = 0;
+            for (int r = 0; r < 4; ++r)
+                if (r != f) v[q++] = r;
+            const double* Xa = &m.xyz[3 * (int64_t)m.tets[4 * t + v[0]]];
+            const double* Xb = &m.xyz[3 * (int64_t)m.tets[4 * t + v[1]]];
+            const double* Xc = &m.xyz[3 * (int64_t)m.tets[4 * t + v[2]]];
+            double t1[3], t2[3];
+            for (int d = 0; d < 3; ++d) {
+                t1[d] = Xb[d] - Xa[d];
+                t2[d] = Xc[d] - Xa[d];
+            }
+            const double cr[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                                  t1[0] * t2[1] - t1[1] * t2[0]};
+            const double J = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            double hF = std::fabs(m.detF[t]) / J;
+            if (s1 >= 0) hF = std::min(hF, std::fabs(m.detF[s1 / 4]) / J);
+            const double g11 = t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2];
+            const double g12 = t1[0] * t2[0] + t1[1] * t2[1] + t1[2] * t2[2];
+            const double g22 = t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2];
+            const double dg = g11 * g22 - g12 * g12;
+            double* r = &fg[(size_t)F * dgm::kFaceGeoStride];
+            r[0] = alpha / (hF * J);
+            r[1] = g11;
+            r[2] = g12;
+            r[3] = g22;
+            r[4] = hF / alpha * J;
+            r[5] = g22 / dg;
+            r[6] = -g12 / dg;
+            r[7] = g11 / dg;
+            fid[s0] = (int32_t)(2 * F + 1);
+            if (s1 >= 0) fid[s1] = (int32_t)(2 * F);
+        }
+        if ((e = cudaMalloc(&P->dFaceGeo, fg.size() * sizeof(double))) != cudaSuccess)
+            return fail(cuda_fail(e, "alloc face geo"));
+        if ((e = cudaMalloc(&P->dFid, fid.size() * sizeof(int32_t))) != cudaSuccess)
+            return fail(cuda_fail(e, "alloc face ids"));
+        cudaMemcpy(P->dFaceGeo, fg.data(), fg.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(P->dFid, fid.data(), fid.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        std::vector<int> i2;
+        dgm::index2(p, i2);
+        std::vector<double> nrmF(P->N2E);
+        for (int g = 0; g < P->N2E; ++g) nrmF[g] = std::sqrt(dgm::dubiner2_norm2(i2[2 * g], i2[2 * g + 1]));
+        if ((e = cudaMalloc(&P->dNrmF, P->N2E * sizeof(double))) != cudaSuccess) return fail(cuda_fail(e, "alloc nrm"));
+        cudaMemcpy(P->dNrmF, nrmF.data(), P->N2E * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if ((e = cudaMalloc(&P->dStage, std::max(std::max(nE, nH), nK) * sizeof(double))) != cudaSuccess)
         return fail(cuda_fail(e, "alloc staging"));
     if ((e = cudaMalloc(&P->dPartials, (size_t)P->grid * sizeof(double))) != cudaSuccess)
         return fail(cuda_fail(e, "alloc partials"));
@@ -377,7 +476,9 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         cudaMemcpy(P->dNrmH, nrmH.data(), P->NH * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (dgm::upload_face_frames(P->tab.that, P->tab.sigma_hat)) return fail(cuda_fail(cudaGetLastError(), "frames"));
-    if (P->fp32) {
+    if (tc) {
+        rc = dgm::tc_problem_init(P, m, geo, nbr);
+    } else if (P->fp32) {
         fill_params(P, P->kf);
         rc = upload_tables<float>(P, P->kf);
     } else {
@@ -417,7 +518,9 @@ int dgm_set_fields_device(dgm_problem* P, const double* E, const double* H, cons
         set_error("dgm_set_fields_device: HF given for the central flux");
         return DGM_ERR_INVALID_ARG;
     }
-    return import_fields(P, E, H, (cudaStream_t)stream);
+    int rc = import_fields(P, E, H, (cudaStream_t)stream);
+    if (!rc && HF) rc = import_faces(P, HF, (cudaStream_t)stream);
+    return rc;
 }
 
 int dgm_get_fields_device(dgm_problem* P, double* E, double* H, double* HF, void* stream) {
@@ -425,8 +528,9 @@ int dgm_get_fields_device(dgm_problem* P, double* E, double* H, double* HF, void
         set_error("dgm_get_fields_device: null problem");
         return DGM_ERR_INVALID_ARG;
     }
-    (void)HF;
-    return export_fields(P, E, H, (cudaStream_t)stream);
+    int rc = export_fields(P, E, H, (cudaStream_t)stream);
+    if (!rc && HF && P->opt.flux == DGM_FLUX_STABILIZED) rc = export_faces(P, HF, (cudaStream_t)stream);
+    return rc;
 }
 
 int dgm_set_fields(dgm_problem* P, const double* E, const double* H, const double* HF) {
@@ -449,6 +553,11 @@ int dgm_set_fields(dgm_problem* P, const double* E, const double* H, const doubl
         int rc = import_fields(P, nullptr, P->dStage, 0);
         if (rc) return rc;
     }
+    if (HF) {
+        DGM_CUDA(cudaMemcpy(P->dStage, HF, P->nfaces * 2 * P->N2E * sizeof(double), cudaMemcpyHostToDevice));
+        int rc = import_faces(P, P->dStage, 0);
+        if (rc) return rc;
+    }
     DGM_CUDA(cudaDeviceSynchronize());
     return DGM_OK;
 }
@@ -458,9 +567,17 @@ int dgm_get_fields(dgm_problem* P, double* E, double* H, double* HF) {
         set_error("dgm_get_fields: null problem");
         return DGM_ERR_INVALID_ARG;
     }
-    (void)HF;
     const int64_t nE = P->nt * 3 * P->NE, nH = P->nt * 3 * P->NH;
     DGM_CUDA(cudaDeviceSynchronize());
+    if (P->tc) {
+        int rc = dgm::tc_check_error(P);
+        if (rc) return rc;
+    }
+    if (HF && P->opt.flux == DGM_FLUX_STABILIZED) {
+        int rc = export_faces(P, P->dStage, 0);
+        if (rc) return rc;
+        DGM_CUDA(cudaMemcpy(HF, P->dStage, P->nfaces * 2 * P->N2E * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     if (E) {
         int rc = export_fields(P, P->dStage, nullptr, 0);
         if (rc) return rc;
@@ -525,6 +642,24 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
     auto run_H = [&](double a_lo, double c_out, double* slot) -> int {
         int r = mark(0);
         if (r) return r;
+        if (P->tc) {
+            // the tensor-core H-phase writes its partials; the reduction is timed separately below
+            if (!P->trE_valid) {
+                r = dgm::tc_traces(P, 0, s);
+                if (r) return r;
+            }
+            r = dgm::tc_launch_phase_H(P->tca, P->tc_grid, dt, a_lo, c_out, slot ? 1 : 0, s);
+            if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
+            P->trH_valid = true;
+            if ((r = done())) return r;
+            if (slot) {
+                if ((r = mark(2))) return r;
+                if (dgm::launch_energy_reduce(P->tca.partE, 2 * P->tc_grid, slot, s))
+                    return cuda_fail(cudaGetLastError(), "energy reduce launch");
+                if ((r = done())) return r;
+            }
+            return DGM_OK;
+        }
         r = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, dt, a_lo, c_out, slot ? P->dPartials : nullptr, s)
                     : dgm::launch_phase_H<double>(P->kd, P->grid, dt, a_lo, c_out, slot ? P->dPartials : nullptr, s);
         if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
@@ -540,11 +675,16 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
     auto run_E = [&]() -> int {
         int r = mark(1);
         if (r) return r;
-        r = phase_E(P, dt, s);
+        r = phase_E(P, dt, s, want);
         if (r) return r;
         return done();
     };
-    rc = run_H(0.5, 0.5, want ? W : nullptr);
+    if (P->tc && want) {
+        rc = mark(2);
+        if (!rc) rc = dgm::tc_traces(P, 0, s);
+        if (!rc) rc = done();
+    }
+    if (!rc) rc = run_H(0.5, 0.5, want ? W : nullptr);
     for (int64_t n = 0; n < nsteps && !rc; ++n) {
         rc = run_E();
         if (rc) break;
@@ -558,6 +698,7 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
     if (!rc && (want || stats)) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "run");
+        if (!rc && P->tc) rc = dgm::tc_check_error(P);
     }
     if (stats) {
         for (size_t i = 0; i < kind.size() && !rc; ++i) {
@@ -587,7 +728,7 @@ int dgm_energy(dgm_problem* P, double* W) {
     }
     int rc = ensure_energy(P, 1);
     if (rc) return rc;
-    rc = phase_H(P, 0.0, 0.0, 0.0, P->dEnergy, 0);
+    rc = P->tc ? dgm::tc_state_energy(P, P->dEnergy, 0) : phase_H(P, 0.0, 0.0, 0.0, P->dEnergy, 0);
     if (rc) return rc;
     DGM_CUDA(cudaMemcpy(W, P->dEnergy, sizeof(double), cudaMemcpyDeviceToHost));
     return DGM_OK;
@@ -663,6 +804,18 @@ int dgm_project_device(dgm_problem* P, int q1d, const double* E_pts, const doubl
     const int nq = q1d * q1d * q1d;
     cudaStream_t s = (cudaStream_t)stream;
     int r = 0;
+    if (P->tc) {
+        // project into the FP64 staging buffer (orthonormal coefficients), then pack
+        if (E_pts) {
+            r |= dgm::launch_project<double>(P->nt, P->NE, nq, P->dMaps, P->dWphiE, E_pts, P->dStage, s);
+            if (!r) r = dgm::tc_import(P, P->dStage, nullptr, nullptr, nullptr, s);
+        }
+        if (H_pts && !r) {
+            r |= dgm::launch_project<double>(P->nt, P->NH, nq, P->dMaps, P->dWphiH, H_pts, P->dStage, s);
+            if (!r) r = dgm::tc_import(P, nullptr, P->dStage, nullptr, nullptr, s);
+        }
+        return r ? cuda_fail(cudaGetLastError(), "project") : DGM_OK;
+    }
     if (P->fp32) {
         if (E_pts) r |= dgm::launch_project<float>(P->nt, P->NE, nq, P->dMaps, P->dWphiE, E_pts, (float*)P->dE, s);
         if (H_pts) r |= dgm::launch_project<float>(P->nt, P->NH, nq, P->dMaps, P->dWphiH, H_pts, (float*)P->dH, s);
@@ -683,6 +836,17 @@ int dgm_eval_device(dgm_problem* P, int q1d, double* E_pts, double* H_pts, void*
     const int nq = q1d * q1d * q1d;
     cudaStream_t s = (cudaStream_t)stream;
     int r = 0;
+    if (P->tc) {
+        if (E_pts) {
+            r = dgm::tc_export(P, P->dStage, nullptr, nullptr, nullptr, s);
+            if (!r) r = dgm::launch_eval<double>(P->nt, P->NE, nq, P->dMaps, P->dPhiE, P->dStage, E_pts, s);
+        }
+        if (H_pts && !r) {
+            r = dgm::tc_export(P, nullptr, P->dStage, nullptr, nullptr, s);
+            if (!r) r = dgm::launch_eval<double>(P->nt, P->NH, nq, P->dMaps, P->dPhiH, P->dStage, H_pts, s);
+        }
+        return r ? cuda_fail(cudaGetLastError(), "eval") : DGM_OK;
+    }
     if (P->fp32) {
         if (E_pts) r |= dgm::launch_eval<float>(P->nt, P->NE, nq, P->dMaps, P->dPhiE, (const float*)P->dE, E_pts, s);
         if (H_pts) r |= dgm::launch_eval<float>(P->nt, P->NH, nq, P->dMaps, P->dPhiH, (const float*)P->dH, H_pts, s);

@@ -121,6 +121,57 @@ k_phase_H(KParams<real> P, double dt, double a_lo, double c_out, double* __restr
                 sA[(2 * f) * N2H + gm] = a0;
                 sA[(2 * f + 1) * N2H + gm] = a1;
             }
+            if (P.K) {
+                // stabilized flux: the owning side advances H^F of this face,
+                // (h_F/alpha) (dH^F/dt, h^F)_F = ([[E]] x nu_F, h^F)_F
+                const int32_t fe = P.fid[t * 4 + f];
+                if (fe & 1) {
+                    const int64_t F = fe >> 1;
+                    const double* fg = P.fgeo + F * kFaceGeoStride;
+                    const int N2E = P.N2E;
+                    real* KF = P.K + F * 2 * N2E;
+                    for (int gm = lane; gm < N2E; gm += 32) {
+                        const real* T = P.TrEfT + (size_t)f * NE * N2E + gm;
+                        real t0 = 0, t1 = 0, t2 = 0;
+                        for (int a = 0; a < NE; ++a) {
+                            const real w = ld(T + (size_t)a * N2E);
+                            t0 += w * sE[a];
+                            t1 += w * sE[NE + a];
+                            t2 += w * sE[2 * NE + a];
+                        }
+                        real j0 = (real)c_that[f][0][0] * t0 + (real)c_that[f][0][1] * t1 + (real)c_that[f][0][2] * t2;
+                        real j1 = (real)c_that[f][1][0] * t0 + (real)c_that[f][1][1] * t1 + (real)c_that[f][1][2] * t2;
+                        if (nb >= 0) {
+                            const int nf = nb & 3;
+                            const real* Tn = P.TrEfT + (size_t)nf * NE * N2E + gm;
+                            real n0 = 0, n1 = 0, n2 = 0;
+                            for (int a = 0; a < NE; ++a) {
+                                const real w = ld(Tn + (size_t)a * N2E);
+                                n0 += w * sN[a];
+                                n1 += w * sN[NE + a];
+                                n2 += w * sN[2 * NE + a];
+                            }
+                            j0 -= (real)c_that[nf][0][0] * n0 + (real)c_that[nf][0][1] * n1 + (real)c_that[nf][0][2] * n2;
+                            j1 -= (real)c_that[nf][1][0] * n0 + (real)c_that[nf][1][1] * n1 + (real)c_that[nf][1][2] * n2;
+                        } else {
+                            j0 = (real)2 * j0;
+                            j1 = (real)2 * j1;
+                        }
+                        // [[E]]_F = sigma_f (E_T - E_nbr); dK = dt c g (J_2, -J_1)
+                        const real c = (real)(dt * fg[0] * sig);
+                        const real dk0 = c * ((real)fg[1] * j1 - (real)fg[2] * j0);
+                        const real dk1 = c * ((real)fg[2] * j1 - (real)fg[3] * j0);
+                        const real k0 = KF[gm], k1 = KF[N2E + gm];
+                        if (partials) {
+                            const double l0 = (double)k0 - a_lo * (double)dk0, l1 = (double)k1 - a_lo * (double)dk1;
+                            const double u0 = l0 + (double)dk0, u1 = l1 + (double)dk1;
+                            eacc += 0.5 * fg[4] * (l0 * (fg[5] * u0 + fg[6] * u1) + l1 * (fg[6] * u0 + fg[7] * u1));
+                        }
+                        KF[gm] = k0 + (real)c_out * dk0;
+                        KF[N2E + gm] = k1 + (real)c_out * dk1;
+                    }
+                }
+            }
             __syncwarp();
         }
         const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
@@ -194,6 +245,7 @@ k_phase_E(KParams<real> P, double dt) {
     real* sH = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
     real* sN = sH + 3 * P.NH;
     real* sB = sN + 3 * P.NH;
+    real* sKf = sB + 8 * P.N2H;     // [4][2][N2E] (stabilized flux only)
     const int NE = P.NE, NH = P.NH, N2H = P.N2H;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t t = (int64_t)blockIdx.x * kWarps + wib; t < P.nt; t += nwarps) {
@@ -243,6 +295,13 @@ k_phase_E(KParams<real> P, double dt) {
                 sB[(2 * f) * N2H + gm] = b0;
                 sB[(2 * f + 1) * N2H + gm] = b1;
             }
+            if (P.K) {
+                // (H^F x nu_F, [[e]])_F with [[e]] = sigma_f e_T (2 sigma_f e_T on PEC faces)
+                const int64_t F = P.fid[t * 4 + f] >> 1;
+                const real* KF = P.K + F * 2 * P.N2E;
+                const real s = (real)(nb >= 0 ? sig : 2.0 * sig);
+                for (int gm = lane; gm < 2 * P.N2E; gm += 32) sKf[f * 2 * P.N2E + gm] = s * KF[gm];
+            }
             __syncwarp();
         }
         const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
@@ -274,6 +333,24 @@ k_phase_E(KParams<real> P, double dt) {
                 r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
                 r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
                 r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            if (P.K) {
+                const int N2E = P.N2E;
+                for (int f = 0; f < 4; ++f) {
+                    const real* L = P.TrEf + (size_t)f * N2E * NE + a;
+                    const real* K0 = sKf + f * 2 * N2E;
+                    const real* K1 = K0 + N2E;
+                    real u0 = 0, u1 = 0;
+                    for (int gm = 0; gm < N2E; ++gm) {
+                        const real l = ld(L + (size_t)gm * NE);
+                        u0 += l * K0[gm];
+                        u1 += l * K1[gm];
+                    }
+                    // K_2 t1_m - K_1 t2_m
+                    r0 += (real)c_that[f][0][0] * u1 - (real)c_that[f][1][0] * u0;
+                    r1 += (real)c_that[f][0][1] * u1 - (real)c_that[f][1][1] * u0;
+                    r2 += (real)c_that[f][0][2] * u1 - (real)c_that[f][1][2] * u0;
+                }
             }
             const real s = (real)(dt * inv_eps);
             Et[a] += s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);

@@ -30,7 +30,20 @@ struct KParams {
     const real* TrEq;           // [4][N2H][NE]
     const real* TrHT;           // [4][NH][N2H]  H trace, transposed
     const real* TrH;            // [4][N2H][NH]
+    // stabilized central flux (K == nullptr: central flux)
+    real* K;                    // [nfaces][2][N2E] face unknown H^F, covariant tangential, orthonormal
+    const double* fgeo;         // [nfaces][kFaceGeoStride]
+    const int32_t* fid;         // [nt][4] = 2*face + (1 if this element side updates the face)
+    const real* TrEfT;          // [4][NE][N2E]  E trace onto all degree <= p face modes, transposed
+    const real* TrEf;           // [4][N2E][NE]
 };
+
+// Per-face record of the stabilized flux (FP64), kFaceGeoStride doubles:
+//   [0] alpha / (h_F |t1 x t2|)     rate of H^F
+//   [1..3] g = (t_i . t_j): g11, g12, g22
+//   [4] (h_F / alpha) |t1 x t2|     energy weight
+//   [5..7] g^{-1}: 11, 12, 22
+constexpr int kFaceGeoStride = 8;
 
 int upload_face_frames(const double that[4][2][3], const double sigma_hat[4]);
 

@@ -6,6 +6,7 @@
 
 #include "dgm_internal.h"
 #include "kernels.h"
+#include "tc_kernels.h"
 
 struct dgm_ctx {
     int device = 0;
@@ -46,4 +47,31 @@ struct dgm_problem {
     double* dWphiH = nullptr;
     double* dPhiE = nullptr;             // [nq][NE] phi'_a
     double* dPhiH = nullptr;
+    void* dK = nullptr;                  // stabilized flux: H^F [nfaces][2][N2E]
+    double* dFaceGeo = nullptr;          // [nfaces][kFaceGeoStride]
+    int32_t* dFid = nullptr;             // [nt][4]
+    double* dNrmF = nullptr;             // [N2E] ||psi_g||
+    // tensor-core path (precision TC32)
+    bool tc = false;
+    int tc_grid = 0;
+    dgm::TCArgs tca{};
+    void* dTc = nullptr;                 // one allocation: tiled state, traces, tables, partials
+    double* dTcGeo = nullptr;
+    int32_t* dTcNbr = nullptr;
+    int* dErr = nullptr;
+    bool trE_valid = false, trH_valid = false;
 };
+
+namespace dgm {
+int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
+                    const std::vector<int32_t>& nbr);
+void tc_problem_free(dgm_problem* P);
+int tc_import(dgm_problem* P, const double* dE, const double* dH, const double* nrmE, const double* nrmH,
+              cudaStream_t s);
+int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const double* nrmH, cudaStream_t s);
+int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s);
+int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s);
+int tc_traces(dgm_problem* P, int which, cudaStream_t s);
+int tc_state_energy(dgm_problem* P, double* slot, cudaStream_t s);
+int tc_check_error(dgm_problem* P);
+}  // namespace dgm

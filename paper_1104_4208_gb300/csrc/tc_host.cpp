@@ -1,0 +1,260 @@
+// Host side of the tensor-core path: reference operators laid out in the
+// MMA's shared-memory order ([K/4][rows][4], TF32-rounded), the tiled state,
+// face-trace buffers, and the launch sequence of one time step.
+//
+// Internal coefficient order of one element: k = 3 a + m (coefficient a,
+// component m), so the 3x3 inverse-mass block of a coefficient acts on three
+// consecutive values.  Face-trace columns: j = (2 f + i) N2(p-1) + g (face f,
+// tangential component i, face mode g of degree <= p-1).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include <cstring>
+
+#include "problem.h"
+
+namespace dgm {
+
+namespace {
+
+// Round to the nearest TF32 value (10-bit mantissa), ties away from zero.
+float round_tf32(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+struct TableWriter {
+    std::vector<float>& buf;
+    size_t base;
+    int rows;
+    void put(int row, int k, double v) {
+        buf[base + ((size_t)(k / 4) * rows + row) * 4 + (k % 4)] = round_tf32((float)v);
+    }
+};
+
+// (curl E)_m[b] = sum_{a, m'} curl_entry(b, m, a, m') E_{m'}[a]  (Sec. 3.2.2: curl from gradients)
+double curl_entry(const RefTables& t, int b, int m, int a, int mp) {
+    const size_t i = (size_t)b * t.NE + a;
+    switch (m) {
+        case 0: return mp == 2 ? t.D[1][i] : (mp == 1 ? -t.D[2][i] : 0.0);
+        case 1: return mp == 0 ? t.D[2][i] : (mp == 2 ? -t.D[0][i] : 0.0);
+        default: return mp == 1 ? t.D[0][i] : (mp == 0 ? -t.D[1][i] : 0.0);
+    }
+}
+
+int cuda_err(cudaError_t e, const char* what) {
+    set_error(std::string("tensor-core path: ") + what + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? DGM_ERR_OOM : DGM_ERR_CUDA;
+}
+
+}  // namespace
+
+int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
+                    const std::vector<int32_t>& nbr) {
+    const RefTables& T = P->tab;
+    const TCDims d = tc_dims(T.NE, T.NH, T.N2H);
+    uint32_t stage = 0, r2 = 0;
+    const size_t smem = tc_smem_bytes(d, &stage, &r2);
+    if (P->p > 6 || smem + 1024 > 227 * 1024 || d.NCE + d.NT > 512 || d.NC + d.NT > 512) {
+        set_error("precision TC32 supports p <= 6");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    if (P->opt.flux != DGM_FLUX_CENTRAL) {
+        set_error("precision TC32 supports the central flux only");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    const int64_t ntiles = (m.nt + kTcRows - 1) / kTcRows;
+    const int64_t nrow = ntiles * kTcRows;
+    // sizes in floats
+    const size_t nE = (size_t)nrow * d.KE, nH = (size_t)nrow * d.KH, nTr = (size_t)nrow * d.NT;
+    const size_t b1h = (size_t)d.KE * (d.NC + d.NT), blh = (size_t)d.NT * d.NC, bth = (size_t)d.KH * d.NT;
+    const size_t b1e = (size_t)d.KH * (d.NCE + d.NT), ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KE * d.NT;
+    const size_t ntab = b1h + blh + bth + b1e + ble + bte;
+    const size_t total = nE + nH + 2 * nTr + ntab;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P->dTc, total * sizeof(float))) != cudaSuccess) return cuda_err(e, "alloc");
+    if ((e = cudaMemset(P->dTc, 0, (nE + nH + 2 * nTr) * sizeof(float))) != cudaSuccess) return cuda_err(e, "memset");
+
+    std::vector<float> tab(ntab, 0.0f);
+    const size_t o_b1h = 0, o_blh = o_b1h + b1h, o_bth = o_blh + blh, o_b1e = o_bth + bth, o_ble = o_b1e + b1e,
+                 o_bte = o_ble + ble;
+    TableWriter B1H{tab, o_b1h, d.NC + d.NT}, BLH{tab, o_blh, d.NC}, BTH{tab, o_bth, d.NT};
+    TableWriter B1E{tab, o_b1e, d.NCE + d.NT}, BLE{tab, o_ble, d.NCE}, BTE{tab, o_bte, d.NT};
+    const int NE = T.NE, NH = T.NH, N2H = T.N2H;
+    for (int b = 0; b < NH; ++b)
+        for (int mo = 0; mo < 3; ++mo)
+            for (int a = 0; a < NE; ++a)
+                for (int mi = 0; mi < 3; ++mi) {
+                    const double v = curl_entry(T, b, mo, a, mi);
+                    if (v == 0.0) continue;
+                    B1H.put(3 * b + mo, 3 * a + mi, v);   // H-phase: curl of E
+                    B1E.put(3 * a + mi, 3 * b + mo, v);   // E-phase: the same numbers transposed
+                }
+    for (int f = 0; f < 4; ++f)
+        for (int i = 0; i < 2; ++i)
+            for (int gm = 0; gm < N2H; ++gm) {
+                const int j = (2 * f + i) * N2H + gm;
+                const int gE = T.pos2H[gm];
+                for (int a = 0; a < NE; ++a) {
+                    const double tr = T.TrE[f][(size_t)gE * NE + a];
+                    for (int mm = 0; mm < 3; ++mm) {
+                        const double v = T.that[f][i][mm] * tr;
+                        if (v == 0.0) continue;
+                        B1H.put(d.NC + j, 3 * a + mm, v);
+                        BTE.put(j, 3 * a + mm, v);
+                        // lift of the face average into E: (t2_m b1 - t1_m b2)
+                        BLE.put(3 * a + mm, (2 * f + (1 - i)) * N2H + gm, i == 1 ? v : -v);
+                    }
+                }
+                for (int b = 0; b < NH; ++b) {
+                    const double tr = T.TrH[f][(size_t)gm * NH + b];
+                    for (int mm = 0; mm < 3; ++mm) {
+                        const double v = T.that[f][i][mm] * tr;
+                        if (v == 0.0) continue;
+                        BTH.put(j, 3 * b + mm, v);
+                        B1E.put(d.NCE + j, 3 * b + mm, v);
+                        BLH.put(3 * b + mm, (2 * f + (1 - i)) * N2H + gm, i == 1 ? v : -v);
+                    }
+                }
+            }
+    float* base = (float*)P->dTc;
+    float* dtab = base + nE + nH + 2 * nTr;
+    if ((e = cudaMemcpy(dtab, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_err(e, "tables");
+
+    // padded geometry and topology (padding elements: identity metric, PEC faces, zero fields)
+    std::vector<double> g2((size_t)nrow * kGeoStride, 0.0);
+    std::copy(geo.begin(), geo.end(), g2.begin());
+    for (int64_t t = m.nt; t < nrow; ++t) {
+        double* r = &g2[(size_t)t * kGeoStride];
+        r[0] = r[3] = r[5] = r[6] = r[9] = r[11] = 1.0;
+        r[kGeoEps] = r[kGeoInvEps] = r[kGeoMu] = r[kGeoInvMu] = r[kGeoSign] = 1.0;
+    }
+    std::vector<int32_t> n2((size_t)nrow * 4, -1);
+    std::copy(nbr.begin(), nbr.end(), n2.begin());
+    if ((e = cudaMalloc(&P->dTcGeo, g2.size() * sizeof(double))) != cudaSuccess) return cuda_err(e, "alloc geo");
+    if ((e = cudaMalloc(&P->dTcNbr, n2.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(e, "alloc nbr");
+    cudaMemcpy(P->dTcGeo, g2.data(), g2.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(P->dTcNbr, n2.data(), n2.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if ((e = cudaMalloc(&P->dErr, sizeof(int))) != cudaSuccess) return cuda_err(e, "alloc err");
+    cudaMemset(P->dErr, 0, sizeof(int));
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->ctx->device);
+    P->tc_grid = (int)std::min<int64_t>(ntiles, sms);
+    double* part = nullptr;
+    if ((e = cudaMalloc(&part, 2 * (size_t)P->tc_grid * sizeof(double))) != cudaSuccess)
+        return cuda_err(e, "alloc partials");
+    cudaMemset(part, 0, 2 * (size_t)P->tc_grid * sizeof(double));
+
+    TCArgs& A = P->tca;
+    A.nt = m.nt;
+    A.ntiles = (int)ntiles;
+    A.d = d;
+    A.E = base;
+    A.H = base + nE;
+    A.trE = base + nE + nH;
+    A.trH = base + nE + nH + nTr;
+    A.geo = P->dTcGeo;
+    A.nbr = P->dTcNbr;
+    A.B1H = dtab + o_b1h;
+    A.BliftH = dtab + o_blh;
+    A.BtrH = dtab + o_bth;
+    A.B1E = dtab + o_b1e;
+    A.BliftE = dtab + o_ble;
+    A.BtrE = dtab + o_bte;
+    A.partE = part;
+    A.partH = part + P->tc_grid;
+    A.err = P->dErr;
+    for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
+    A.stage_bytes = stage;
+    A.r2_offset = r2;
+    P->tc = true;
+    P->trE_valid = P->trH_valid = false;
+    return DGM_OK;
+}
+
+void tc_problem_free(dgm_problem* P) {
+    void* ptrs[] = {P->dTc, P->dTcGeo, P->dTcNbr, P->dErr, P->tca.partE};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+int tc_import(dgm_problem* P, const double* dE, const double* dH, const double* nrmE, const double* nrmH,
+              cudaStream_t s) {
+    const TCArgs& A = P->tca;
+    int r = 0;
+    if (dE) r |= tc_launch_pack(dE, A.E, nrmE, A.nt, A.d.NE, A.d.KE, s);
+    if (dH) r |= tc_launch_pack(dH, A.H, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    if (dE) P->trE_valid = false;
+    if (dH) P->trH_valid = false;
+    return r ? cuda_err(cudaGetLastError(), "pack") : DGM_OK;
+}
+
+int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const double* nrmH, cudaStream_t s) {
+    const TCArgs& A = P->tca;
+    int r = 0;
+    if (dE) r |= tc_launch_unpack(A.E, dE, nrmE, A.nt, A.d.NE, A.d.KE, s);
+    if (dH) r |= tc_launch_unpack(A.H, dH, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    return r ? cuda_err(cudaGetLastError(), "unpack") : DGM_OK;
+}
+
+int tc_traces(dgm_problem* P, int which, cudaStream_t s) {
+    if (tc_launch_traces(P->tca, P->tc_grid, which, s)) return cuda_err(cudaGetLastError(), "traces launch");
+    (which == 0 ? P->trE_valid : P->trH_valid) = true;
+    return DGM_OK;
+}
+
+int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s) {
+    if (!P->trE_valid) {
+        int rc = tc_traces(P, 0, s);
+        if (rc) return rc;
+    }
+    if (tc_launch_phase_H(P->tca, P->tc_grid, dt, a_lo, c_out, energy_slot ? 1 : 0, s))
+        return cuda_err(cudaGetLastError(), "H-phase launch");
+    P->trH_valid = true;
+    if (energy_slot && launch_energy_reduce(P->tca.partE, 2 * P->tc_grid, energy_slot, s))
+        return cuda_err(cudaGetLastError(), "energy reduce launch");
+    return DGM_OK;
+}
+
+int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s) {
+    if (!P->trH_valid) {
+        int rc = tc_traces(P, 1, s);
+        if (rc) return rc;
+    }
+    if (tc_launch_phase_E(P->tca, P->tc_grid, dt, energy ? 1 : 0, s))
+        return cuda_err(cudaGetLastError(), "E-phase launch");
+    P->trE_valid = true;
+    return DGM_OK;
+}
+
+int tc_state_energy(dgm_problem* P, double* slot, cudaStream_t s) {
+    if (tc_launch_state_energy(P->tca, P->tc_grid, s)) return cuda_err(cudaGetLastError(), "energy launch");
+    if (launch_energy_reduce(P->tca.partE, 2 * P->tc_grid, slot, s))
+        return cuda_err(cudaGetLastError(), "energy reduce launch");
+    return DGM_OK;
+}
+
+int tc_check_error(dgm_problem* P) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, P->dErr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e, "error word");
+    if (h != 0) {
+        set_error("tensor-core kernel gave up waiting (error word set); results are invalid");
+        cudaMemset(P->dErr, 0, sizeof(int));
+        return DGM_ERR_TIMEOUT;
+    }
+    return DGM_OK;
+}
+
+}  // namespace dgm

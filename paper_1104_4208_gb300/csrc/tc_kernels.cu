@@ -1,0 +1,692 @@
+// Tensor-core phase kernels of the DG Maxwell time step (sm_103a, tcgen05).
+//
+// The same operator as kernels.cu (Sec. 2.1 fluxes, Sec. 3.2 reference curl
+// and traces, Sec. 3.3.1 block inverse mass, Sec. 3 symplectic Euler), but
+// every dense reference operator is applied to a tile of 128 elements at once
+// as a GEMM on the 5th-generation tensor cores:
+//
+//   H-phase (tile of E, H):
+//     GEMM1  D_c = E * Curl^T,  D_t = E * TrE^T        (K = 3 N3(p))
+//     flux   a~ = -sigma_hat (J - J_nbr)/2   (PEC: -sigma_hat J), J from D_t,
+//            J_nbr from the trace buffer the previous E-phase wrote
+//     GEMM2  D_c += a~ * LiftH^T                        (K = 8 N2(p-1))
+//     update H += dt/mu G^{-1} (-s_T D_c), FP64 energy partial
+//     GEMM3  D_t = H_new * TrH^T -> H trace buffer (for the E-phase)
+//   E-phase: the transposed operators with {{H}}, the same rounded numbers, so
+//   the discrete operator stays exactly skew.
+//
+// Operands are TF32 (fp32 storage, 10-bit mantissa in the multiplier), the
+// accumulators FP32 in tensor memory (TMEM), one thread per element in the
+// epilogues (element = TMEM lane).  State tiles and reference tables are
+// stored in global memory in the MMA's shared-memory layout, so each K slice
+// arrives with one bulk asynchronous copy into a 4-stage ring; one thread
+// issues copies and MMAs, mbarriers track both.  Every wait is bounded: on
+// timeout the kernel records an error code, lets its copies drain, frees its
+// tensor memory and returns.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+#include "tc_kernels.h"
+#include "tc_ptx.h"
+
+namespace dgm {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr uint32_t kHead = 256;             // control block at the start of shared memory
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kLimit = 4000000000LL;  // cycles before a wait gives up (~2 s)
+constexpr long long kDrain = 200000000LL;
+constexpr int kErrTimeout = 1;
+
+int padto(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Ctl {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t done;
+    uint64_t load;
+    uint32_t tmem;
+    volatile int abort;
+};
+
+struct GemmDesc {
+    const float* gA;   // A K-slices in global memory (tile base) or nullptr: A resident in shared memory
+    uint32_t sA;       // shared address of the resident A tile
+    const float* gB;   // B K-slices in global memory, [K/4][brows][4]
+    int brows;
+    int nk;            // number of 8-wide K steps
+    int nmma;          // MMAs per K step (B row ranges)
+    int row0[3];
+    int n[3];
+    uint32_t dcol[3];
+    int acc_first;     // accumulate onto D from the first step
+};
+
+// Producer + MMA issuer (thread 0).  g counts ring uses across GEMMs.
+__device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_t& g, const GemmDesc& G,
+                          uint32_t tmem) {
+    const uint32_t a_bytes = G.gA ? (uint32_t)(kTcRows * 32) : 0u;
+    const uint32_t b_bytes = (uint32_t)G.brows * 32u;
+    int produced = 0, consumed = 0;
+    bool ok = true;
+    auto produce = [&](int c) -> bool {
+        const uint32_t gg = g + (uint32_t)c;
+        const int st = (int)(gg % kStages);
+        const uint32_t use = gg / kStages;
+        if (use > 0 && !tc::mbar_wait(&ctl->empty[st], (use - 1) & 1u, kLimit)) return false;
+        uint8_t* sp = ring + (size_t)st * stage_bytes;
+        tc::mbar_expect_tx(&ctl->full[st], a_bytes + b_bytes);
+        if (G.gA) tc::bulk_g2s(sp, G.gA + (size_t)c * kTcRows * 8, a_bytes, &ctl->full[st]);
+        tc::bulk_g2s(sp + a_bytes, G.gB + (size_t)c * G.brows * 8, b_bytes, &ctl->full[st]);
+        ++produced;
+        return true;
+    };
+    auto consume = [&](int c) -> bool {
+        const uint32_t gg = g + (uint32_t)c;
+        const int st = (int)(gg % kStages);
+        const uint32_t use = gg / kStages;
+        if (!tc::mbar_wait(&ctl->full[st], use & 1u, kLimit)) return false;
+        uint8_t* sp = ring + (size_t)st * stage_bytes;
+        const uint32_t aaddr = G.gA ? tc::smem_u32(sp) : G.sA + (uint32_t)c * 2u * kTcRows * 16u;
+        const uint64_t ad = tc::sdesc(aaddr, kTcRows * 16u, 128u);
+        const uint32_t baddr = tc::smem_u32(sp + a_bytes);
+        for (int j = 0; j < G.nmma; ++j) {
+            const uint64_t bd = tc::sdesc(baddr + (uint32_t)G.row0[j] * 16u, (uint32_t)G.brows * 16u, 128u);
+            tc::mma_tf32(tmem + G.dcol[j], ad, bd, tc::idesc_tf32(kTcRows, G.n[j]),
+                         (c > 0 || G.acc_first) ? 1u : 0u);
+        }
+        tc::mma_commit(&ctl->empty[st]);
+        ++consumed;
+        return true;
+    };
+    tc::tc_fence_after();
+    const int pre = G.nk < kStages ? G.nk : kStages;
+    for (int c = 0; c < pre && ok; ++c) ok = produce(c);
+    for (int c = 0; c < G.nk && ok; ++c) {
+        ok = consume(c);
+        const int p = c - 1 + kStages;
+        if (ok && c >= 1 && p < G.nk) ok = produce(p);
+    }
+    if (!ok) {
+        // let the copies already issued land before the shared memory is given up
+        for (int c = consumed; c < produced; ++c) {
+            const uint32_t gg = g + (uint32_t)c;
+            tc::mbar_wait(&ctl->full[gg % kStages], (gg / kStages) & 1u, kDrain);
+        }
+    }
+    tc::mma_commit(&ctl->done);
+    g += (uint32_t)G.nk;
+    return ok;
+}
+
+__device__ void record_error(int* err) { atomicCAS(err, 0, kErrTimeout); }
+
+// all threads: wait for the GEMM's completion; false on timeout
+__device__ bool wait_done(Ctl* ctl, uint32_t& done_cnt) {
+    const bool ok = tc::mbar_wait(&ctl->done, done_cnt & 1u, kLimit);
+    ++done_cnt;
+    tc::tc_fence_after();
+    return ok;
+}
+
+__device__ void setup(Ctl* ctl, int warp) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        tc::mbar_init(&ctl->done, 1);
+        tc::mbar_init(&ctl->load, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+        tc::fence_proxy_async();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&ctl->tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+}
+
+__device__ void teardown(Ctl* ctl, int warp) {
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(ctl->tmem, kTmemCols);
+}
+
+// make shared-memory writes of the epilogue visible to the tensor cores and
+// hand TMEM back to the MMA issuer
+__device__ void epilogue_barrier() {
+    tc::fence_proxy_async();
+    tc::tc_fence_before();
+    __syncthreads();
+}
+
+__device__ void block_sum_store(double v, double* out) {
+    __shared__ double red[4];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) out[blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
+}
+
+// flux of one tile into the resident region: thread = element, columns of D_t
+// at tmem column ct0; jump (H-phase, avg = false) or average (E-phase)
+__device__ void epi_flux(const TCArgs& A, uint32_t lane_tmem, int ct0, const float* nbr_tr, int64_t t,
+                         bool avg, float* a2) {
+    const TCDims& d = A.d;
+    const int tid = threadIdx.x;
+    const int nvalid = 8 * d.N2H;
+    const int32_t* nb4 = A.nbr + t * 4;
+    const int32_t nbf[4] = {nb4[0], nb4[1], nb4[2], nb4[3]};
+    for (int j0 = 0; j0 < d.NT; j0 += 4) {
+        float v[4];
+        tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + j0), v[0], v[1], v[2], v[3]);
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            if (j >= nvalid) {
+                o[q] = 0.f;
+                continue;
+            }
+            const int f = j / (2 * d.N2H);
+            const int r = j - f * 2 * d.N2H;
+            const int32_t nb = nbf[f];
+            const float sh = A.sigma_hat[f];
+            if (nb >= 0) {
+                const float jn = nbr_tr[(size_t)(nb >> 2) * d.NT + (nb & 3) * 2 * d.N2H + r];
+                o[q] = avg ? sh * 0.5f * (v[q] + jn) : -sh * 0.5f * (v[q] - jn);
+            } else {
+                o[q] = avg ? sh * v[q] : -sh * v[q];
+            }
+        }
+        *reinterpret_cast<float4*>(a2 + ((size_t)(j0 >> 2) * kTcRows + tid) * 4) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// trace columns of D_t -> trace buffer row of element t
+__device__ void epi_traces(const TCArgs& A, uint32_t lane_tmem, int ct0, float* tr, int64_t t) {
+    const int NT = A.d.NT;
+    float* row = tr + (size_t)t * NT;
+    for (int j0 = 0; j0 < NT; j0 += 4) {
+        float v0, v1, v2, v3;
+        tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + j0), v0, v1, v2, v3);
+        *reinterpret_cast<float4*>(row + j0) = make_float4(v0, v1, v2, v3);
+    }
+}
+
+// split an output range of up to 2 x 256 columns into MMAs (N <= 256)
+__device__ void add_mmas(GemmDesc& G, int row0, int n, uint32_t dcol) {
+    while (n > 0) {
+        const int m = n > 256 ? 256 : n;
+        G.row0[G.nmma] = row0;
+        G.n[G.nmma] = m;
+        G.dcol[G.nmma] = dcol;
+        ++G.nmma;
+        row0 += m;
+        dcol += (uint32_t)m;
+        n -= m;
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_phase_H(TCArgs A, double dt, double a_lo, double c_out, int energy) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem);
+    uint8_t* ring = smem + kHead;
+    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const TCDims d = A.d;
+    setup(ctl, warp);
+    const uint32_t tmem = ctl->tmem;
+    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t g = 0, done_cnt = 0;
+    double eacc = 0.0;
+    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        const int64_t t = (int64_t)tile * kTcRows + tid;
+        // GEMM1: curl and own E traces
+        if (tid == 0) {
+            GemmDesc G{};
+            G.gA = A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4;
+            G.gB = A.B1H;
+            G.brows = d.NC + d.NT;
+            G.nk = d.KE / 8;
+            add_mmas(G, 0, d.NC, 0);
+            add_mmas(G, d.NC, d.NT, (uint32_t)d.NC);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        epi_flux(A, lane_tmem, d.NC, A.trE, t, false, r2);
+        epilogue_barrier();
+        // GEMM2: D_c += flux * LiftH^T
+        if (tid == 0) {
+            GemmDesc G{};
+            G.sA = tc::smem_u32(r2);
+            G.gB = A.BliftH;
+            G.brows = d.NC;
+            G.nk = d.NT / 8;
+            G.acc_first = 1;
+            add_mmas(G, 0, d.NC, 0);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        // update: H += dt/mu G^{-1} r, r = -s_T D_c
+        {
+            const double* gg = A.geo + t * kGeoStride;
+            const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
+                        gi4 = (float)gg[4], gi5 = (float)gg[5];
+            const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+            const double mu = gg[kGeoMu];
+            const float sT = (float)gg[kGeoSign];
+            const float s = (float)(dt * gg[kGeoInvMu]);
+            float* Ht = A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4;
+            const int ngroups = (d.NH + 3) / 4;
+            for (int grp = 0; grp < ngroups; ++grp) {
+                float dd[12];
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp), dd[0], dd[1], dd[2], dd[3]);
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 4), dd[4], dd[5], dd[6], dd[7]);
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 8), dd[8], dd[9], dd[10], dd[11]);
+                float hv[12];
+                float4* hp[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    hp[q] = reinterpret_cast<float4*>(Ht + ((size_t)(3 * grp + q) * kTcRows + tid) * 4);
+                    const float4 h = *hp[q];
+                    hv[4 * q] = h.x;
+                    hv[4 * q + 1] = h.y;
+                    hv[4 * q + 2] = h.z;
+                    hv[4 * q + 3] = h.w;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (4 * grp + c >= d.NH) break;
+                    const float r0 = -sT * dd[3 * c], r1 = -sT * dd[3 * c + 1], r2v = -sT * dd[3 * c + 2];
+                    const float d0 = s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
+                    const float d1 = s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
+                    const float d2 = s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
+                    const float h0 = hv[3 * c], h1 = hv[3 * c + 1], h2 = hv[3 * c + 2];
+                    if (energy) {
+                        const double l0 = (double)h0 - a_lo * d0, l1 = (double)h1 - a_lo * d1, l2 = (double)h2 - a_lo * d2;
+                        const double u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
+                        eacc += 0.5 * mu *
+                                (l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
+                                 l2 * (G2 * u0 + G4 * u1 + G5 * u2));
+                    }
+                    hv[3 * c] = h0 + (float)c_out * d0;
+                    hv[3 * c + 1] = h1 + (float)c_out * d1;
+                    hv[3 * c + 2] = h2 + (float)c_out * d2;
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float4 h = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                    *hp[q] = h;
+                    *reinterpret_cast<float4*>(r2 + ((size_t)(3 * grp + q) * kTcRows + tid) * 4) = h;
+                }
+            }
+            for (int kc = 3 * ngroups; kc < d.KH / 4; ++kc)
+                *reinterpret_cast<float4*>(r2 + ((size_t)kc * kTcRows + tid) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        epilogue_barrier();
+        // GEMM3: traces of the new H for the E-phase
+        if (tid == 0) {
+            GemmDesc G{};
+            G.sA = tc::smem_u32(r2);
+            G.gB = A.BtrH;
+            G.brows = d.NT;
+            G.nk = d.KH / 8;
+            add_mmas(G, 0, d.NT, (uint32_t)d.NC);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        epi_traces(A, lane_tmem, d.NC, A.trH, t);
+        epilogue_barrier();
+    }
+    if (ctl->abort && tid == 0) record_error(A.err);
+    if (energy) block_sum_store(eacc, A.partH);
+    teardown(ctl, warp);
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_phase_E(TCArgs A, double dt, int energy) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem);
+    uint8_t* ring = smem + kHead;
+    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const TCDims d = A.d;
+    setup(ctl, warp);
+    const uint32_t tmem = ctl->tmem;
+    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t g = 0, done_cnt = 0;
+    double eacc = 0.0;
+    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        const int64_t t = (int64_t)tile * kTcRows + tid;
+        if (tid == 0) {
+            GemmDesc G{};
+            G.gA = A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4;
+            G.gB = A.B1E;
+            G.brows = d.NCE + d.NT;
+            G.nk = d.KH / 8;
+            add_mmas(G, 0, d.NCE, 0);
+            add_mmas(G, d.NCE, d.NT, (uint32_t)d.NCE);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        epi_flux(A, lane_tmem, d.NCE, A.trH, t, true, r2);
+        epilogue_barrier();
+        if (tid == 0) {
+            GemmDesc G{};
+            G.sA = tc::smem_u32(r2);
+            G.gB = A.BliftE;
+            G.brows = d.NCE;
+            G.nk = d.NT / 8;
+            G.acc_first = 1;
+            add_mmas(G, 0, d.NCE, 0);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        // update: E += dt/eps G^{-1} r, r = s_T D_c
+        {
+            const double* gg = A.geo + t * kGeoStride;
+            const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
+                        gi4 = (float)gg[4], gi5 = (float)gg[5];
+            const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+            const double eps = gg[kGeoEps];
+            const float sT = (float)gg[kGeoSign];
+            const float s = (float)(dt * gg[kGeoInvEps]);
+            float* Et = A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4;
+            const int ngroups = (d.NE + 3) / 4;
+            for (int grp = 0; grp < ngroups; ++grp) {
+                float dd[12];
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp), dd[0], dd[1], dd[2], dd[3]);
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 4), dd[4], dd[5], dd[6], dd[7]);
+                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 8), dd[8], dd[9], dd[10], dd[11]);
+                float ev[12];
+                float4* ep[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    ep[q] = reinterpret_cast<float4*>(Et + ((size_t)(3 * grp + q) * kTcRows + tid) * 4);
+                    const float4 e = *ep[q];
+                    ev[4 * q] = e.x;
+                    ev[4 * q + 1] = e.y;
+                    ev[4 * q + 2] = e.z;
+                    ev[4 * q + 3] = e.w;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (4 * grp + c >= d.NE) break;
+                    const float r0 = sT * dd[3 * c], r1 = sT * dd[3 * c + 1], r2v = sT * dd[3 * c + 2];
+                    const float e0 = ev[3 * c] + s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
+                    const float e1 = ev[3 * c + 1] + s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
+                    const float e2 = ev[3 * c + 2] + s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
+                    if (energy) {
+                        const double x0 = e0, x1 = e1, x2 = e2;
+                        eacc += 0.5 * eps *
+                                (x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
+                                 x2 * (G2 * x0 + G4 * x1 + G5 * x2));
+                    }
+                    ev[3 * c] = e0;
+                    ev[3 * c + 1] = e1;
+                    ev[3 * c + 2] = e2;
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float4 e = make_float4(ev[4 * q], ev[4 * q + 1], ev[4 * q + 2], ev[4 * q + 3]);
+                    *ep[q] = e;
+                    *reinterpret_cast<float4*>(r2 + ((size_t)(3 * grp + q) * kTcRows + tid) * 4) = e;
+                }
+            }
+            for (int kc = 3 * ngroups; kc < d.KE / 4; ++kc)
+                *reinterpret_cast<float4*>(r2 + ((size_t)kc * kTcRows + tid) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        epilogue_barrier();
+        if (tid == 0) {
+            GemmDesc G{};
+            G.sA = tc::smem_u32(r2);
+            G.gB = A.BtrE;
+            G.brows = d.NT;
+            G.nk = d.KE / 8;
+            add_mmas(G, 0, d.NT, (uint32_t)d.NCE);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        epi_traces(A, lane_tmem, d.NCE, A.trE, t);
+        epilogue_barrier();
+    }
+    if (ctl->abort && tid == 0) record_error(A.err);
+    if (energy) block_sum_store(eacc, A.partE);
+    teardown(ctl, warp);
+}
+
+// traces of E (which = 0, with the energy partials of E) or H (which = 1)
+__global__ void __launch_bounds__(128, 1) k_tc_traces(TCArgs A, int which) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem);
+    uint8_t* ring = smem + kHead;
+    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const TCDims d = A.d;
+    setup(ctl, warp);
+    const uint32_t tmem = ctl->tmem;
+    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t g = 0, done_cnt = 0, load_cnt = 0;
+    const int K = which == 0 ? d.KE : d.KH;
+    const float* field = which == 0 ? A.E : A.H;
+    double eacc = 0.0;
+    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        const int64_t t = (int64_t)tile * kTcRows + tid;
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(kTcRows * K * 4);
+            tc::mbar_expect_tx(&ctl->load, bytes);
+            tc::bulk_g2s(r2, field + (size_t)tile * (K / 4) * kTcRows * 4, bytes, &ctl->load);
+        }
+        if (!tc::mbar_wait(&ctl->load, load_cnt & 1u, kLimit)) ctl->abort = 1;
+        ++load_cnt;
+        __syncthreads();
+        if (ctl->abort) break;
+        if (which == 0) {
+            const double* gg = A.geo + t * kGeoStride;
+            const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+            for (int a = 0; a < d.NE; ++a) {
+                double x[3];
+                for (int m = 0; m < 3; ++m) {
+                    const int k = 3 * a + m;
+                    x[m] = r2[((size_t)(k >> 2) * kTcRows + tid) * 4 + (k & 3)];
+                }
+                eacc += 0.5 * gg[kGeoEps] *
+                        (x[0] * (G0 * x[0] + G1 * x[1] + G2 * x[2]) + x[1] * (G1 * x[0] + G3 * x[1] + G4 * x[2]) +
+                         x[2] * (G2 * x[0] + G4 * x[1] + G5 * x[2]));
+            }
+        }
+        if (tid == 0) {
+            GemmDesc G{};
+            G.sA = tc::smem_u32(r2);
+            G.gB = which == 0 ? A.BtrE : A.BtrH;
+            G.brows = d.NT;
+            G.nk = K / 8;
+            add_mmas(G, 0, d.NT, 0);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        }
+        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+        __syncthreads();
+        if (ctl->abort) break;
+        epi_traces(A, lane_tmem, 0, which == 0 ? A.trE : A.trH, t);
+        tc::tc_fence_before();
+        __syncthreads();   // r2 is overwritten by the next tile's load
+    }
+    if (ctl->abort && tid == 0) record_error(A.err);
+    if (which == 0) block_sum_store(eacc, A.partE);
+    teardown(ctl, warp);
+}
+
+// 1/2 (eps E, E) and 1/2 (mu H, H) partials of the tiled state
+__global__ void k_tc_state_energy(TCArgs A) {
+    const TCDims d = A.d;
+    double eE = 0.0, eH = 0.0;
+    const int64_t n = (int64_t)A.ntiles * kTcRows;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double* gg = A.geo + t * kGeoStride;
+        const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+        const int64_t tile = t / kTcRows, e = t % kTcRows;
+        for (int which = 0; which < 2; ++which) {
+            const int N = which == 0 ? d.NE : d.NH, K = which == 0 ? d.KE : d.KH;
+            const float* base = (which == 0 ? A.E : A.H) + (size_t)tile * (K / 4) * kTcRows * 4;
+            const double c = which == 0 ? gg[kGeoEps] : gg[kGeoMu];
+            double acc = 0.0;
+            for (int a = 0; a < N; ++a) {
+                double x[3];
+                for (int m = 0; m < 3; ++m) {
+                    const int k = 3 * a + m;
+                    x[m] = base[((size_t)(k >> 2) * kTcRows + e) * 4 + (k & 3)];
+                }
+                acc += x[0] * (G0 * x[0] + G1 * x[1] + G2 * x[2]) + x[1] * (G1 * x[0] + G3 * x[1] + G4 * x[2]) +
+                       x[2] * (G2 * x[0] + G4 * x[1] + G5 * x[2]);
+            }
+            (which == 0 ? eE : eH) += 0.5 * c * acc;
+        }
+    }
+    __shared__ double red[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        eE += __shfl_down_sync(0xffffffffu, eE, o);
+        eH += __shfl_down_sync(0xffffffffu, eH, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = eE;
+        red[1][threadIdx.x >> 5] = eH;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        A.partE[blockIdx.x] = a;
+        A.partH[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_tc_pack(const double* __restrict__ src, float* __restrict__ dst, const double* __restrict__ nrm,
+                          int64_t nt, int N, int K) {
+    const int64_t n = nt * 3 * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / (3 * N);
+        const int rem = (int)(i - t * 3 * N);
+        const int m = rem / N, a = rem - m * N;
+        const int k = 3 * a + m;
+        const double sc = nrm ? nrm[a] : 1.0;
+        dst[(((t / kTcRows) * (K / 4) + (k >> 2)) * kTcRows + (t % kTcRows)) * 4 + (k & 3)] = (float)(src[i] * sc);
+    }
+}
+
+__global__ void k_tc_unpack(const float* __restrict__ src, double* __restrict__ dst, const double* __restrict__ nrm,
+                            int64_t nt, int N, int K) {
+    const int64_t n = nt * 3 * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / (3 * N);
+        const int rem = (int)(i - t * 3 * N);
+        const int m = rem / N, a = rem - m * N;
+        const int k = 3 * a + m;
+        const double sc = nrm ? nrm[a] : 1.0;
+        dst[i] = (double)src[(((t / kTcRows) * (K / 4) + (k >> 2)) * kTcRows + (t % kTcRows)) * 4 + (k & 3)] / sc;
+    }
+}
+
+int set_smem(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess ? 0 : -1;
+}
+
+size_t smem_of(const TCArgs& a) {
+    uint32_t sb, r2;
+    return tc_smem_bytes(a.d, &sb, &r2);
+}
+
+}  // namespace
+
+TCDims tc_dims(int NE, int NH, int N2H) {
+    TCDims d;
+    d.NE = NE;
+    d.NH = NH;
+    d.N2H = N2H;
+    d.KE = padto(3 * NE, 24);
+    d.KH = padto(3 * NH, 24);
+    d.NT = padto(8 * N2H, 16);
+    d.NC = padto(12 * ((NH + 3) / 4), 16);
+    d.NCE = padto(12 * ((NE + 3) / 4), 16);
+    return d;
+}
+
+size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset) {
+    const int maxB = std::max(d.NC + d.NT, d.NCE + d.NT);
+    const uint32_t stage = (uint32_t)(kTcRows + maxB) * 32u;
+    const int maxK = std::max(std::max(d.KE, d.KH), d.NT);
+    const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)maxK * 4u;
+    *stage_bytes = stage;
+    *r2_offset = kHead + kStages * stage;
+    // at least 116 KB so that one CTA (and its 512 TMEM columns) occupies an SM
+    return std::max<size_t>((size_t)kHead + kStages * stage + r2, 116 * 1024);
+}
+
+int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
+    const size_t sm = smem_of(a);
+    if (set_smem((const void*)k_tc_phase_H, sm)) return -1;
+    k_tc_phase_H<<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s) {
+    const size_t sm = smem_of(a);
+    if (set_smem((const void*)k_tc_phase_E, sm)) return -1;
+    k_tc_phase_E<<<grid, 128, sm, s>>>(a, dt, energy);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
+    const size_t sm = smem_of(a);
+    if (set_smem((const void*)k_tc_traces, sm)) return -1;
+    k_tc_traces<<<grid, 128, sm, s>>>(a, which);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s) {
+    k_tc_state_energy<<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s) {
+    const int64_t n = nt * 3 * N;
+    if (n == 0) return 0;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
+    k_tc_pack<<<(int)blocks, 256, 0, s>>>(src, dst, nrm, nt, N, K);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s) {
+    const int64_t n = nt * 3 * N;
+    if (n == 0) return 0;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
+    k_tc_unpack<<<(int)blocks, 256, 0, s>>>(src, dst, nrm, nt, N, K);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace dgm

@@ -1,0 +1,60 @@
+// Tensor-core (tcgen05, TF32 operands, FP32 accumulation) phase kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dgm {
+
+constexpr int kTcRows = 128;   // elements per tile = MMA M
+
+// Dimensions of the tensor-core path for one p (all counts in fp32 values).
+struct TCDims {
+    int NE, NH, N2H;
+    int KE, KH;      // padded state row lengths (multiples of 24): E, H
+    int NT;          // face-trace columns 8 N2H padded to 16
+    int NC;          // H-output columns (12 ceil(NH/4) padded to 16)
+    int NCE;         // E-output columns (12 ceil(NE/4) padded to 16)
+};
+
+TCDims tc_dims(int NE, int NH, int N2H);
+
+struct TCArgs {
+    int64_t nt;
+    int ntiles;
+    TCDims d;
+    float* E;                  // [ntiles][KE/4][128][4]
+    float* H;                  // [ntiles][KH/4][128][4]
+    float* trE;                // [ntiles*128][NT] tangential E traces (degree <= p-1 face modes)
+    float* trH;                // [ntiles*128][NT]
+    const double* geo;         // [ntiles*128][kGeoStride] (padding rows benign)
+    const int32_t* nbr;        // [ntiles*128][4]
+    const float* B1H;          // [KE/4][NC+NT][4]   curl | E trace
+    const float* BliftH;       // [NT/4][NC][4]
+    const float* BtrH;         // [KH/4][NT][4]
+    const float* B1E;          // [KH/4][NCE+NT][4]  curl^T | H trace
+    const float* BliftE;       // [NT/4][NCE][4]
+    const float* BtrE;         // [KE/4][NT][4]
+    double* partE;             // [grid] energy partials, E part
+    double* partH;             // [grid] energy partials, H part
+    int* err;                  // device error word (0 = ok)
+    float sigma_hat[4];        // reference face orientation signs
+    uint32_t stage_bytes;      // bytes of one ring stage
+    uint32_t r2_offset;        // offset of the resident tile region
+};
+
+size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset);
+
+int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s);
+int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s);
+// traces (and, for E, the energy partials of E) of the current field: which = 0 E, 1 H
+int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s);
+// energy partials of the state (no staggering)
+int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s);
+// canonical (or orthonormal) [t][3][N] doubles <-> tiled floats, scaled by nrm[a] (import) / 1/nrm[a] (export)
+int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s);
+int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s);
+
+}  // namespace dgm

@@ -36,9 +36,9 @@ def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def _solver(capi, m, p, eps, mu=1.0, precision="fp64"):
+def _solver(capi, m, p, eps, mu=1.0, precision="fp64", flux="central"):
     from paper_1104_4208_gb300.solver import Solver
-    return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=precision)
+    return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=precision, flux=flux)
 
 
 def _cases():
@@ -241,4 +241,61 @@ def test_invalid_arguments(capi):
         S.kick(0, float("nan"))
     with pytest.raises(capi.DgmError):
         S.set_fields(np.zeros(S.nE), np.zeros(S.nH), np.zeros(4))
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,p", [("jitter_n2", 2), ("jitter_n2", 3), ("periodic_n3", 2), ("jitter_n1", 6)])
+def test_stabilized_kick_parity(capi, name, p, precision):
+    """Stabilized central flux (Sec. 2.1): H-kick advances H and H^F from E; E-kick
+    includes the (H^F x nu_F, [[e]]) term; vs the oracle's assembled blocks."""
+    from oracle.dg import OracleDG
+    m = _mesh(name)
+    rng = np.random.default_rng(200 + p)
+    eps = rng.uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0, vertex_key=m.vertex_key, flux="stabilized")
+    A = dg.assemble()
+    S = _solver(capi, m, p, eps, 1.0, precision, flux="stabilized")
+    assert S.nHF == dg.sizeK
+    E0 = rng.standard_normal(S.nE)
+    H0 = rng.standard_normal(S.nH)
+    K0 = rng.standard_normal(S.nHF)
+    dt = 0.02
+    S.set_fields(E0, H0, K0)
+    S.kick(0, dt)
+    _, H, K = S.get_fields()
+    assert _rel(H - H0, dt * dg._blockmul(A["MHinv"], A["CH"] @ E0)) < TOL[precision]
+    assert _rel(K - K0, dt * dg._blockmul(A["MFinv"], A["S"] @ E0)) < TOL[precision]
+    S.set_fields(E0, H0, K0)
+    S.kick(1, dt)
+    E, _, K = S.get_fields()
+    dE = dt * dg._blockmul(A["MEinv"], A["CE"] @ H0 + A["CEK"] @ K0)
+    assert _rel(E - E0, dE) < TOL[precision]
+    assert _rel(K, K0) < (1e-15 if precision == "fp64" else 1e-7)   # E-kick leaves H^F unchanged
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_stabilized_trajectory_and_energy(capi, precision):
+    """Leapfrog with the stabilized flux on a jittered PEC cube (n=3, p=3, eps~U[1,4]):
+    fields, H^F and the modified energy (with its face term) vs the oracle."""
+    from oracle.dg import OracleDG
+    m = kuhn_cube_mesh(3, jitter=0.1, seed=31, shuffle_local=True)
+    rng = np.random.default_rng(32)
+    eps = rng.uniform(1, 4, m.nt)
+    p = 3
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0, flux="stabilized")
+    E0 = rng.standard_normal(dg.sizeE)
+    H0 = rng.standard_normal(dg.sizeH)
+    dt = 0.1 * (1 / 3) / p ** 2
+    Eo, Ho, Ko, Wo = dg.run(E0, H0, dt, 30)
+    S = _solver(capi, m, p, eps, 1.0, precision, flux="stabilized")
+    S.set_fields(E0, H0, np.zeros(S.nHF))
+    W = S.run(dt, 30, energies=True)
+    E, H, K = S.get_fields()
+    assert _rel(E, Eo) < TOL_TRAJ[precision]
+    assert _rel(H, Ho) < TOL_TRAJ[precision]
+    assert _rel(K, Ko) < TOL_TRAJ[precision]
+    assert np.abs(W - Wo).max() / Wo[0] < TOL_TRAJ[precision]
+    assert np.abs(W - W[0]).max() / W[0] < (1e-11 if precision == "fp64" else 1e-5)
     S.close()
