@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="planewave_n32_p6")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=4, help="steps of the FP64 comparison run (0: skip)")
+    ap.add_argument("--precision", default="tc32", choices=["tc32", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="nonzero: also run the FP64 path over the same steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -175,9 +175,11 @@ def project_initial(S, w, torch, q1d):
     return maps, xh
 
 
-def l2_rel_error(S, w, torch, q1d, maps, xh, T):
+def l2_rel_error(S, w, torch, q1d, maps, xh, T, keep=None):
+    """Relative L2 error of E against the analytic field at time T (None for the
+    pulse, which has no closed form); keep: list receiving (values, weights)."""
     from paper_1104_4208_gb300 import _capi as capi
-    if w.init not in ("plane", "te110"):
+    if w.init not in ("plane", "te110") and keep is None:
         return None
     _, wq = capi.dgm_quad_rule(q1d)
     Ed = torch.empty((S.nt, xh.shape[0], 3), dtype=torch.float64, device="cuda")
@@ -188,6 +190,10 @@ def l2_rel_error(S, w, torch, q1d, maps, xh, T):
     torch.cuda.empty_cache()
     F = maps[:, 3:].reshape(-1, 3, 3)
     det = np.abs(np.linalg.det(F))
+    if keep is not None:
+        keep.append((Eh_all, det[:, None] * wq[None, :]))
+    if w.init not in ("plane", "te110"):
+        return None
     fn = analytic(w)
     err2 = ref2 = 0.0
     chunk = 16384
@@ -295,13 +301,14 @@ def run_gpu(args, rank, world, local):
         ms, stats, W = timed_run(S, torch, dt, args.steps, args.warmup)
     clocks = clk.summary()
     T = (args.warmup + args.steps) * dt
-    err = l2_rel_error(S, w, torch, q1d, maps, xh, T)
+    kept = []
+    err = l2_rel_error(S, w, torch, q1d, maps, xh, T, keep=kept if args.fp64_steps else None)
     drift = float(np.abs(W - W[0]).max() / W[0])
     ms_max = dist_max(ms)
     value = world * dofs * args.steps / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
-    b = 4 if args.precision == "fp32" else 8
+    b = 8 if args.precision == "fp64" else 4
     NE, NH = n3(w.p), n3(w.p - 1)
     # algorithmic bytes per element and phase (g = 64 B geometry, c = 20 B topology):
     # H-phase reads E, H and writes H; E-phase reads H, E and writes E
@@ -309,29 +316,37 @@ def run_gpu(args, rank, world, local):
     bytes_E = w.nt * (b * (6 * NE + 3 * NH) + 64 + 20)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
+    kpre = "k_tc_phase" if args.precision == "tc32" else "k_phase"
     if stats.h_phase_ms >= stats.e_phase_ms:
-        kname, kbytes, kms = "k_phase_H", bytes_H, tH
+        kname, kbytes, kms = kpre + "_H", bytes_H, tH
     else:
-        kname, kbytes, kms = "k_phase_E", bytes_E, tE
+        kname, kbytes, kms = kpre + "_E", bytes_E, tE
     peak, peak_src = measured_peak_hbm()
     achieved = kbytes / (kms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
-            "traffic": profile_traffic(f"{kname}<{'float' if b == 4 else 'double'}>"),
+            "traffic": profile_traffic(kname if args.precision == "tc32" else f"{kname}<{'float' if b == 4 else 'double'}>"),
             "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
-            "share": {"k_phase_H": stats.h_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms),
-                      "k_phase_E": stats.e_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms)}}
+            "share": {kpre + "_H": stats.h_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms),
+                      kpre + "_E": stats.e_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms)}}
 
-    # FP64 plain path on the same workload, same initial data
+    # FP64 plain path on the same workload, same initial data, same number of
+    # steps: its throughput, and the mixed path's deviation from it at equal time
     fp64 = None
     if args.fp64_steps > 0 and args.precision != "fp64":
         S.close()
         S64 = make_solver(w, "fp64")
         project_initial(S64, w, torch, q1d)
-        ms64, st64, W64 = timed_run(S64, torch, dt, args.fp64_steps, 1)
-        v64 = world * dofs * args.fp64_steps / (dist_max(ms64) * 1e-3)
-        fp64 = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "speedup_of_mixed": value / v64,
-                "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0])}
+        ms64, st64, W64 = timed_run(S64, torch, dt, args.steps, args.warmup)
+        v64 = world * dofs * args.steps / (dist_max(ms64) * 1e-3)
+        kept64 = []
+        err64 = l2_rel_error(S64, w, torch, q1d, maps, xh, T, keep=kept64)
+        (Em, wts), (E64, _) = kept[0], kept64[0]
+        dev = float(np.sqrt(np.einsum("tq,tqc->", wts, (Em - E64) ** 2) / np.einsum("tq,tqc->", wts, E64 ** 2)))
+        del kept, kept64, Em, E64
+        fp64 = {"value": v64, "ms_per_step": ms64 / args.steps, "speedup_of_mixed": value / v64,
+                "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0]),
+                "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev}
         S64.close()
         S = make_solver(w, args.precision)
         project_initial(S, w, torch, q1d)
@@ -372,11 +387,15 @@ def run_gpu(args, rank, world, local):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+               "dtype": {"tc32": "tf32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
                "config": {"workload": w.name, "tets": w.nt, "p": w.p, "dof": dofs, "precision": args.precision,
                           "flux": "central", "dt": dt, "parallelism": f"replicas{world}",
                           "l2": "state larger than L2 (no flush needed)",
-                          "state_mb": dofs * (4 if args.precision == 'fp32' else 8) / 1e6},
+                          "state_mb": dofs * (8 if args.precision == 'fp64' else 4) / 1e6,
+                          "arithmetic": {"tc32": "fp32 state, TF32 tensor-core operators (tcgen05), fp32 accumulate, "
+                                                 "fp64 geometry and energy",
+                                         "fp32": "fp32 state and CUDA-core arithmetic, fp64 geometry and energy",
+                                         "fp64": "fp64 throughout"}[args.precision]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks,
                "err": {"l2_rel_E_vs_analytic": err, "l2_rel_E_initial_projection": err0,

@@ -6,6 +6,12 @@ Tolerances (relative to the max-abs of the reference):
         uses FMA; observed differences are a few 1e-15).
   FP32: 2e-5 per operator application, 2e-4 on trajectories (single-precision
         state and arithmetic, FP64 tables rounded once, FP64 energy sums).
+  TC32: 3e-3 per operator application, 3e-2 on the 100-step cavity trajectory
+        (max-coefficient measure at a time where the mode's amplitude is 28% of
+        its peak), and the L2 error against the analytic mode within 2% of the
+        FP64 oracle's: the tensor cores multiply TF32 operands (10-bit mantissa:
+        state truncated, tables rounded to nearest) and accumulate in FP32.
+        First measurements: 4e-4..1.2e-3 per application, 1.3e-2 trajectory.
 """
 
 import numpy as np
@@ -17,8 +23,8 @@ from workloads.fields import te110_fields, gaussian_pulse_fields
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 2e-5}
-TOL_TRAJ = {"fp64": 1e-12, "fp32": 2e-4}
+TOL = {"fp64": 1e-12, "fp32": 2e-5, "tc32": 3e-3}
+TOL_TRAJ = {"fp64": 1e-12, "fp32": 2e-4, "tc32": 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -298,4 +304,74 @@ def test_stabilized_trajectory_and_energy(capi, precision):
     assert _rel(K, Ko) < TOL_TRAJ[precision]
     assert np.abs(W - Wo).max() / Wo[0] < TOL_TRAJ[precision]
     assert np.abs(W - W[0]).max() / W[0] < (1e-11 if precision == "fp64" else 1e-5)
+    S.close()
+
+
+def _log(name, **kw):
+    import json, os
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(d):
+        with open(os.path.join(d, "tc_errors.jsonl"), "a") as fh:
+            fh.write(json.dumps(dict(test=name, **kw)) + "\n")
+
+
+@pytest.mark.parametrize("name,p", [("jitter_n3", 1), ("jitter_n3", 2), ("jitter_n3", 3), ("jitter_n3", 4),
+                                    ("jitter_n3", 5), ("jitter_n3", 6), ("periodic_n3", 3)])
+def test_tc32_kick_parity(capi, name, p):
+    """Tensor-core path (tiles of 128 elements, 162 tets = 2 tiles with a ragged
+    tail): one H-kick and one E-kick vs the oracle at the TF32 tolerance."""
+    from oracle.dg import OracleDG
+    m = _mesh(name)
+    rng = np.random.default_rng(300 + p)
+    eps = rng.uniform(1, 4, m.nt)
+    mu = rng.uniform(1, 2, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key)
+    A = dg.assemble()
+    S = _solver(capi, m, p, eps, mu, "tc32")
+    E0 = rng.standard_normal(S.nE)
+    H0 = rng.standard_normal(S.nH)
+    dt = 0.05
+    S.set_fields(E0, H0)
+    E1, H1 = S.get_fields()
+    assert _rel(E1, E0) < 1e-6 and _rel(H1, H0) < 1e-6      # float storage round trip
+    S.kick(0, dt)
+    _, H = S.get_fields()
+    dH = dt * dg._blockmul(A["MHinv"], A["CH"] @ E0)
+    eH = _rel(H - H0, dH)
+    S.set_fields(E0, H0)
+    S.kick(1, dt)
+    E, _ = S.get_fields()
+    dE = dt * dg._blockmul(A["MEinv"], A["CE"] @ H0)
+    eE = _rel(E - E0, dE)
+    _log("tc32_kick", mesh=name, p=p, errH=eH, errE=eE)
+    assert eH < TOL["tc32"] and eE < TOL["tc32"]
+    S.close()
+
+
+def test_tc32_cavity_trajectory(capi):
+    """cavity_n4_p3 (384 tets = 3 tiles) with the tensor-core path: fields and
+    energies vs the oracle, energy drift, error vs the analytic TE110 mode."""
+    from oracle.dg import OracleDG
+    from oracle.project import project, l2_error
+    w = make_workload("cavity_n4_p3")
+    m = w.mesh
+    dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu)
+    E0 = project(dg, lambda x: te110_fields(x, 0.0)[0], w.p)
+    H0 = project(dg, lambda x: te110_fields(x, 0.0)[1], w.p - 1)
+    Eo, Ho, _, Wo = dg.run(E0, H0, w.dt, w.steps)
+    S = _solver(capi, m, w.p, w.eps, w.mu, "tc32")
+    S.set_fields(E0, H0)
+    W = S.run(w.dt, w.steps, energies=True)
+    E, H = S.get_fields()
+    T = w.steps * w.dt
+    e, r = l2_error(dg, E, lambda x: te110_fields(x, T)[0], w.p)
+    eo, _ = l2_error(dg, Eo, lambda x: te110_fields(x, T)[0], w.p)
+    drift = float(np.abs(W - W[0]).max() / W[0])
+    _log("tc32_cavity", errE=_rel(E, Eo), errH=_rel(H, Ho), errW=float(np.abs(W - Wo).max() / Wo[0]),
+         drift=drift, l2=e / r, l2_oracle=eo / r)
+    assert _rel(E, Eo) < TOL_TRAJ["tc32"]
+    assert _rel(H, Ho) < TOL_TRAJ["tc32"]
+    assert np.abs(W - Wo).max() / Wo[0] < 1e-3
+    assert drift < 1e-3
+    assert abs(e - eo) < 0.02 * eo
     S.close()
