@@ -151,6 +151,54 @@ int dgm_kick(dgm_problem* prob, int which, double dt, void* stream);
  * Blocks until the energies are on the host when energy_out != NULL. */
 int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* energy_out);
 
+/* Stability bound of the explicit scheme (Sec. 3): dt <= 2 / sqrt(rho) with rho
+ * the spectral radius of M_mu^{-1} C_h M_eps^{-1} C_h^T (face unknowns included
+ * for the stabilized flux), estimated by `iters` power iterations (Sec. 3:
+ * "estimated once by an iterative method like the power iteration") that apply
+ * the library's own E- and H-kicks.  The printed bound 2 rho^{-1} is read as
+ * 2 rho^{-1/2} (dimensionally a time).  The state is saved and restored; the
+ * start vector is a fixed pseudo-random H.  Blocks; allocates temporaries. */
+int dgm_estimate_dt(dgm_problem* prob, int iters, double* rho, double* dt_max);
+
+/* Point dipole current J(x, t) = dir delta(x - xs) f(t) with the zero-mean
+ * pulse f(t) = -amp ((t - t0)/tau) exp(-((t - t0)/tau)^2): the E-equation of
+ * Sec. 2 gains -(J, e), applied in every E-kick of dgm_run (and of the forward
+ * runs of dgm_adjoint_grad) at the kick's midpoint time.  One source per
+ * problem; amp = 0 removes it; dgm_kick applies no source.  xs must lie in the
+ * mesh (DGM_ERR_INVALID_ARG otherwise). */
+int dgm_set_source(dgm_problem* prob, const double* xs, const double* dir, double t0, double tau, double amp);
+/* Time of the state: set by the caller, advanced by nsteps*dt in dgm_run. */
+int dgm_set_time(dgm_problem* prob, double t);
+int dgm_get_time(const dgm_problem* prob, double* t);
+
+/* Replace the per-element eps and mu (> 0) of an existing problem; the fields
+ * are kept.  Mass blocks of Sec. 3.3.1 scale with eps, mu. */
+int dgm_set_materials(dgm_problem* prob, const double* eps, const double* mu);
+
+/* Gradient of a field observable with respect to the per-element permittivity
+ * by the discrete adjoint of the leapfrog (Sec. 3; central flux):
+ *   J = sum_{n=1..nsteps} sum_o |E^n(x_o)|^2,  x_o = xobs[o][0..2],
+ * E^n the fields of dgm_run started from the current state.  The adjoint runs
+ * the same E- and H-kicks backward in time (negative step) with point sources
+ * 2 P^T P E^n; E^n is recomputed segment by segment from checkpoints taken every
+ * ckpt_every steps.  dJdeps[nt] (host) receives dJ/d eps_T, J_out (host) J.
+ * The state is restored.  Points must lie in the mesh.  Blocks; allocates. */
+int dgm_adjoint_grad(dgm_problem* prob, double dt, int64_t nsteps, int nobs, const double* xobs,
+                     int ckpt_every, double* J_out, double* dJdeps);
+
+/* Batches: many independent problems on one device advanced together.  The
+ * whole time loop of every run is captured once into a CUDA graph -- a fork,
+ * one branch (stream) per run with all its phase kernels, a join -- so small
+ * runs execute concurrently and the launch cost is paid once per call; the
+ * graph is replayed while (nsteps, dt[], energy request, stream) stay the same.
+ * dgm_batch_run: dt[nruns]; energy_out (nullable, host) [nruns][nsteps+1] as in
+ * dgm_run.  Problems keep their own state, source and time; a problem must not
+ * be used outside the batch while a batched run is in flight. */
+typedef struct dgm_batch dgm_batch;
+int dgm_batch_create(dgm_ctx* ctx, dgm_problem** probs, int nruns, dgm_batch** out);
+int dgm_batch_destroy(dgm_batch* batch);
+int dgm_batch_run(dgm_batch* batch, const double* dt, int64_t nsteps, void* stream, double* energy_out);
+
 /* Per-kernel timing of one dgm_run_timed call: CUDA events recorded on the
  * launching stream around every phase kernel (summed, milliseconds) and the
  * number of kernels the call launched. */

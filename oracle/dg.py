@@ -404,3 +404,100 @@ class OracleDG:
         L = np.linalg.cholesky(M)
         y = np.linalg.solve(L, r[..., None])
         return dt * np.linalg.solve(np.swapaxes(L, 1, 2), y)[..., 0]
+
+
+# ------------------------------------------------------------ observations
+def locate_points(dg, pts):
+    """Element containing each physical point (brute force over barycentric
+    coordinates) and the point's reference coordinates in that element."""
+    g = dg.geo
+    out_t, out_xh = [], []
+    for x in np.asarray(pts, dtype=float):
+        xh = np.einsum("tij,tj->ti", g.Finv, x[None, :] - g.X0)
+        bary = np.concatenate([1 - xh.sum(1, keepdims=True), xh], axis=1)
+        t = int(np.argmax(bary.min(1)))
+        if bary[t].min() < -1e-12:
+            raise ValueError("point outside the mesh")
+        out_t.append(t)
+        out_xh.append(xh[t])
+    return np.array(out_t), np.array(out_xh)
+
+
+def observation_matrix(dg, pts):
+    """Sparse P (3 nobs x sizeE): rows = physical E components at the points."""
+    ts, xhs = locate_points(dg, pts)
+    vals, _ = phi3(dg.p, xhs)                        # (NE, nobs)
+    rows, cols, data = [], [], []
+    for o, (t, xh) in enumerate(zip(ts, xhs)):
+        Finv = dg.geo.Finv[t]
+        # E(x) = F^{-T} sum_a c[:, a] phi_a  ->  E_c = sum_{m,a} Finv[m, c] phi_a c[m, a]
+        for c in range(3):
+            for mm in range(3):
+                for a in range(dg.NE):
+                    rows.append(3 * o + c)
+                    cols.append((t * 3 + mm) * dg.NE + a)
+                    data.append(Finv[mm, c] * vals[a, o])
+    return sps.csr_matrix((data, (rows, cols)), shape=(3 * len(ts), dg.sizeE))
+
+
+def adjoint_grad_eps(dg, E0, H0, dt, nsteps, pts):
+    """J = sum_{n=1..N} sum_o |E^n(x_o)|^2 for the leapfrog of OracleDG.run (central
+    flux) and dJ/d eps_T by the discrete adjoint:
+      e^m = 2 P^T P E^m + dt A^T g^m + e^{m+1},   g^{m-1} = g^m - dt B^T e^m,
+      dJ/d eps_T = -(1/eps_T) sum_m e^m_T . (E^m - E^{m-1})_T,
+    with A = M_mu^{-1} C_H (H-kick), B = -M_eps^{-1} C_E (E-kick), e^{N+1} = 0, g^N = 0."""
+    A_ = dg.assemble()
+    P = observation_matrix(dg, pts)
+    PtP = (P.T @ P).tocsr()
+    E = np.array(E0, dtype=float)
+    H = np.array(H0, dtype=float)
+    G = H + 0.5 * dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
+    Es = [E.copy()]
+    J = 0.0
+    for n in range(nsteps):
+        E = E + dt * dg._blockmul(A_["MEinv"], A_["CE"] @ G)
+        Es.append(E.copy())
+        J += float(E @ (PtP @ E))
+        G = G + dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
+    # transposes of A = MHinv CH and B = -MEinv CE  (block inverses are symmetric)
+    e_next = np.zeros(dg.sizeE)
+    g = np.zeros(dg.sizeH)
+    grad = np.zeros(dg.nt)
+    for m in range(nsteps, 0, -1):
+        e = 2 * (PtP @ Es[m]) + dt * (A_["CH"].T @ dg._blockmul(A_["MHinv"], g)) + e_next
+        dE = (Es[m] - Es[m - 1]).reshape(dg.nt, -1)
+        grad -= np.einsum("ti,ti->t", e.reshape(dg.nt, -1), dE) / dg.eps
+        g = g + dt * (A_["CE"].T @ dg._blockmul(A_["MEinv"], e))
+        e_next = e
+    return J, grad
+
+
+def objective(dg, E0, H0, dt, nsteps, pts):
+    """J of adjoint_grad_eps by a plain forward run (for finite differences)."""
+    A_ = dg.assemble()
+    P = observation_matrix(dg, pts)
+    E = np.array(E0, dtype=float)
+    G = np.array(H0, dtype=float) + 0.5 * dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
+    J = 0.0
+    for n in range(nsteps):
+        E = E + dt * dg._blockmul(A_["MEinv"], A_["CE"] @ G)
+        v = P @ E
+        J += float(v @ v)
+        G = G + dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
+    return J
+
+
+def dipole_source_vector(dg, xs, direction, fval):
+    """r_E contribution -(J, e) of a point current J = direction delta(x - xs) f:
+    entries -f direction . N_{a,m}(xs) on the element containing xs."""
+    ts, xhs = locate_points(dg, [xs])
+    t, xh = ts[0], xhs[0]
+    vals, _ = phi3(dg.p, xh[None, :])
+    Finv = dg.geo.Finv[t]
+    out = np.zeros(dg.sizeE)
+    d = np.asarray(direction, dtype=float)
+    for mm in range(3):
+        # N_{a,m}(x) = F^{-T} e_m phi_a  ->  d . N = (Finv d)_m phi_a
+        coef = Finv[mm] @ d
+        out[(t * 3 + mm) * dg.NE:(t * 3 + mm + 1) * dg.NE] = -fval * coef * vals[:, 0]
+    return out

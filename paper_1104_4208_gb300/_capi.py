@@ -69,9 +69,18 @@ _SIGS = {
     "dgm_run": ([_vp, C.c_double, _i64, _vp, _pd], C.c_int),
     "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
     "dgm_energy": ([_vp, _pd], C.c_int),
+    "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
+    "dgm_set_materials": ([_vp, _pd, _pd], C.c_int),
+    "dgm_set_source": ([_vp, _pd, _pd, C.c_double, C.c_double, C.c_double], C.c_int),
+    "dgm_set_time": ([_vp, C.c_double], C.c_int),
+    "dgm_get_time": ([_vp, _pd], C.c_int),
+    "dgm_adjoint_grad": ([_vp, C.c_double, _i64, C.c_int, _pd, C.c_int, _pd, _pd], C.c_int),
     "dgm_energy_noalloc": ([_vp, _vp, _vp], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
+    "dgm_batch_create": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)], C.c_int),
+    "dgm_batch_destroy": ([_vp], C.c_int),
+    "dgm_batch_run": ([_vp, _pd, _i64, _vp, _pd], C.c_int),
     "dgm_element_maps": ([_vp, _pd], C.c_int),
     "dgm_project_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
     "dgm_eval_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
@@ -194,6 +203,43 @@ def dgm_run_timed(prob, dt, nsteps, stream=None, energy_out=None):
     return st
 
 
+def dgm_estimate_dt(prob, iters=50):
+    rho, dt = C.c_double(), C.c_double()
+    _check(_lib.dgm_estimate_dt(prob, int(iters), C.byref(rho), C.byref(dt)))
+    return rho.value, dt.value
+
+
+def dgm_set_source(prob, xs, direction, t0, tau, amp):
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    _check(_lib.dgm_set_source(prob, _dptr(xs), _dptr(d), float(t0), float(tau), float(amp)))
+
+
+def dgm_set_time(prob, t):
+    _check(_lib.dgm_set_time(prob, float(t)))
+
+
+def dgm_get_time(prob):
+    t = C.c_double()
+    _check(_lib.dgm_get_time(prob, C.byref(t)))
+    return t.value
+
+
+def dgm_set_materials(prob, eps, mu):
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    _check(_lib.dgm_set_materials(prob, _dptr(eps), _dptr(mu)))
+
+
+def dgm_adjoint_grad(prob, dt, nsteps, xobs, ckpt_every, nt):
+    xobs = np.ascontiguousarray(xobs, dtype=np.float64).reshape(-1, 3)
+    J = C.c_double()
+    g = np.empty(nt)
+    _check(_lib.dgm_adjoint_grad(prob, float(dt), int(nsteps), xobs.shape[0], _dptr(xobs), int(ckpt_every),
+                                 C.byref(J), _dptr(g)))
+    return J.value, g
+
+
 def dgm_energy(prob):
     w = C.c_double()
     _check(_lib.dgm_energy(prob, C.byref(w)))
@@ -233,3 +279,19 @@ def dgm_project_device(prob, q1d, E_ptr, H_ptr, stream=None):
 
 def dgm_eval_device(prob, q1d, E_ptr, H_ptr, stream=None):
     _check(_lib.dgm_eval_device(prob, int(q1d), E_ptr, H_ptr, stream))
+
+
+def dgm_batch_create(ctx, probs):
+    arr = (_vp * len(probs))(*[p.value if isinstance(p, _vp) else p for p in probs])
+    h = _vp()
+    _check(_lib.dgm_batch_create(ctx, arr, len(probs), C.byref(h)))
+    return h
+
+
+def dgm_batch_destroy(batch):
+    _check(_lib.dgm_batch_destroy(batch))
+
+
+def dgm_batch_run(batch, dts, nsteps, stream=None, energy_out=None):
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    _check(_lib.dgm_batch_run(batch, _dptr(dts), int(nsteps), stream, _dptr(energy_out)))

@@ -12,6 +12,7 @@
 #include "dgm_internal.h"
 #include "kernels.h"
 #include "problem.h"
+#include "adjoint.h"
 
 namespace dgm {
 
@@ -29,6 +30,10 @@ int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? DGM_ERR_OOM : DGM_ERR_CUDA;
 }
+
+int prepare_source(dgm_problem* P, double t0, double dt, int64_t nsteps);
+int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s);
+void* current_E(dgm_problem* P);
 
 #define DGM_CUDA(call)                                   \
     do {                                                 \
@@ -189,7 +194,7 @@ int export_fields(dgm_problem* P, double* dEdst, double* dHdst, cudaStream_t s) 
 void free_problem(dgm_problem* P) {
     void* ptrs[] = {P->dE, P->dH, P->dTables, P->dGeo, P->dNbr, P->dNrmE, P->dNrmH,
                     P->dPartials, P->dEnergy, P->dStage, P->dMaps, P->dWphiE, P->dWphiH, P->dPhiE, P->dPhiH,
-                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF};
+                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF, P->dSrc, P->dSrcF};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->tc) dgm::tc_problem_free(P);
@@ -459,6 +464,8 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         if ((e = cudaMalloc(&P->dMaps, maps.size() * sizeof(double))) != cudaSuccess)
             return fail(cuda_fail(e, "alloc maps"));
         cudaMemcpy(P->dMaps, maps.data(), maps.size() * sizeof(double), cudaMemcpyHostToDevice);
+        P->hmaps = maps;
+        P->hgeo = geo;
     }
     if ((e = cudaMalloc(&P->dGeo, geo.size() * sizeof(double))) != cudaSuccess) return fail(cuda_fail(e, "alloc geo"));
     if ((e = cudaMalloc(&P->dNbr, nbr.size() * sizeof(int32_t))) != cudaSuccess) return fail(cuda_fail(e, "alloc nbr"));
@@ -672,20 +679,24 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
         }
         return DGM_OK;
     };
+    int64_t step = 0;
     auto run_E = [&]() -> int {
         int r = mark(1);
         if (r) return r;
         r = phase_E(P, dt, s, want);
         if (r) return r;
+        if ((r = apply_source(P, current_E(P), step, dt, s))) return r;
         return done();
     };
-    if (P->tc && want) {
+    rc = prepare_source(P, P->time, dt, nsteps);
+    if (!rc && P->tc && want) {
         rc = mark(2);
         if (!rc) rc = dgm::tc_traces(P, 0, s);
         if (!rc) rc = done();
     }
     if (!rc) rc = run_H(0.5, 0.5, want ? W : nullptr);
     for (int64_t n = 0; n < nsteps && !rc; ++n) {
+        step = n;
         rc = run_E();
         if (rc) break;
         const bool last = n == nsteps - 1;
@@ -711,6 +722,7 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
     if (rc) return rc;
+    P->time += nsteps * dt;
     if (want) {
         for (int64_t n = 0; n <= nsteps; ++n)
             if (!std::isfinite(energy_out[n]) || energy_out[n] > 10.0 * std::fabs(energy_out[0]) + 1e-300) {
@@ -731,6 +743,621 @@ int dgm_energy(dgm_problem* P, double* W) {
     rc = P->tc ? dgm::tc_state_energy(P, P->dEnergy, 0) : phase_H(P, 0.0, 0.0, 0.0, P->dEnergy, 0);
     if (rc) return rc;
     DGM_CUDA(cudaMemcpy(W, P->dEnergy, sizeof(double), cudaMemcpyDeviceToHost));
+    return DGM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Element of the mesh containing x (largest minimum barycentric coordinate),
+// its reference coordinates and F^{-1} (row-major).  Returns the element or -1.
+int64_t locate_point(const dgm_problem* P, const double* x, double* xh_out, double* Fi_out) {
+    int64_t best = -1;
+    double bestmin = -1e300;
+    for (int64_t t = 0; t < P->nt; ++t) {
+        const double* M = &P->hmaps[12 * t];
+        const double* F = M + 3;
+        const double det = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                           F[2] * (F[3] * F[7] - F[4] * F[6]);
+        double Fi[9];
+        Fi[0] = (F[4] * F[8] - F[5] * F[7]) / det;
+        Fi[1] = (F[2] * F[7] - F[1] * F[8]) / det;
+        Fi[2] = (F[1] * F[5] - F[2] * F[4]) / det;
+        Fi[3] = (F[5] * F[6] - F[3] * F[8]) / det;
+        Fi[4] = (F[0] * F[8] - F[2] * F[6]) / det;
+        Fi[5] = (F[2] * F[3] - F[0] * F[5]) / det;
+        Fi[6] = (F[3] * F[7] - F[4] * F[6]) / det;
+        Fi[7] = (F[1] * F[6] - F[0] * F[7]) / det;
+        Fi[8] = (F[0] * F[4] - F[1] * F[3]) / det;
+        double xh[3];
+        for (int i = 0; i < 3; ++i)
+            xh[i] = Fi[3 * i] * (x[0] - M[0]) + Fi[3 * i + 1] * (x[1] - M[1]) + Fi[3 * i + 2] * (x[2] - M[2]);
+        const double mn = std::min(std::min(xh[0], xh[1]), std::min(xh[2], 1.0 - xh[0] - xh[1] - xh[2]));
+        if (mn > bestmin) {
+            bestmin = mn;
+            best = t;
+            std::memcpy(xh_out, xh, sizeof(xh));
+            std::memcpy(Fi_out, Fi, sizeof(Fi));
+        }
+    }
+    return bestmin < -1e-10 ? -1 : best;
+}
+
+double dipole_waveform(const dgm_problem* P, double t) {
+    const double s = (t - P->src_t0) / P->src_tau;
+    return -P->src_amp * s * std::exp(-s * s);
+}
+
+// f(t0 + (n + 1/2) dt), n = 0..nsteps-1, into the device array of the source
+int prepare_source(dgm_problem* P, double t0, double dt, int64_t nsteps) {
+    if (!P->src_on) return DGM_OK;
+    if (P->src_cap < nsteps) {
+        if (P->dSrcF) cudaFree(P->dSrcF);
+        P->dSrcF = nullptr;
+        P->src_cap = 0;
+        DGM_CUDA(cudaMalloc(&P->dSrcF, nsteps * sizeof(double)));
+        P->src_cap = nsteps;
+    }
+    std::vector<double> f(nsteps);
+    for (int64_t n = 0; n < nsteps; ++n) f[n] = dipole_waveform(P, t0 + (n + 0.5) * dt);
+    DGM_CUDA(cudaMemcpy(P->dSrcF, f.data(), nsteps * sizeof(double), cudaMemcpyHostToDevice));
+    return DGM_OK;
+}
+
+// E += -dt f(t_{n+1/2}) M_eps^{-1} (dir . e(x_s)) on the source element
+int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s) {
+    if (!P->src_on) return DGM_OK;
+    const int K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? 1 : 0;
+    const bool f32 = P->tc || P->fp32;
+    const int r = f32 ? dgm::add_point_source<float>((float*)E, P->NE, K, tiled, P->src_elem, P->dSrc + 3, P->dSrc,
+                                                     P->dSrcF, n, dt, s)
+                      : dgm::add_point_source<double>((double*)E, P->NE, K, tiled, P->src_elem, P->dSrc + 3, P->dSrc,
+                                                      P->dSrcF, n, dt, s);
+    if (P->tc) P->trE_valid = false;
+    return r ? cuda_fail(cudaGetLastError(), "source launch") : DGM_OK;
+}
+
+void* current_E(dgm_problem* P) {
+    if (P->tc) return P->tca.E;
+    return P->fp32 ? (void*)P->kf.E : (void*)P->kd.E;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgm_set_source(dgm_problem* P, const double* xs, const double* dir, double t0, double tau, double amp) {
+    if (!P || !xs || !dir || !(tau > 0.0) || !std::isfinite(t0) || !std::isfinite(amp)) {
+        set_error("dgm_set_source: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    if (amp == 0.0) {
+        P->src_on = false;
+        return DGM_OK;
+    }
+    double xh[3], Fi[9];
+    const int64_t t = locate_point(P, xs, xh, Fi);
+    if (t < 0) {
+        set_error("dgm_set_source: point outside the mesh");
+        return DGM_ERR_INVALID_ARG;
+    }
+    std::vector<double> phi;
+    dgm::phi_at_points(P->p, xh, 1, phi);
+    const double* g = &P->hgeo[(size_t)t * dgm::kGeoStride];
+    double w[3];
+    for (int m = 0; m < 3; ++m) w[m] = Fi[3 * m] * dir[0] + Fi[3 * m + 1] * dir[1] + Fi[3 * m + 2] * dir[2];
+    std::vector<double> rec(3 + P->NE);
+    const double ie = g[dgm::kGeoInvEps];
+    rec[0] = ie * (g[0] * w[0] + g[1] * w[1] + g[2] * w[2]);
+    rec[1] = ie * (g[1] * w[0] + g[3] * w[1] + g[4] * w[2]);
+    rec[2] = ie * (g[2] * w[0] + g[4] * w[1] + g[5] * w[2]);
+    for (int a = 0; a < P->NE; ++a) rec[3 + a] = phi[a];
+    if (!P->dSrc) DGM_CUDA(cudaMalloc(&P->dSrc, rec.size() * sizeof(double)));
+    DGM_CUDA(cudaMemcpy(P->dSrc, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice));
+    P->src_elem = t;
+    P->src_t0 = t0;
+    P->src_tau = tau;
+    P->src_amp = amp;
+    P->src_on = true;
+    return DGM_OK;
+}
+
+int dgm_set_time(dgm_problem* P, double t) {
+    if (!P || !std::isfinite(t)) {
+        set_error("dgm_set_time: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    P->time = t;
+    return DGM_OK;
+}
+
+int dgm_get_time(const dgm_problem* P, double* t) {
+    if (!P || !t) {
+        set_error("dgm_get_time: null argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    *t = P->time;
+    return DGM_OK;
+}
+
+namespace {
+
+struct StateView {
+    void* E;
+    int64_t nE;
+    void* H;
+    int64_t nH;
+    void* K;
+    int64_t nK;
+    bool f32;
+};
+
+StateView state_view(dgm_problem* P) {
+    StateView v{};
+    if (P->tc) {
+        v.E = P->tca.E;
+        v.nE = (int64_t)P->tca.ntiles * dgm::kTcRows * P->tca.d.KE;
+        v.H = P->tca.H;
+        v.nH = (int64_t)P->tca.ntiles * dgm::kTcRows * P->tca.d.KH;
+        v.f32 = true;
+    } else {
+        v.E = P->dE;
+        v.nE = P->nt * 3 * P->NE;
+        v.H = P->dH;
+        v.nH = P->nt * 3 * P->NH;
+        v.f32 = P->fp32;
+    }
+    v.K = P->dK;
+    v.nK = P->dK ? P->nfaces * 2 * P->N2E : 0;
+    return v;
+}
+
+int axpby(const StateView& v, int64_t n, double a, const void* x, double b, void* y) {
+    if (!n) return 0;
+    return v.f32 ? dgm::launch_axpby<float>(n, a, (const float*)x, b, (float*)y, 0)
+                 : dgm::launch_axpby<double>(n, a, (const double*)x, b, (double*)y, 0);
+}
+
+}  // namespace
+
+int dgm_estimate_dt(dgm_problem* P, int iters, double* rho_out, double* dt_out) {
+    if (!P || iters < 1) {
+        set_error("dgm_estimate_dt: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const StateView v = state_view(P);
+    const size_t es = v.f32 ? sizeof(float) : sizeof(double);
+    const size_t bytes = (size_t)(v.nE + 2 * v.nH + 2 * v.nK) * es;
+    void* tmp = nullptr;
+    DGM_CUDA(cudaMalloc(&tmp, bytes));
+    char* saveE = (char*)tmp;
+    char* saveH = saveE + v.nE * es;
+    char* saveK = saveH + v.nH * es;
+    char* xH = saveK + v.nK * es;
+    char* xK = xH + v.nH * es;
+    int rc = DGM_OK;
+    double rho = 0.0;
+    auto fin = [&](int code) {
+        cudaFree(tmp);
+        P->trE_valid = P->trH_valid = false;
+        return code;
+    };
+    if (cudaMemcpy(saveE, v.E, v.nE * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(saveH, v.H, v.nH * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        (v.nK && cudaMemcpy(saveK, v.K, v.nK * es, cudaMemcpyDeviceToDevice) != cudaSuccess))
+        return fin(cuda_fail(cudaGetLastError(), "dgm_estimate_dt save"));
+    // start vector: fixed pseudo-random canonical H (and H^F), through the normal import
+    {
+        const int64_t nHc = P->nt * 3 * P->NH, nKc = v.nK ? P->nfaces * 2 * P->N2E : 0;
+        std::vector<double> h(std::max(nHc, nKc));
+        uint64_t st = 0x9E3779B97F4A7C15ull;
+        auto rnd = [&]() {
+            st ^= st << 13;
+            st ^= st >> 7;
+            st ^= st << 17;
+            return (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        };
+        for (int64_t i = 0; i < nHc; ++i) h[i] = rnd();
+        if (cudaMemcpy(P->dStage, h.data(), nHc * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fin(cuda_fail(cudaGetLastError(), "dgm_estimate_dt init"));
+        if ((rc = import_fields(P, nullptr, P->dStage, 0))) return fin(rc);
+        if (v.nK) {
+            for (int64_t i = 0; i < nKc; ++i) h[i] = rnd();
+            cudaMemcpy(P->dStage, h.data(), nKc * sizeof(double), cudaMemcpyHostToDevice);
+            if ((rc = import_faces(P, P->dStage, 0))) return fin(rc);
+        }
+    }
+    double nx = 0.0;
+    cudaMemset(v.E, 0, v.nE * es);
+    P->trE_valid = P->trH_valid = false;
+    if ((rc = dgm_energy(P, &nx))) return fin(rc);
+    for (int it = 0; it < iters; ++it) {
+        // x := H (and K) / ||.||;  H <- x - dt=1 kicks (E=0) = x - B x;  y = x - H = B x
+        const double sc = 1.0 / std::sqrt(2.0 * nx);
+        if (axpby(v, v.nH, 0.0, v.H, sc, v.H) || axpby(v, v.nK, 0.0, v.K, sc, v.K))
+            return fin(cuda_fail(cudaGetLastError(), "axpby"));
+        cudaMemcpy(xH, v.H, v.nH * es, cudaMemcpyDeviceToDevice);
+        if (v.nK) cudaMemcpy(xK, v.K, v.nK * es, cudaMemcpyDeviceToDevice);
+        cudaMemset(v.E, 0, v.nE * es);
+        P->trE_valid = P->trH_valid = false;
+        if ((rc = phase_E(P, 1.0, 0)) || (rc = phase_H(P, 1.0, 0.0, 1.0, nullptr, 0))) return fin(rc);
+        if (axpby(v, v.nH, 1.0, xH, -1.0, v.H) || axpby(v, v.nK, 1.0, xK, -1.0, v.K))
+            return fin(cuda_fail(cudaGetLastError(), "axpby"));
+        cudaMemset(v.E, 0, v.nE * es);
+        P->trE_valid = P->trH_valid = false;
+        double ny = 0.0;
+        if ((rc = dgm_energy(P, &ny))) return fin(rc);
+        rho = std::sqrt(ny / 0.5);   // ||B x||_M with ||x||_M = 1
+        nx = ny;
+        if (!(nx > 0.0) || !std::isfinite(nx)) break;
+    }
+    if (cudaMemcpy(v.E, saveE, v.nE * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(v.H, saveH, v.nH * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        (v.nK && cudaMemcpy(v.K, saveK, v.nK * es, cudaMemcpyDeviceToDevice) != cudaSuccess))
+        return fin(cuda_fail(cudaGetLastError(), "dgm_estimate_dt restore"));
+    if (rho_out) *rho_out = rho;
+    if (dt_out) *dt_out = rho > 0.0 ? 2.0 / std::sqrt(rho) : INFINITY;
+    return fin(DGM_OK);
+}
+
+namespace {
+
+void set_state_ptrs(dgm_problem* P, void* E, void* H) {
+    if (P->tc) {
+        P->tca.E = (float*)E;
+        P->tca.H = (float*)H;
+    } else if (P->fp32) {
+        P->kf.E = (float*)E;
+        P->kf.H = (float*)H;
+    } else {
+        P->kd.E = (double*)E;
+        P->kd.H = (double*)H;
+    }
+    P->trE_valid = P->trH_valid = false;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const double* xobs, int ckpt_every,
+                     double* J_out, double* dJdeps) {
+    if (!P || !xobs || nobs < 1 || nobs > 1024 || nsteps < 1 || ckpt_every < 1 || !std::isfinite(dt)) {
+        set_error("dgm_adjoint_grad: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    if (P->opt.flux != DGM_FLUX_CENTRAL) {
+        set_error("dgm_adjoint_grad: central flux only");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    // observation points: containing element, reference coordinates, basis values
+    std::vector<int32_t> oe(nobs);
+    std::vector<double> oxh(3 * nobs), oFi(9 * nobs), ogi(6 * nobs);
+    for (int o = 0; o < nobs; ++o) {
+        const double* x = xobs + 3 * o;
+        int64_t best = -1;
+        double bestmin = -1e300, bxh[3] = {0, 0, 0}, bFi[9] = {0};
+        for (int64_t t = 0; t < P->nt; ++t) {
+            const double* M = &P->hmaps[12 * t];
+            const double* F = M + 3;
+            const double det = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                               F[2] * (F[3] * F[7] - F[4] * F[6]);
+            double Fi[9];
+            Fi[0] = (F[4] * F[8] - F[5] * F[7]) / det;
+            Fi[1] = (F[2] * F[7] - F[1] * F[8]) / det;
+            Fi[2] = (F[1] * F[5] - F[2] * F[4]) / det;
+            Fi[3] = (F[5] * F[6] - F[3] * F[8]) / det;
+            Fi[4] = (F[0] * F[8] - F[2] * F[6]) / det;
+            Fi[5] = (F[2] * F[3] - F[0] * F[5]) / det;
+            Fi[6] = (F[3] * F[7] - F[4] * F[6]) / det;
+            Fi[7] = (F[1] * F[6] - F[0] * F[7]) / det;
+            Fi[8] = (F[0] * F[4] - F[1] * F[3]) / det;
+            double xh[3];
+            for (int i = 0; i < 3; ++i)
+                xh[i] = Fi[3 * i] * (x[0] - M[0]) + Fi[3 * i + 1] * (x[1] - M[1]) + Fi[3 * i + 2] * (x[2] - M[2]);
+            const double mn = std::min(std::min(xh[0], xh[1]), std::min(xh[2], 1.0 - xh[0] - xh[1] - xh[2]));
+            if (mn > bestmin) {
+                bestmin = mn;
+                best = t;
+                std::memcpy(bxh, xh, sizeof(bxh));
+                std::memcpy(bFi, Fi, sizeof(bFi));
+            }
+        }
+        if (bestmin < -1e-10) {
+            set_error("dgm_adjoint_grad: observation point outside the mesh");
+            return DGM_ERR_INVALID_ARG;
+        }
+        oe[o] = (int32_t)best;
+        std::memcpy(&oxh[3 * o], bxh, sizeof(bxh));
+        std::memcpy(&oFi[9 * o], bFi, sizeof(bFi));
+        const double* g = &P->hgeo[(size_t)best * dgm::kGeoStride];
+        for (int q = 0; q < 6; ++q) ogi[6 * o + q] = g[q] * g[dgm::kGeoInvEps];
+    }
+    std::vector<double> ophi;
+    dgm::phi_at_points(P->p, oxh.data(), nobs, ophi);
+    const StateView v = state_view(P);
+    const size_t es = v.f32 ? sizeof(float) : sizeof(double);
+    const int64_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
+    const int N = P->NE, K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? 1 : 0;
+    const size_t sE = v.nE * es, sH = v.nH * es;
+    // one allocation: obs data, J, grad, saved state, checkpoints, segment, adjoint state
+    const size_t obs_bytes = ((nobs * sizeof(int32_t) + 255) / 256) * 256 + (ophi.size() + oFi.size() + ogi.size()) * 8;
+    const size_t total = obs_bytes + 256 + (size_t)P->nt * 8 + 256 + (sE + sH) * (1 + nck) + sE * (ckpt_every + 1) +
+                         sE + sH + 1024;
+    DevBuf buf;
+    DGM_CUDA(cudaMalloc(&buf.p, total));
+    char* q = (char*)buf.p;
+    auto take = [&](size_t bytes) {
+        char* r = q;
+        q += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    int32_t* dElem = (int32_t*)take(nobs * sizeof(int32_t));
+    double* dPhi = (double*)take(ophi.size() * 8);
+    double* dFi = (double*)take(oFi.size() * 8);
+    double* dGi = (double*)take(ogi.size() * 8);
+    double* dJ = (double*)take(8);
+    double* dGrad = (double*)take((size_t)P->nt * 8);
+    char* save = take(sE + sH);
+    char* ck = take((sE + sH) * nck);
+    char* seg = take(sE * (ckpt_every + 1));
+    char* aE = take(sE);
+    char* aH = take(sH);
+    cudaMemcpy(dElem, oe.data(), nobs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(dPhi, ophi.data(), ophi.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dFi, oFi.data(), oFi.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dGi, ogi.data(), ogi.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemset(dJ, 0, 8);
+    cudaMemset(dGrad, 0, (size_t)P->nt * 8);
+    cudaMemset(aE, 0, sE);
+    cudaMemset(aH, 0, sH);
+    const dgm::ObsDev O{nobs, dElem, dPhi, dFi, dGi};
+    const double* geo = P->tc ? P->dTcGeo : P->dGeo;
+    auto observe = [&](const void* E) {
+        return v.f32 ? dgm::adj_observe<float>(O, (const float*)E, N, K, tiled, dJ, 0)
+                     : dgm::adj_observe<double>(O, (const double*)E, N, K, tiled, dJ, 0);
+    };
+    int rc = DGM_OK;
+    void* E0p = v.E;
+    void* H0p = v.H;
+    cudaMemcpy(save, v.E, sE, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(save + sE, v.H, sH, cudaMemcpyDeviceToDevice);
+    P->trE_valid = P->trH_valid = false;
+    // forward: G^0 = H^0 + dt/2 A E^0; per step E-kick, observe, H-kick; checkpoints (E^n, G^n)
+    rc = prepare_source(P, P->time, dt, nsteps);
+    if (!rc) rc = phase_H(P, 0.5 * dt, 0.0, 1.0, nullptr, 0);
+    for (int64_t n = 0; n < nsteps && !rc; ++n) {
+        if (n % ckpt_every == 0) {
+            cudaMemcpy(ck + (n / ckpt_every) * (sE + sH), v.E, sE, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(ck + (n / ckpt_every) * (sE + sH) + sE, v.H, sH, cudaMemcpyDeviceToDevice);
+        }
+        rc = phase_E(P, dt, 0);
+        if (!rc) rc = apply_source(P, v.E, n, dt, 0);
+        if (!rc && observe(v.E)) rc = cuda_fail(cudaGetLastError(), "observe");
+        if (!rc) rc = phase_H(P, dt, 0.0, 1.0, nullptr, 0);
+    }
+    // backward over segments, recomputing each segment's E from its checkpoint
+    for (int64_t s = nck - 1; s >= 0 && !rc; --s) {
+        const int64_t n0 = s * ckpt_every, n1 = std::min<int64_t>(nsteps, n0 + ckpt_every);
+        set_state_ptrs(P, E0p, H0p);
+        cudaMemcpy(v.E, ck + s * (sE + sH), sE, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(v.H, ck + s * (sE + sH) + sE, sH, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(seg, v.E, sE, cudaMemcpyDeviceToDevice);
+        for (int64_t n = n0; n < n1 && !rc; ++n) {
+            rc = phase_E(P, dt, 0);
+            if (!rc) rc = apply_source(P, v.E, n, dt, 0);
+            cudaMemcpyAsync(seg + (n - n0 + 1) * sE, v.E, sE, cudaMemcpyDeviceToDevice, 0);
+            if (!rc && n < n1 - 1) rc = phase_H(P, dt, 0.0, 1.0, nullptr, 0);
+        }
+        set_state_ptrs(P, aE, aH);
+        for (int64_t m = n1; m > n0 && !rc; --m) {
+            const char* Em = seg + (m - n0) * sE;
+            const char* Emm = seg + (m - n0 - 1) * sE;
+            rc = phase_E(P, -dt, 0);   // e^ += dt M_eps^{-1} C^T g^
+            if (rc) break;
+            int r = v.f32 ? dgm::adj_source<float>(O, (const float*)Em, (float*)aE, N, K, tiled, 0)
+                          : dgm::adj_source<double>(O, (const double*)Em, (double*)aE, N, K, tiled, 0);
+            P->trE_valid = false;
+            r |= v.f32 ? dgm::adj_grad<float>(P->nt, geo, (const float*)aE, (const float*)Em, (const float*)Emm, N,
+                                              K, tiled, dGrad, 0)
+                       : dgm::adj_grad<double>(P->nt, geo, (const double*)aE, (const double*)Em, (const double*)Emm,
+                                               N, K, tiled, dGrad, 0);
+            if (r) {
+                rc = cuda_fail(cudaGetLastError(), "adjoint kernels");
+                break;
+            }
+            rc = phase_H(P, -dt, 0.0, 1.0, nullptr, 0);   // g^ -= dt M_mu^{-1} C e^
+        }
+    }
+    set_state_ptrs(P, E0p, H0p);
+    cudaMemcpy(v.E, save, sE, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(v.H, save + sE, sH, cudaMemcpyDeviceToDevice);
+    P->trE_valid = P->trH_valid = false;
+    if (rc) return rc;
+    DGM_CUDA(cudaDeviceSynchronize());
+    if (P->tc && (rc = dgm::tc_check_error(P))) return rc;
+    if (J_out) DGM_CUDA(cudaMemcpy(J_out, dJ, 8, cudaMemcpyDeviceToHost));
+    if (dJdeps) DGM_CUDA(cudaMemcpy(dJdeps, dGrad, (size_t)P->nt * 8, cudaMemcpyDeviceToHost));
+    return DGM_OK;
+}
+
+int dgm_set_materials(dgm_problem* P, const double* eps, const double* mu) {
+    if (!P || !eps || !mu) {
+        set_error("dgm_set_materials: null argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    for (int64_t t = 0; t < P->nt; ++t)
+        if (!(eps[t] > 0.0) || !(mu[t] > 0.0) || !std::isfinite(eps[t]) || !std::isfinite(mu[t])) {
+            set_error("dgm_set_materials: eps and mu must be positive and finite");
+            return DGM_ERR_INVALID_ARG;
+        }
+    for (int64_t t = 0; t < P->nt; ++t) {
+        double* g = &P->hgeo[(size_t)t * dgm::kGeoStride];
+        g[dgm::kGeoEps] = eps[t];
+        g[dgm::kGeoInvEps] = 1.0 / eps[t];
+        g[dgm::kGeoMu] = mu[t];
+        g[dgm::kGeoInvMu] = 1.0 / mu[t];
+    }
+    P->eps.assign(eps, eps + P->nt);
+    P->mu.assign(mu, mu + P->nt);
+    DGM_CUDA(cudaDeviceSynchronize());
+    DGM_CUDA(cudaMemcpy(P->dGeo, P->hgeo.data(), P->hgeo.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (P->tc) DGM_CUDA(cudaMemcpy(P->dTcGeo, P->hgeo.data(), P->hgeo.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return DGM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Enqueue the kernels of nsteps leapfrog steps on stream s, no host
+// synchronisation or copies (usable inside stream capture); the source values
+// must have been prepared.  Energies (optional) go to the problem's device array.
+int enqueue_run(dgm_problem* P, double dt, int64_t nsteps, cudaStream_t s, bool want) {
+    double* W = P->dEnergy;
+    if (P->tc) P->trE_valid = false;   // the first H-phase recomputes E traces (and E^0's energy)
+    int rc = phase_H(P, dt, 0.5, 0.5, want ? W : nullptr, s);
+    for (int64_t n = 0; n < nsteps && !rc; ++n) {
+        rc = phase_E(P, dt, s, want);
+        if (!rc) rc = apply_source(P, current_E(P), n, dt, s);
+        if (!rc) rc = phase_H(P, dt, 0.0, n == nsteps - 1 ? 0.5 : 1.0, want ? W + n + 1 : nullptr, s);
+    }
+    return rc;
+}
+
+void batch_release_graph(dgm_batch* B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    B->g_nsteps = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgm_batch_create(dgm_ctx* ctx, dgm_problem** probs, int nruns, dgm_batch** out) {
+    if (!ctx || !probs || nruns < 1 || !out) {
+        set_error("dgm_batch_create: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    dgm_batch* B = new (std::nothrow) dgm_batch;
+    if (!B) return DGM_ERR_OOM;
+    B->ctx = ctx;
+    for (int r = 0; r < nruns; ++r) {
+        if (!probs[r] || probs[r]->ctx->device != ctx->device) {
+            delete B;
+            set_error("dgm_batch_create: null problem or problem on another device");
+            return DGM_ERR_INVALID_ARG;
+        }
+        for (int q = 0; q < r; ++q)
+            if (probs[q] == probs[r]) {
+                delete B;
+                set_error("dgm_batch_create: a problem appears twice");
+                return DGM_ERR_INVALID_ARG;
+            }
+        B->probs.push_back(probs[r]);
+    }
+    B->streams.resize(nruns);
+    B->joins.resize(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        if (cudaStreamCreateWithFlags(&B->streams[r], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->joins[r], cudaEventDisableTiming) != cudaSuccess) {
+            dgm_batch_destroy(B);
+            return cuda_fail(cudaGetLastError(), "dgm_batch_create");
+        }
+    }
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) {
+        dgm_batch_destroy(B);
+        return cuda_fail(cudaGetLastError(), "dgm_batch_create");
+    }
+    *out = B;
+    return DGM_OK;
+}
+
+int dgm_batch_destroy(dgm_batch* B) {
+    if (!B) return DGM_OK;
+    batch_release_graph(B);
+    for (cudaStream_t s : B->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : B->joins)
+        if (e) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
+    delete B;
+    return DGM_OK;
+}
+
+int dgm_batch_run(dgm_batch* B, const double* dt, int64_t nsteps, void* stream, double* energy_out) {
+    if (!B || !dt || nsteps < 1) {
+        set_error("dgm_batch_run: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const int nr = (int)B->probs.size();
+    for (int r = 0; r < nr; ++r)
+        if (!std::isfinite(dt[r])) {
+            set_error("dgm_batch_run: non-finite time step");
+            return DGM_ERR_INVALID_ARG;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool want = energy_out != nullptr;
+    int rc = DGM_OK;
+    for (int r = 0; r < nr && !rc; ++r) {
+        dgm_problem* P = B->probs[r];
+        rc = ensure_energy(P, nsteps + 1);
+        if (!rc) rc = prepare_source(P, P->time, dt[r], nsteps);   // values refreshed before every launch
+    }
+    if (rc) return rc;
+    const bool same = B->exec && B->g_nsteps == nsteps && B->g_energy == want && B->g_stream == s &&
+                      std::equal(B->g_dt.begin(), B->g_dt.end(), dt);
+    if (!same) {
+        batch_release_graph(B);
+        // one graph: fork from s, every run's loop on its own stream, join back into s
+        DGM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        int crc = cudaEventRecord(B->fork, s) == cudaSuccess ? DGM_OK : DGM_ERR_CUDA;
+        for (int r = 0; r < nr && !crc; ++r) {
+            if (cudaStreamWaitEvent(B->streams[r], B->fork, 0) != cudaSuccess) crc = DGM_ERR_CUDA;
+            if (!crc) crc = enqueue_run(B->probs[r], dt[r], nsteps, B->streams[r], want);
+            if (!crc && cudaEventRecord(B->joins[r], B->streams[r]) != cudaSuccess) crc = DGM_ERR_CUDA;
+            if (!crc && cudaStreamWaitEvent(s, B->joins[r], 0) != cudaSuccess) crc = DGM_ERR_CUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        if (crc || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return crc ? crc : cuda_fail(ee, "dgm_batch_run capture");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&B->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            B->exec = nullptr;
+            return cuda_fail(ie, "dgm_batch_run instantiate");
+        }
+        B->g_nsteps = nsteps;
+        B->g_dt.assign(dt, dt + nr);
+        B->g_energy = want;
+        B->g_stream = s;
+    }
+    DGM_CUDA(cudaGraphLaunch(B->exec, s));
+    for (int r = 0; r < nr; ++r) B->probs[r]->time += nsteps * dt[r];
+    if (want) {
+        DGM_CUDA(cudaStreamSynchronize(s));
+        for (int r = 0; r < nr; ++r) {
+            double* Wr = energy_out + (size_t)r * (nsteps + 1);
+            DGM_CUDA(cudaMemcpy(Wr, B->probs[r]->dEnergy, (nsteps + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+            if (B->probs[r]->tc && (rc = dgm::tc_check_error(B->probs[r]))) return rc;
+            for (int64_t n = 0; n <= nsteps; ++n)
+                if (!std::isfinite(Wr[n]) || Wr[n] > 10.0 * std::fabs(Wr[0]) + 1e-300) {
+                    set_error("dgm_batch_run: energy blew up in run " + std::to_string(r));
+                    return DGM_ERR_UNSTABLE;
+                }
+        }
+    }
     return DGM_OK;
 }
 

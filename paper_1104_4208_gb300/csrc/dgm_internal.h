@@ -42,6 +42,8 @@ void index3(int p, std::vector<int>& ijk);   // 3 ints per entry, lexicographic
 void collapsed_rule(int q1d, std::vector<double>& xh, std::vector<double>& w, std::vector<double>& col);
 // Orthonormalised phi'_a at the collapsed rule's points, [nq][N3(p)].
 void phi_table(int p, int q1d, std::vector<double>& phi);
+// Orthonormalised phi'_a at n Cartesian reference points xh [n][3], [n][N3(p)].
+void phi_at_points(int p, const double* xh, int n, std::vector<double>& out);
 void index2(int p, std::vector<int>& ij);
 
 // ---------------------------------------------------------------- mesh

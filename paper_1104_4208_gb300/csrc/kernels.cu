@@ -376,6 +376,13 @@ __global__ void k_export(const real* __restrict__ src, double* __restrict__ dst,
         dst[i] = (double)src[i] / nrm[i % ncoef];
 }
 
+// y = a x + b y (power iteration of the stability estimate)
+template <typename real>
+__global__ void k_axpby(int64_t n, double a, const real* __restrict__ x, double b, real* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (real)(a * (double)x[i] + b * (double)y[i]);
+}
+
 __global__ void k_energy_reduce(const double* __restrict__ partials, int n, double* __restrict__ out) {
     __shared__ double red[256];
     double s = 0.0;
@@ -515,6 +522,16 @@ int launch_export(const real* src, double* dst, const double* nrm, int64_t n, in
     k_export<real><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, nrm, n, ncoef);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+template <typename real>
+int launch_axpby(int64_t n, double a, const real* x, double b, real* y, cudaStream_t s) {
+    if (n == 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_axpby<real><<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, a, x, b, y);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+template int launch_axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);
+template int launch_axpby<float>(int64_t, double, const float*, double, float*, cudaStream_t);
 
 int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s) {
     k_energy_reduce<<<1, 256, 0, s>>>(partials, n, out);

@@ -63,6 +63,8 @@ template <typename real>
 int launch_eval(int64_t nt, int N, int nq, const double* maps, const double* phi, const real* c, double* pts,
                 cudaStream_t s);
 int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s);
+template <typename real>
+int launch_axpby(int64_t n, double a, const real* x, double b, real* y, cudaStream_t s);
 int phase_warps_per_block();
 
 }  // namespace dgm

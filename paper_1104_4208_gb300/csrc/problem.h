@@ -60,6 +60,29 @@ struct dgm_problem {
     int32_t* dTcNbr = nullptr;
     int* dErr = nullptr;
     bool trE_valid = false, trH_valid = false;
+    std::vector<double> hmaps;           // [nt][12] X0, F (host copy, point location)
+    double time = 0.0;                   // time of the state (advanced by dgm_run)
+    // point dipole source (dgm_set_source)
+    bool src_on = false;
+    int64_t src_elem = -1;
+    double src_t0 = 0.0, src_tau = 1.0, src_amp = 0.0;
+    double* dSrc = nullptr;              // [3 + NE]: v = G^{-1} F^{-1} dir / eps, phi'(xh_s)
+    double* dSrcF = nullptr;             // [src_cap] f(t_{n+1/2}) of the current run
+    int64_t src_cap = 0;
+    std::vector<double> hgeo;            // [nt][kGeoStride] (host copy)
+};
+
+struct dgm_batch {
+    dgm_ctx* ctx = nullptr;
+    std::vector<dgm_problem*> probs;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t g_nsteps = -1;
+    std::vector<double> g_dt;
+    bool g_energy = false;
+    cudaStream_t g_stream = nullptr;
 };
 
 namespace dgm {

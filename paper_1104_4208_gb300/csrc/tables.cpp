@@ -19,6 +19,7 @@
 // Host arithmetic is compiled with -ffp-contract=off so that the tables are
 // bit-identical on x86-64 and aarch64.
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -258,6 +259,23 @@ void phi_table(int p, int q1d, std::vector<double>& phi) {
         phi3_at(p, idx, col[3 * q], col[3 * q + 1], col[3 * q + 2], &phi[(size_t)q * N], nullptr, nullptr, nullptr);
         for (int a = 0; a < N; ++a)
             phi[(size_t)q * N + a] /= std::sqrt(dubiner3_norm2(idx[3 * a], idx[3 * a + 1], idx[3 * a + 2]));
+    }
+}
+
+void phi_at_points(int p, const double* xh, int n, std::vector<double>& out) {
+    std::vector<int> idx;
+    index3(p, idx);
+    const int N = (int)idx.size() / 3;
+    out.assign((size_t)n * N, 0.0);
+    for (int q = 0; q < n; ++q) {
+        // keep the collapsed map away from its singular edges for points on faces/edges
+        const double x = std::min(std::max(xh[3 * q], 0.0), 1.0 - 1e-13);
+        const double y = std::min(std::max(xh[3 * q + 1], 0.0), 1.0 - x - 1e-13);
+        const double z = std::min(std::max(xh[3 * q + 2], 0.0), 1.0 - x - y);
+        const double eta = y / (1.0 - x), zeta = z / (1.0 - x - y);
+        phi3_at(p, idx, x, eta, zeta, &out[(size_t)q * N], nullptr, nullptr, nullptr);
+        for (int a = 0; a < N; ++a)
+            out[(size_t)q * N + a] /= std::sqrt(dubiner3_norm2(idx[3 * a], idx[3 * a + 1], idx[3 * a + 2]));
     }
 }
 

@@ -4,8 +4,9 @@
 //
 // Internal coefficient order of one element: k = 3 a + m (coefficient a,
 // component m), so the 3x3 inverse-mass block of a coefficient acts on three
-// consecutive values.  Face-trace columns: j = (2 f + i) N2(p-1) + g (face f,
-// tangential component i, face mode g of degree <= p-1).
+// consecutive values.  Face-trace columns: j = f FB + i N2(p-1) + g (face f,
+// tangential component i, face mode g of degree <= p-1; FB = 2 N2(p-1) padded
+// to a multiple of 4 so that each face's block is 16-byte aligned).
 
 #include <cuda_runtime.h>
 
@@ -102,7 +103,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     for (int f = 0; f < 4; ++f)
         for (int i = 0; i < 2; ++i)
             for (int gm = 0; gm < N2H; ++gm) {
-                const int j = (2 * f + i) * N2H + gm;
+                const int j = f * d.FB + i * N2H + gm;
                 const int gE = T.pos2H[gm];
                 for (int a = 0; a < NE; ++a) {
                     const double tr = T.TrE[f][(size_t)gE * NE + a];
@@ -112,7 +113,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
                         B1H.put(d.NC + j, 3 * a + mm, v);
                         BTE.put(j, 3 * a + mm, v);
                         // lift of the face average into E: (t2_m b1 - t1_m b2)
-                        BLE.put(3 * a + mm, (2 * f + (1 - i)) * N2H + gm, i == 1 ? v : -v);
+                        BLE.put(3 * a + mm, f * d.FB + (1 - i) * N2H + gm, i == 1 ? v : -v);
                     }
                 }
                 for (int b = 0; b < NH; ++b) {
@@ -122,7 +123,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
                         if (v == 0.0) continue;
                         BTH.put(j, 3 * b + mm, v);
                         B1E.put(d.NCE + j, 3 * b + mm, v);
-                        BLH.put(3 * b + mm, (2 * f + (1 - i)) * N2H + gm, i == 1 ? v : -v);
+                        BLH.put(3 * b + mm, f * d.FB + (1 - i) * N2H + gm, i == 1 ? v : -v);
                     }
                 }
             }

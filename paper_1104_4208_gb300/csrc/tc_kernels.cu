@@ -179,50 +179,101 @@ __device__ void block_sum_store(double v, double* out) {
     if (threadIdx.x == 0) out[blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
 }
 
-// flux of one tile into the resident region: thread = element, columns of D_t
-// at tmem column ct0; jump (H-phase, avg = false) or average (E-phase)
+// flux of one tile into the resident region: thread = element; per face the
+// neighbour's trace block (FB floats, 16-B aligned) is loaded with vector loads
+// issued together, then the own trace columns are read from TMEM.  Jump
+// (H-phase, avg = false) or average (E-phase); PEC faces use the ghost state.
+constexpr int kMaxFaceChunks = 11;   // FB / 4 for p <= 6
+
 __device__ void epi_flux(const TCArgs& A, uint32_t lane_tmem, int ct0, const float* nbr_tr, int64_t t,
                          bool avg, float* a2) {
     const TCDims& d = A.d;
     const int tid = threadIdx.x;
-    const int nvalid = 8 * d.N2H;
-    const int32_t* nb4 = A.nbr + t * 4;
-    const int32_t nbf[4] = {nb4[0], nb4[1], nb4[2], nb4[3]};
-    for (int j0 = 0; j0 < d.NT; j0 += 4) {
-        float v[4];
-        tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + j0), v[0], v[1], v[2], v[3]);
-        float o[4];
+    const int FB = d.FB, nvalid = 2 * d.N2H, nchunk = FB / 4;
+    const int4 nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
+    const int32_t nbf[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        const int32_t nb = nbf[f];
+        const float sh = A.sigma_hat[f];
+        float4 nv[kMaxFaceChunks];
+        if (nb >= 0) {
+            const float4* src = reinterpret_cast<const float4*>(nbr_tr + (size_t)(nb >> 2) * d.NT + (nb & 3) * FB);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + q;
-            if (j >= nvalid) {
-                o[q] = 0.f;
-                continue;
-            }
-            const int f = j / (2 * d.N2H);
-            const int r = j - f * 2 * d.N2H;
-            const int32_t nb = nbf[f];
-            const float sh = A.sigma_hat[f];
-            if (nb >= 0) {
-                const float jn = nbr_tr[(size_t)(nb >> 2) * d.NT + (nb & 3) * 2 * d.N2H + r];
-                o[q] = avg ? sh * 0.5f * (v[q] + jn) : -sh * 0.5f * (v[q] - jn);
-            } else {
-                o[q] = avg ? sh * v[q] : -sh * v[q];
-            }
+            for (int c = 0; c < kMaxFaceChunks; ++c)
+                if (c < nchunk) nv[c] = src[c];
         }
-        *reinterpret_cast<float4*>(a2 + ((size_t)(j0 >> 2) * kTcRows + tid) * 4) = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+        for (int c = 0; c < kMaxFaceChunks; ++c) {
+            if (c >= nchunk) break;
+            float v[4];
+            tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + f * FB + 4 * c), v[0], v[1], v[2], v[3]);
+            const float n4[4] = {nv[c].x, nv[c].y, nv[c].z, nv[c].w};
+            float o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = 4 * c + q;
+                if (r >= nvalid) {
+                    o[q] = 0.f;
+                } else if (nb >= 0) {
+                    o[q] = avg ? sh * 0.5f * (v[q] + n4[q]) : -sh * 0.5f * (v[q] - n4[q]);
+                } else {
+                    o[q] = avg ? sh * v[q] : -sh * v[q];
+                }
+            }
+            *reinterpret_cast<float4*>(a2 + ((size_t)((f * FB >> 2) + c) * kTcRows + tid) * 4) =
+                make_float4(o[0], o[1], o[2], o[3]);
+        }
     }
 }
 
 // trace columns of D_t -> trace buffer row of element t
 __device__ void epi_traces(const TCArgs& A, uint32_t lane_tmem, int ct0, float* tr, int64_t t) {
     const int NT = A.d.NT;
-    float* row = tr + (size_t)t * NT;
-    for (int j0 = 0; j0 < NT; j0 += 4) {
-        float v0, v1, v2, v3;
-        tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + j0), v0, v1, v2, v3);
-        *reinterpret_cast<float4*>(row + j0) = make_float4(v0, v1, v2, v3);
+    float4* row = reinterpret_cast<float4*>(tr + (size_t)t * NT);
+    for (int j0 = 0; j0 < NT; j0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_tmem + (uint32_t)(ct0 + j0), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) row[(j0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
+}
+
+// The update epilogue: per batch of up to 16 coefficients (48 values) the old
+// field values are loaded first (12 float4, one per 4 values), then the 48
+// accumulator columns, then r = sgn * D, delta = s G^{-1} r per coefficient.
+// `Op` applies the per-coefficient update and the energy partial.
+template <typename Op>
+__device__ void epi_update(uint32_t lane_tmem, float* field_tile, float* a3, int N, int K, Op op) {
+    const int tid = threadIdx.x;
+    float4* F4 = reinterpret_cast<float4*>(field_tile);
+    float4* A4 = reinterpret_cast<float4*>(a3);
+    const int ngroups = (N + 3) / 4;
+#pragma unroll 1
+    for (int g0 = 0; g0 < ngroups; g0 += 4) {
+        const int nq = 3 * min(4, ngroups - g0);
+        float4 hv[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+            if (q < nq) hv[q] = F4[(size_t)(3 * g0 + q) * kTcRows + tid];
+        float dd[48];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) tc::tmem_ld16(lane_tmem + (uint32_t)(12 * g0 + 16 * s), dd + 16 * s);
+        float* h = reinterpret_cast<float*>(hv);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            if (c >= 4 * (nq / 3)) break;
+            if (4 * g0 + c >= N) break;
+            op(h + 3 * c, dd + 3 * c);
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+            if (q < nq) {
+                F4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
+                A4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
+            }
+    }
+    for (int kc = 3 * ngroups; kc < K / 4; ++kc) A4[(size_t)kc * kTcRows + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // split an output range of up to 2 x 256 columns into MMAs (N <= 256)
@@ -292,52 +343,25 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_H(TCArgs A, double dt, doub
             const double mu = gg[kGeoMu];
             const float sT = (float)gg[kGeoSign];
             const float s = (float)(dt * gg[kGeoInvMu]);
-            float* Ht = A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4;
-            const int ngroups = (d.NH + 3) / 4;
-            for (int grp = 0; grp < ngroups; ++grp) {
-                float dd[12];
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp), dd[0], dd[1], dd[2], dd[3]);
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 4), dd[4], dd[5], dd[6], dd[7]);
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 8), dd[8], dd[9], dd[10], dd[11]);
-                float hv[12];
-                float4* hp[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    hp[q] = reinterpret_cast<float4*>(Ht + ((size_t)(3 * grp + q) * kTcRows + tid) * 4);
-                    const float4 h = *hp[q];
-                    hv[4 * q] = h.x;
-                    hv[4 * q + 1] = h.y;
-                    hv[4 * q + 2] = h.z;
-                    hv[4 * q + 3] = h.w;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (4 * grp + c >= d.NH) break;
-                    const float r0 = -sT * dd[3 * c], r1 = -sT * dd[3 * c + 1], r2v = -sT * dd[3 * c + 2];
-                    const float d0 = s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
-                    const float d1 = s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
-                    const float d2 = s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
-                    const float h0 = hv[3 * c], h1 = hv[3 * c + 1], h2 = hv[3 * c + 2];
-                    if (energy) {
-                        const double l0 = (double)h0 - a_lo * d0, l1 = (double)h1 - a_lo * d1, l2 = (double)h2 - a_lo * d2;
-                        const double u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
-                        eacc += 0.5 * mu *
-                                (l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
-                                 l2 * (G2 * u0 + G4 * u1 + G5 * u2));
-                    }
-                    hv[3 * c] = h0 + (float)c_out * d0;
-                    hv[3 * c + 1] = h1 + (float)c_out * d1;
-                    hv[3 * c + 2] = h2 + (float)c_out * d2;
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const float4 h = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                    *hp[q] = h;
-                    *reinterpret_cast<float4*>(r2 + ((size_t)(3 * grp + q) * kTcRows + tid) * 4) = h;
-                }
-            }
-            for (int kc = 3 * ngroups; kc < d.KH / 4; ++kc)
-                *reinterpret_cast<float4*>(r2 + ((size_t)kc * kTcRows + tid) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float co = (float)c_out;
+            epi_update(lane_tmem, A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4, r2, d.NH, d.KH,
+                       [&](float* h, const float* dd) {
+                           const float r0 = -sT * dd[0], r1 = -sT * dd[1], r2v = -sT * dd[2];
+                           const float d0 = s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
+                           const float d1 = s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
+                           const float d2 = s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
+                           if (energy) {
+                               const double l0 = (double)h[0] - a_lo * d0, l1 = (double)h[1] - a_lo * d1,
+                                            l2 = (double)h[2] - a_lo * d2;
+                               const double u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
+                               eacc += 0.5 * mu *
+                                       (l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
+                                        l2 * (G2 * u0 + G4 * u1 + G5 * u2));
+                           }
+                           h[0] += co * d0;
+                           h[1] += co * d1;
+                           h[2] += co * d2;
+                       });
         }
         epilogue_barrier();
         // GEMM3: traces of the new H for the E-phase
@@ -412,50 +436,19 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_E(TCArgs A, double dt, int 
             const double eps = gg[kGeoEps];
             const float sT = (float)gg[kGeoSign];
             const float s = (float)(dt * gg[kGeoInvEps]);
-            float* Et = A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4;
-            const int ngroups = (d.NE + 3) / 4;
-            for (int grp = 0; grp < ngroups; ++grp) {
-                float dd[12];
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp), dd[0], dd[1], dd[2], dd[3]);
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 4), dd[4], dd[5], dd[6], dd[7]);
-                tc::tmem_ld4(lane_tmem + (uint32_t)(12 * grp + 8), dd[8], dd[9], dd[10], dd[11]);
-                float ev[12];
-                float4* ep[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    ep[q] = reinterpret_cast<float4*>(Et + ((size_t)(3 * grp + q) * kTcRows + tid) * 4);
-                    const float4 e = *ep[q];
-                    ev[4 * q] = e.x;
-                    ev[4 * q + 1] = e.y;
-                    ev[4 * q + 2] = e.z;
-                    ev[4 * q + 3] = e.w;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (4 * grp + c >= d.NE) break;
-                    const float r0 = sT * dd[3 * c], r1 = sT * dd[3 * c + 1], r2v = sT * dd[3 * c + 2];
-                    const float e0 = ev[3 * c] + s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
-                    const float e1 = ev[3 * c + 1] + s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
-                    const float e2 = ev[3 * c + 2] + s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
-                    if (energy) {
-                        const double x0 = e0, x1 = e1, x2 = e2;
-                        eacc += 0.5 * eps *
-                                (x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
-                                 x2 * (G2 * x0 + G4 * x1 + G5 * x2));
-                    }
-                    ev[3 * c] = e0;
-                    ev[3 * c + 1] = e1;
-                    ev[3 * c + 2] = e2;
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const float4 e = make_float4(ev[4 * q], ev[4 * q + 1], ev[4 * q + 2], ev[4 * q + 3]);
-                    *ep[q] = e;
-                    *reinterpret_cast<float4*>(r2 + ((size_t)(3 * grp + q) * kTcRows + tid) * 4) = e;
-                }
-            }
-            for (int kc = 3 * ngroups; kc < d.KE / 4; ++kc)
-                *reinterpret_cast<float4*>(r2 + ((size_t)kc * kTcRows + tid) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+            epi_update(lane_tmem, A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4, r2, d.NE, d.KE,
+                       [&](float* e, const float* dd) {
+                           const float r0 = sT * dd[0], r1 = sT * dd[1], r2v = sT * dd[2];
+                           e[0] += s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
+                           e[1] += s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
+                           e[2] += s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
+                           if (energy) {
+                               const double x0 = e[0], x1 = e[1], x2 = e[2];
+                               eacc += 0.5 * eps *
+                                       (x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
+                                        x2 * (G2 * x0 + G4 * x1 + G5 * x2));
+                           }
+                       });
         }
         epilogue_barrier();
         if (tid == 0) {
@@ -630,7 +623,8 @@ TCDims tc_dims(int NE, int NH, int N2H) {
     d.N2H = N2H;
     d.KE = padto(3 * NE, 24);
     d.KH = padto(3 * NH, 24);
-    d.NT = padto(8 * N2H, 16);
+    d.FB = padto(2 * N2H, 4);
+    d.NT = 4 * d.FB;
     d.NC = padto(12 * ((NH + 3) / 4), 16);
     d.NCE = padto(12 * ((NE + 3) / 4), 16);
     return d;

@@ -14,7 +14,8 @@ constexpr int kTcRows = 128;   // elements per tile = MMA M
 struct TCDims {
     int NE, NH, N2H;
     int KE, KH;      // padded state row lengths (multiples of 24): E, H
-    int NT;          // face-trace columns 8 N2H padded to 16
+    int FB;          // trace columns per face: 2 N2(p-1) padded to 4 (16-byte blocks)
+    int NT;          // face-trace columns 4 FB (multiple of 16)
     int NC;          // H-output columns (12 ceil(NH/4) padded to 16)
     int NCE;         // E-output columns (12 ceil(NE/4) padded to 16)
 };
@@ -27,7 +28,8 @@ struct TCArgs {
     TCDims d;
     float* E;                  // [ntiles][KE/4][128][4]
     float* H;                  // [ntiles][KH/4][128][4]
-    float* trE;                // [ntiles*128][NT] tangential E traces (degree <= p-1 face modes)
+    float* trE;                // [ntiles*128][NT] tangential E traces (degree <= p-1 face modes),
+                               // column f FB + i N2(p-1) + g
     float* trH;                // [ntiles*128][NT]
     const double* geo;         // [ntiles*128][kGeoStride] (padding rows benign)
     const int32_t* nbr;        // [ntiles*128][4]

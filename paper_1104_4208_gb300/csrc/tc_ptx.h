@@ -127,21 +127,34 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// Four consecutive fp32 columns of this thread's TMEM lane (lane = warp's
-// sub-partition * 32 + lane id, encoded in taddr bits 31..16); waits for
-// completion inside the same asm block so the registers are valid on return.
+// Four / sixteen consecutive fp32 columns of this thread's TMEM lane (lane =
+// warp's sub-partition * 32 + lane id, encoded in taddr bits 31..16); the wait
+// is inside the same asm block, so the registers are valid on return.  No
+// memory clobber: global loads may be scheduled across these.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float& v0, float& v1, float& v2, float& v3) {
     uint32_t r0, r1, r2, r3;
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-        : "r"(taddr)
-        : "memory");
+        : "r"(taddr));
     v0 = __uint_as_float(r0);
     v1 = __uint_as_float(r1);
     v2 = __uint_as_float(r2);
     v3 = __uint_as_float(r3);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace tc

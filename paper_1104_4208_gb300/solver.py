@@ -24,6 +24,8 @@ class Solver:
         eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.nt,))
         mu = np.broadcast_to(np.asarray(mu, dtype=np.float64), (self.nt,))
         self.prob = capi.dgm_problem_create(self.ctx, self.mesh, p, eps, mu, opt)
+        self.eps = np.array(eps)
+        self.mu = np.array(mu)
         self.p = p
         self.nE, self.nH, self.nHF = capi.dgm_problem_sizes(self.prob)
 

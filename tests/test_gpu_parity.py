@@ -375,3 +375,173 @@ def test_tc32_cavity_trajectory(capi):
     assert drift < 1e-3
     assert abs(e - eo) < 0.02 * eo
     S.close()
+
+
+@pytest.mark.parametrize("precision,flux", [("fp64", "central"), ("fp64", "stabilized"), ("tc32", "central")])
+def test_stability_bound_power_iteration(capi, precision, flux):
+    """Sec. 3: dt <= 2/sqrt(rho(M_mu^{-1} C M_eps^{-1} C^T)); the library's power
+    iteration vs the oracle's dense eigenvalue (upper bound, within 5% from below);
+    the workload time step 0.2 h/p^2 lies below the bound."""
+    import scipy.linalg as sl
+    from oracle.dg import OracleDG
+    m = kuhn_cube_mesh(2, jitter=0.1, seed=41)
+    p = 3
+    eps = np.random.default_rng(5).uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0, flux=flux)
+    A = dg.assemble()
+    CH = A["CH"].toarray()
+    K = CH @ sl.block_diag(*A["MEinv"]) @ CH.T
+    Mh = sl.block_diag(*A["MH"])
+    if flux == "stabilized":
+        S_ = A["S"].toarray()
+        C2 = np.vstack([CH, S_])
+        K = C2 @ sl.block_diag(*A["MEinv"]) @ C2.T
+        Mh = sl.block_diag(Mh, sl.block_diag(*A["MF"]))
+    rho_exact = sl.eigh(K, Mh, eigvals_only=True).max()
+    S = _solver(capi, m, p, eps, 1.0, precision, flux=flux)
+    rng = np.random.default_rng(6)
+    E0, H0 = rng.standard_normal(S.nE), rng.standard_normal(S.nH)
+    S.set_fields(E0, H0)
+    rho, dtmax = capi.dgm_estimate_dt(S.prob, 300)
+    E1, H1 = S.get_fields()[:2]
+    assert np.array_equal(E1, S.get_fields()[0])
+    assert _rel(E1, E0) < 1e-6 and _rel(H1, H0) < 1e-6          # state restored
+    _log("cfl", precision=precision, flux=flux, rho=rho, rho_exact=rho_exact)
+    assert 0.95 * rho_exact <= rho <= rho_exact * (1 + (1e-9 if precision == "fp64" else 5e-3))
+    assert dtmax == pytest.approx(2 / np.sqrt(rho))
+    assert 0.2 * 0.5 / p ** 2 < dtmax
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tc32"])
+def test_adjoint_gradient_vs_oracle(capi, precision):
+    """dJ/d eps by the library's checkpointed discrete adjoint (4 segments of 10
+    steps, 8 observation points, 162 tets, p=3) vs the oracle's adjoint."""
+    from oracle.dg import OracleDG, adjoint_grad_eps
+    from workloads.fields import random_points
+    m = kuhn_cube_mesh(3, jitter=0.1, seed=51, shuffle_local=True)
+    rng = np.random.default_rng(52)
+    eps = rng.uniform(1, 4, m.nt)
+    p, dt, N = 3, 0.2 / 3 / 9, 40
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+    E0 = rng.standard_normal(dg.sizeE) * 0.1
+    H0 = rng.standard_normal(dg.sizeH) * 0.1
+    pts = random_points(5005, 8, 0.1, 0.9)
+    Jo, go = adjoint_grad_eps(dg, E0, H0, dt, N, pts)
+    S = _solver(capi, m, p, eps, 1.0, precision)
+    S.set_fields(E0, H0)
+    J, g = capi.dgm_adjoint_grad(S.prob, dt, N, pts, 10, m.nt)
+    E1, H1 = S.get_fields()
+    assert _rel(E1, E0) < 1e-6                              # state restored
+    tol = 1e-10 if precision == "fp64" else 3e-2
+    _log("adjoint", precision=precision, errJ=abs(J - Jo) / Jo, errg=_rel(g, go))
+    assert abs(J - Jo) <= tol * Jo
+    assert _rel(g, go) < tol
+    S.close()
+
+
+def test_adjoint_full_workload_finite_differences(capi):
+    """Workload adjoint_n16_p4 (24,576 tets, p=4, eps~U[1,4], 500 steps, checkpoint
+    every 50, 8 seeded observation points, initial Gaussian pulse), FP64: the
+    adjoint gradient on 8 random elements vs central finite differences of J
+    with delta = 1e-6 eps_T."""
+    import torch
+    from oracle.dg import OracleDG
+    from oracle.project import project
+    from workloads.fields import random_points
+    from paper_1104_4208_gb300.autograd import ObservationObjective
+    w = make_workload("adjoint_n16_p4")
+    m = w.mesh
+    S = _solver(capi, m, w.p, w.eps, w.mu, "fp64")
+    dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu)
+    E0 = project(dg, lambda x: gaussian_pulse_fields(x, w.centre)[0], w.p)
+    H0 = np.zeros(S.nH)
+    pts = random_points(5000, 8, 0.1, 0.9)
+    eps = torch.tensor(w.eps, dtype=torch.float64, requires_grad=True)
+    J = ObservationObjective.apply(eps, S, E0, H0, w.dt, w.steps, pts, 50)
+    J.backward()
+    g = eps.grad.numpy()
+    rng = np.random.default_rng(53)
+    errs = []
+    for T in rng.choice(m.nt, 8, replace=False):
+        d = 1e-6 * w.eps[T]
+        vals = []
+        for sgn in (1, -1):
+            e2 = w.eps.copy()
+            e2[T] += sgn * d
+            capi.dgm_set_materials(S.prob, e2, w.mu)
+            S.set_fields(E0, H0)
+            vals.append(capi.dgm_adjoint_grad(S.prob, w.dt, w.steps, pts, 50, m.nt)[0])
+        fd = (vals[0] - vals[1]) / (2 * d)
+        errs.append(abs(fd - g[T]) / max(abs(g).max(), 1e-300))
+    _log("adjoint_fd", J=float(J), errs=[float(e) for e in errs])
+    assert max(errs) < 1e-6
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tc32"])
+def test_dipole_source_trajectory(capi, precision):
+    """Point dipole current (zero-mean Gaussian-derivative pulse) switched on from
+    zero fields: the library's source term in the E-kicks vs the oracle's
+    -(J, e) at the kick midpoints, 30 steps on a jittered PEC cube."""
+    from oracle.dg import OracleDG, dipole_source_vector
+    from workloads.fields import dipole_waveform
+    m = kuhn_cube_mesh(3, jitter=0.1, seed=61, shuffle_local=True)
+    rng = np.random.default_rng(62)
+    eps = rng.uniform(1, 4, m.nt)
+    p, dt, N = 3, 0.2 / 3 / 9, 30
+    xs, d = np.array([0.43, 0.52, 0.47]), np.array([0.0, 0.0, 1.0])
+    tau = N * dt / 6
+    t0 = 3 * tau
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+    unit = dipole_source_vector(dg, xs, d, 1.0)
+    src = lambda n: unit * dipole_waveform((n + 0.5) * dt, t0, tau)
+    Eo, Ho, _, Wo = dg.run(np.zeros(dg.sizeE), np.zeros(dg.sizeH), dt, N, source=src)
+    S = _solver(capi, m, p, eps, 1.0, precision)
+    capi.dgm_set_source(S.prob, xs, d, t0, tau, 1.0)
+    capi.dgm_set_time(S.prob, 0.0)
+    S.run(dt, N)
+    assert capi.dgm_get_time(S.prob) == pytest.approx(N * dt)
+    E, H = S.get_fields()
+    tol = TOL_TRAJ[precision]
+    _log("source", precision=precision, errE=_rel(E, Eo), errH=_rel(H, Ho))
+    assert _rel(E, Eo) < tol and _rel(H, Ho) < tol
+    S.close()
+
+
+def test_batch_graph_matches_individual_runs(capi):
+    """dgm_batch_run (one CUDA graph, one branch per run, replayed on the second
+    call) gives bitwise the fields and energies of separate dgm_run calls, for
+    runs of different sizes, orders, precisions and fluxes, one with a source."""
+    from paper_1104_4208_gb300.solver import Solver
+    specs = [(2, 2, "fp64", "central"), (3, 3, "tc32", "central"), (2, 4, "fp32", "central"),
+             (3, 5, "tc32", "central"), (2, 2, "fp64", "stabilized"), (3, 1, "tc32", "central")]
+    rng = np.random.default_rng(71)
+    made = []
+    for k, (n, p, prec, flux) in enumerate(specs):
+        m = kuhn_cube_mesh(n, jitter=0.1, seed=700 + k)
+        eps = rng.uniform(1, 4, m.nt)
+        pair = [Solver(m.xyz, m.tets, p, eps, 1.0, precision=prec, flux=flux) for _ in range(2)]
+        E0, H0 = rng.standard_normal(pair[0].nE), rng.standard_normal(pair[0].nH)
+        for S in pair:
+            S.set_fields(E0, H0, np.zeros(S.nHF) if S.nHF else None)
+            if k == 1:
+                capi.dgm_set_source(S.prob, [0.5, 0.45, 0.52], [0.0, 1.0, 0.0], 0.01, 0.004, 1.0)
+        made.append((pair, 0.1 / n / p ** 2))
+    dts = np.array([dt for _, dt in made])
+    B = capi.dgm_batch_create(made[0][0][0].ctx, [pair[0].prob for pair, _ in made])
+    nsteps = 7
+    Wb = np.empty((len(made), nsteps + 1))
+    for call in range(2):
+        capi.dgm_batch_run(B, dts, nsteps, None, Wb)
+        for r, (pair, dt) in enumerate(made):
+            W = pair[1].run(dt, nsteps, energies=True)
+            assert np.array_equal(W, Wb[r]), (call, r)
+            a, b = pair[0].get_fields(), pair[1].get_fields()
+            for x, y in zip(a, b):
+                if x is not None:
+                    assert np.array_equal(x, y), (call, r)
+    capi.dgm_batch_destroy(B)
+    for pair, _ in made:
+        for S in pair:
+            S.close()

@@ -366,3 +366,29 @@ def test_spurious_modes_removed_by_stabilization():
             assert np.allclose(nz[3:5], 3 * np.pi ** 2, rtol=0.01)
     assert counts["stabilized"] == ((p + 1) * n - 1) ** 3
     assert counts["central"] > counts["stabilized"] + 500
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    """Discrete adjoint of the leapfrog (objective J = sum_n sum_o |E^n(x_o)|^2,
+    derivative with respect to per-element eps) vs central finite differences with
+    delta = 1e-6 eps_T, both on the oracle (brute force on a tiny case)."""
+    from oracle.dg import adjoint_grad_eps, objective
+    m = kuhn_cube_mesh(2, jitter=0.1, seed=3)
+    p = 2
+    rng = np.random.default_rng(0)
+    eps = rng.uniform(1, 4, m.nt)
+    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+    E0 = rng.standard_normal(dg.sizeE) * 0.1
+    H0 = rng.standard_normal(dg.sizeH) * 0.1
+    pts = rng.uniform(0.1, 0.9, (4, 3))
+    dt, N = 0.01, 20
+    J, grad = adjoint_grad_eps(dg, E0, H0, dt, N, pts)
+    assert J == pytest.approx(objective(dg, E0, H0, dt, N, pts), rel=1e-13)
+    for T in (0, 5, 17, 33):
+        d = 1e-6 * eps[T]
+        ep, em = eps.copy(), eps.copy()
+        ep[T] += d
+        em[T] -= d
+        fd = (objective(OracleDG(m.xyz, m.tets, p, ep, 1.0), E0, H0, dt, N, pts)
+              - objective(OracleDG(m.xyz, m.tets, p, em, 1.0), E0, H0, dt, N, pts)) / (2 * d)
+        assert grad[T] == pytest.approx(fd, rel=1e-6, abs=1e-9)
