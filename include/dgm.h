@@ -72,7 +72,8 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
  * TC32: float state; the reference operators are applied to tiles of 128
  * elements on the tensor cores with TF32 operands (10-bit mantissa) and FP32
  * accumulation; one rounded table serves C_h and C_h^T, so the discrete
- * operator stays skew; geometry and energy in double.  Central flux, p <= 6. */
+ * operator stays skew; geometry in double, per-element energy partials in float
+ * summed in double.  Central flux, p <= 6. */
 enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2 };
 
 typedef struct dgm_options {

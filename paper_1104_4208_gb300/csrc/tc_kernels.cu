@@ -334,16 +334,20 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_H(TCArgs A, double dt, doub
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        // update: H += dt/mu G^{-1} r, r = -s_T D_c
+        // update: H += dt/mu G^{-1} r, r = -s_T D_c.  The element's energy
+        // partial is summed in FP32 (FP64 is scarce on this GPU) and added to
+        // the FP64 per-thread sum once per element.
         {
             const double* gg = A.geo + t * kGeoStride;
             const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
                         gi4 = (float)gg[4], gi5 = (float)gg[5];
-            const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+            const float G0 = (float)gg[6], G1 = (float)gg[7], G2 = (float)gg[8], G3 = (float)gg[9],
+                        G4 = (float)gg[10], G5 = (float)gg[11];
             const double mu = gg[kGeoMu];
             const float sT = (float)gg[kGeoSign];
             const float s = (float)(dt * gg[kGeoInvMu]);
-            const float co = (float)c_out;
+            const float co = (float)c_out, alo = (float)a_lo;
+            float eloc = 0.f;
             epi_update(lane_tmem, A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4, r2, d.NH, d.KH,
                        [&](float* h, const float* dd) {
                            const float r0 = -sT * dd[0], r1 = -sT * dd[1], r2v = -sT * dd[2];
@@ -351,17 +355,16 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_H(TCArgs A, double dt, doub
                            const float d1 = s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
                            const float d2 = s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
                            if (energy) {
-                               const double l0 = (double)h[0] - a_lo * d0, l1 = (double)h[1] - a_lo * d1,
-                                            l2 = (double)h[2] - a_lo * d2;
-                               const double u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
-                               eacc += 0.5 * mu *
-                                       (l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
-                                        l2 * (G2 * u0 + G4 * u1 + G5 * u2));
+                               const float l0 = h[0] - alo * d0, l1 = h[1] - alo * d1, l2 = h[2] - alo * d2;
+                               const float u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
+                               eloc += l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
+                                       l2 * (G2 * u0 + G4 * u1 + G5 * u2);
                            }
                            h[0] += co * d0;
                            h[1] += co * d1;
                            h[2] += co * d2;
                        });
+            eacc += 0.5 * mu * (double)eloc;
         }
         epilogue_barrier();
         // GEMM3: traces of the new H for the E-phase
@@ -427,15 +430,17 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_E(TCArgs A, double dt, int 
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        // update: E += dt/eps G^{-1} r, r = s_T D_c
+        // update: E += dt/eps G^{-1} r, r = s_T D_c (energy partial as in the H-phase)
         {
             const double* gg = A.geo + t * kGeoStride;
             const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
                         gi4 = (float)gg[4], gi5 = (float)gg[5];
-            const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
+            const float G0 = (float)gg[6], G1 = (float)gg[7], G2 = (float)gg[8], G3 = (float)gg[9],
+                        G4 = (float)gg[10], G5 = (float)gg[11];
             const double eps = gg[kGeoEps];
             const float sT = (float)gg[kGeoSign];
             const float s = (float)(dt * gg[kGeoInvEps]);
+            float eloc = 0.f;
             epi_update(lane_tmem, A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4, r2, d.NE, d.KE,
                        [&](float* e, const float* dd) {
                            const float r0 = sT * dd[0], r1 = sT * dd[1], r2v = sT * dd[2];
@@ -443,12 +448,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_phase_E(TCArgs A, double dt, int 
                            e[1] += s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
                            e[2] += s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
                            if (energy) {
-                               const double x0 = e[0], x1 = e[1], x2 = e[2];
-                               eacc += 0.5 * eps *
-                                       (x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
-                                        x2 * (G2 * x0 + G4 * x1 + G5 * x2));
+                               const float x0 = e[0], x1 = e[1], x2 = e[2];
+                               eloc += x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
+                                       x2 * (G2 * x0 + G4 * x1 + G5 * x2);
                            }
                        });
+            eacc += 0.5 * eps * (double)eloc;
         }
         epilogue_barrier();
         if (tid == 0) {
