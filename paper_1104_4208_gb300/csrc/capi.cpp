@@ -1273,7 +1273,8 @@ int dgm_batch_create(dgm_ctx* ctx, dgm_problem** probs, int nruns, dgm_batch** o
             return cuda_fail(cudaGetLastError(), "dgm_batch_create");
         }
     }
-    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) {
         dgm_batch_destroy(B);
         return cuda_fail(cudaGetLastError(), "dgm_batch_create");
     }
@@ -1289,6 +1290,7 @@ int dgm_batch_destroy(dgm_batch* B) {
     for (cudaEvent_t e : B->joins)
         if (e) cudaEventDestroy(e);
     if (B->fork) cudaEventDestroy(B->fork);
+    if (B->cap) cudaStreamDestroy(B->cap);
     delete B;
     return DGM_OK;
 }
@@ -1313,21 +1315,23 @@ int dgm_batch_run(dgm_batch* B, const double* dt, int64_t nsteps, void* stream, 
         if (!rc) rc = prepare_source(P, P->time, dt[r], nsteps);   // values refreshed before every launch
     }
     if (rc) return rc;
-    const bool same = B->exec && B->g_nsteps == nsteps && B->g_energy == want && B->g_stream == s &&
+    const bool same = B->exec && B->g_nsteps == nsteps && B->g_energy == want &&
                       std::equal(B->g_dt.begin(), B->g_dt.end(), dt);
     if (!same) {
         batch_release_graph(B);
-        // one graph: fork from s, every run's loop on its own stream, join back into s
-        DGM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-        int crc = cudaEventRecord(B->fork, s) == cudaSuccess ? DGM_OK : DGM_ERR_CUDA;
+        // one graph: fork from the capture stream, every run's loop on its own
+        // stream, join back; launched afterwards on the caller's stream
+        cudaStream_t c = B->cap;
+        DGM_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeRelaxed));
+        int crc = cudaEventRecord(B->fork, c) == cudaSuccess ? DGM_OK : DGM_ERR_CUDA;
         for (int r = 0; r < nr && !crc; ++r) {
             if (cudaStreamWaitEvent(B->streams[r], B->fork, 0) != cudaSuccess) crc = DGM_ERR_CUDA;
             if (!crc) crc = enqueue_run(B->probs[r], dt[r], nsteps, B->streams[r], want);
             if (!crc && cudaEventRecord(B->joins[r], B->streams[r]) != cudaSuccess) crc = DGM_ERR_CUDA;
-            if (!crc && cudaStreamWaitEvent(s, B->joins[r], 0) != cudaSuccess) crc = DGM_ERR_CUDA;
+            if (!crc && cudaStreamWaitEvent(c, B->joins[r], 0) != cudaSuccess) crc = DGM_ERR_CUDA;
         }
         cudaGraph_t graph = nullptr;
-        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        const cudaError_t ee = cudaStreamEndCapture(c, &graph);
         if (crc || ee != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             return crc ? crc : cuda_fail(ee, "dgm_batch_run capture");
@@ -1341,7 +1345,6 @@ int dgm_batch_run(dgm_batch* B, const double* dt, int64_t nsteps, void* stream, 
         B->g_nsteps = nsteps;
         B->g_dt.assign(dt, dt + nr);
         B->g_energy = want;
-        B->g_stream = s;
     }
     DGM_CUDA(cudaGraphLaunch(B->exec, s));
     for (int r = 0; r < nr; ++r) B->probs[r]->time += nsteps * dt[r];

@@ -78,6 +78,7 @@ struct dgm_batch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;          // capture stream (the legacy default stream cannot be captured)
     cudaGraphExec_t exec = nullptr;
     int64_t g_nsteps = -1;
     std::vector<double> g_dt;

@@ -65,7 +65,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     const TCDims d = tc_dims(T.NE, T.NH, T.N2H);
     uint32_t stage = 0, r2 = 0;
     const size_t smem = tc_smem_bytes(d, &stage, &r2);
-    if (P->p > 6 || smem + 1024 > 227 * 1024 || d.NCE + d.NT > 512 || d.NC + d.NT > 512) {
+    if (P->p > 6 || smem + 1024 > 227 * 1024 || tc_tmem_cols(d) > 512) {
         set_error("precision TC32 supports p <= 6");
         return DGM_ERR_UNSUPPORTED;
     }
@@ -77,8 +77,8 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     const int64_t nrow = ntiles * kTcRows;
     // sizes in floats
     const size_t nE = (size_t)nrow * d.KE, nH = (size_t)nrow * d.KH, nTr = (size_t)nrow * d.NT;
-    const size_t b1h = (size_t)d.KE * (d.NC + d.NT), blh = (size_t)d.NT * d.NC, bth = (size_t)d.KH * d.NT;
-    const size_t b1e = (size_t)d.KH * (d.NCE + d.NT), ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KE * d.NT;
+    const size_t b1h = (size_t)d.KE * d.NC, blh = (size_t)d.NT * d.NC, bth = (size_t)d.KH * d.NT;
+    const size_t b1e = (size_t)d.KH * d.NCE, ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KE * d.NT;
     const size_t ntab = b1h + blh + bth + b1e + ble + bte;
     const size_t total = nE + nH + 2 * nTr + ntab;
     cudaError_t e;
@@ -88,8 +88,8 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     std::vector<float> tab(ntab, 0.0f);
     const size_t o_b1h = 0, o_blh = o_b1h + b1h, o_bth = o_blh + blh, o_b1e = o_bth + bth, o_ble = o_b1e + b1e,
                  o_bte = o_ble + ble;
-    TableWriter B1H{tab, o_b1h, d.NC + d.NT}, BLH{tab, o_blh, d.NC}, BTH{tab, o_bth, d.NT};
-    TableWriter B1E{tab, o_b1e, d.NCE + d.NT}, BLE{tab, o_ble, d.NCE}, BTE{tab, o_bte, d.NT};
+    TableWriter B1H{tab, o_b1h, d.NC}, BLH{tab, o_blh, d.NC}, BTH{tab, o_bth, d.NT};
+    TableWriter B1E{tab, o_b1e, d.NCE}, BLE{tab, o_ble, d.NCE}, BTE{tab, o_bte, d.NT};
     const int NE = T.NE, NH = T.NH, N2H = T.N2H;
     for (int b = 0; b < NH; ++b)
         for (int mo = 0; mo < 3; ++mo)
@@ -110,7 +110,6 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
                     for (int mm = 0; mm < 3; ++mm) {
                         const double v = T.that[f][i][mm] * tr;
                         if (v == 0.0) continue;
-                        B1H.put(d.NC + j, 3 * a + mm, v);
                         BTE.put(j, 3 * a + mm, v);
                         // lift of the face average into E: (t2_m b1 - t1_m b2)
                         BLE.put(3 * a + mm, f * d.FB + (1 - i) * N2H + gm, i == 1 ? v : -v);
@@ -122,7 +121,6 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
                         const double v = T.that[f][i][mm] * tr;
                         if (v == 0.0) continue;
                         BTH.put(j, 3 * b + mm, v);
-                        B1E.put(d.NCE + j, 3 * b + mm, v);
                         BLH.put(3 * b + mm, f * d.FB + (1 - i) * N2H + gm, i == 1 ? v : -v);
                     }
                 }
@@ -151,7 +149,10 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->ctx->device);
-    P->tc_grid = (int)std::min<int64_t>(ntiles, sms);
+    // CTAs resident per SM: two when their TMEM columns and shared memory allow it
+    const uint32_t tcols = tc_tmem_cols(d);
+    const int per_sm = (tcols <= 256 && 2 * (smem + 1024) <= 227 * 1024) ? 2 : 1;
+    P->tc_grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
     double* part = nullptr;
     if ((e = cudaMalloc(&part, 2 * (size_t)P->tc_grid * sizeof(double))) != cudaSuccess)
         return cuda_err(e, "alloc partials");
@@ -178,6 +179,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     A.err = P->dErr;
     for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
     A.stage_bytes = stage;
+    A.tmem_cols = tcols;
     A.r2_offset = r2;
     P->tc = true;
     P->trE_valid = P->trH_valid = false;

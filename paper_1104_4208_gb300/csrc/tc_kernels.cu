@@ -39,7 +39,6 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr uint32_t kHead = 256;             // control block at the start of shared memory
-constexpr uint32_t kTmemCols = 512;
 constexpr long long kLimit = 4000000000LL;  // cycles before a wait gives up (~2 s)
 constexpr long long kDrain = 200000000LL;
 constexpr int kErrTimeout = 1;
@@ -135,7 +134,7 @@ __device__ bool wait_done(Ctl* ctl, uint32_t& done_cnt) {
     return ok;
 }
 
-__device__ void setup(Ctl* ctl, int warp) {
+__device__ void setup(Ctl* ctl, int warp, uint32_t tmem_cols) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&ctl->full[s], 1);
@@ -148,7 +147,7 @@ __device__ void setup(Ctl* ctl, int warp) {
         tc::fence_proxy_async();
     }
     if (warp == 0) {
-        tc::tmem_alloc(&ctl->tmem, kTmemCols);
+        tc::tmem_alloc(&ctl->tmem, tmem_cols);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
@@ -156,11 +155,11 @@ __device__ void setup(Ctl* ctl, int warp) {
     tc::tc_fence_after();
 }
 
-__device__ void teardown(Ctl* ctl, int warp) {
+__device__ void teardown(Ctl* ctl, int warp, uint32_t tmem_cols) {
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (warp == 0) tc::tmem_dealloc(ctl->tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(ctl->tmem, tmem_cols);
 }
 
 // make shared-memory writes of the epilogue visible to the tensor cores and
@@ -179,35 +178,37 @@ __device__ void block_sum_store(double v, double* out) {
     if (threadIdx.x == 0) out[blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
 }
 
-// flux of one tile into the resident region: thread = element; per face the
-// neighbour's trace block (FB floats, 16-B aligned) is loaded with vector loads
-// issued together, then the own trace columns are read from TMEM.  Jump
-// (H-phase, avg = false) or average (E-phase); PEC faces use the ghost state.
+// flux of a tile's faces [f0, f0+2) into the resident region: thread =
+// element; the element's own trace block and its neighbour's (FB floats each,
+// 16-B aligned, written by the previous phase) are loaded with vector loads
+// issued together.  Jump (H-phase, avg = false) or average (E-phase); PEC
+// faces use the ghost state.  A2 column = (f - f0) FB + r.
 constexpr int kMaxFaceChunks = 11;   // FB / 4 for p <= 6
 
-__device__ void epi_flux(const TCArgs& A, uint32_t lane_tmem, int ct0, const float* nbr_tr, int64_t t,
-                         bool avg, float* a2) {
+__device__ void epi_flux(const TCArgs& A, int f0, const float* tr, int64_t t, bool avg, float* a2) {
     const TCDims& d = A.d;
     const int tid = threadIdx.x;
     const int FB = d.FB, nvalid = 2 * d.N2H, nchunk = FB / 4;
     const int4 nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
     const int32_t nbf[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
 #pragma unroll 1
-    for (int f = 0; f < 4; ++f) {
+    for (int f = f0; f < f0 + 2; ++f) {
         const int32_t nb = nbf[f];
         const float sh = A.sigma_hat[f];
-        float4 nv[kMaxFaceChunks];
-        if (nb >= 0) {
-            const float4* src = reinterpret_cast<const float4*>(nbr_tr + (size_t)(nb >> 2) * d.NT + (nb & 3) * FB);
+        const float4* own = reinterpret_cast<const float4*>(tr + (size_t)t * d.NT + f * FB);
+        const float4* src = reinterpret_cast<const float4*>(tr + (size_t)(nb >= 0 ? nb >> 2 : t) * d.NT +
+                                                            (nb >= 0 ? (nb & 3) : f) * FB);
+        float4 ov[kMaxFaceChunks], nv[kMaxFaceChunks];
 #pragma unroll
-            for (int c = 0; c < kMaxFaceChunks; ++c)
-                if (c < nchunk) nv[c] = src[c];
-        }
+        for (int c = 0; c < kMaxFaceChunks; ++c)
+            if (c < nchunk) {
+                ov[c] = own[c];
+                nv[c] = src[c];
+            }
 #pragma unroll
         for (int c = 0; c < kMaxFaceChunks; ++c) {
             if (c >= nchunk) break;
-            float v[4];
-            tc::tmem_ld4(lane_tmem + (uint32_t)(ct0 + f * FB + 4 * c), v[0], v[1], v[2], v[3]);
+            const float v[4] = {ov[c].x, ov[c].y, ov[c].z, ov[c].w};
             const float n4[4] = {nv[c].x, nv[c].y, nv[c].z, nv[c].w};
             float o[4];
 #pragma unroll
@@ -221,7 +222,7 @@ __device__ void epi_flux(const TCArgs& A, uint32_t lane_tmem, int ct0, const flo
                     o[q] = avg ? sh * v[q] : -sh * v[q];
                 }
             }
-            *reinterpret_cast<float4*>(a2 + ((size_t)((f * FB >> 2) + c) * kTcRows + tid) * 4) =
+            *reinterpret_cast<float4*>(a2 + ((size_t)(((f - f0) * FB >> 2) + c) * kTcRows + tid) * 4) =
                 make_float4(o[0], o[1], o[2], o[3]);
         }
     }
@@ -241,13 +242,12 @@ __device__ void epi_traces(const TCArgs& A, uint32_t lane_tmem, int ct0, float* 
 
 // The update epilogue: per batch of up to 16 coefficients (48 values) the old
 // field values are loaded first (12 float4, one per 4 values), then the 48
-// accumulator columns, then r = sgn * D, delta = s G^{-1} r per coefficient.
-// `Op` applies the per-coefficient update and the energy partial.
+// accumulator columns; `op` applies the per-coefficient update (and energy
+// partial); the new values are stored back to the tiled field in HBM.
 template <typename Op>
-__device__ void epi_update(uint32_t lane_tmem, float* field_tile, float* a3, int N, int K, Op op) {
+__device__ void epi_update(uint32_t lane_tmem, float* field_tile, int N, Op op) {
     const int tid = threadIdx.x;
     float4* F4 = reinterpret_cast<float4*>(field_tile);
-    float4* A4 = reinterpret_cast<float4*>(a3);
     const int ngroups = (N + 3) / 4;
 #pragma unroll 1
     for (int g0 = 0; g0 < ngroups; g0 += 4) {
@@ -268,12 +268,8 @@ __device__ void epi_update(uint32_t lane_tmem, float* field_tile, float* a3, int
         }
 #pragma unroll
         for (int q = 0; q < 12; ++q)
-            if (q < nq) {
-                F4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
-                A4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
-            }
+            if (q < nq) F4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
     }
-    for (int kc = 3 * ngroups; kc < K / 4; ++kc) A4[(size_t)kc * kTcRows + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // split an output range of up to 2 x 256 columns into MMAs (N <= 256)
@@ -290,218 +286,163 @@ __device__ void add_mmas(GemmDesc& G, int row0, int n, uint32_t dcol) {
     }
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_phase_H(TCArgs A, double dt, double a_lo, double c_out, int energy) {
+// make this thread's generic-proxy global stores visible to later bulk copies
+__device__ __forceinline__ void fence_global_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// One phase on every tile: IS_H = H-phase (update H from E), else E-phase.
+//   GEMM1  D = in * Curl^T                 (in = E for the H-phase, H for the E-phase)
+//   2 x    flux of two faces -> A2,  D += A2 * Lift^T
+//   update out (= H or E) in HBM, FP32 energy partial
+//   GEMM3  D = out_new * Tr^T  (A streamed back from L2) -> trace buffer of `out`
+template <bool IS_H>
+__global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double a_lo, double c_out, int energy) {
     extern __shared__ __align__(1024) uint8_t smem[];
     Ctl* ctl = reinterpret_cast<Ctl*>(smem);
     uint8_t* ring = smem + kHead;
     float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
     const int tid = threadIdx.x, warp = tid >> 5;
     const TCDims d = A.d;
-    setup(ctl, warp);
+    const int Kin = IS_H ? d.KE : d.KH, Kout = IS_H ? d.KH : d.KE;
+    const int Nout = IS_H ? d.NC : d.NCE, Nfield = IS_H ? d.NH : d.NE;
+    const float* in = IS_H ? A.E : A.H;
+    float* out = IS_H ? A.H : A.E;
+    const float* tr_in = IS_H ? A.trE : A.trH;
+    float* tr_out = IS_H ? A.trH : A.trE;
+    const float* Bc = IS_H ? A.B1H : A.B1E;
+    const float* Bl = IS_H ? A.BliftH : A.BliftE;
+    const float* Bt = IS_H ? A.BtrH : A.BtrE;
+    double* part = IS_H ? A.partH : A.partE;
+    setup(ctl, warp, A.tmem_cols);
     const uint32_t tmem = ctl->tmem;
     const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t g = 0, done_cnt = 0;
     double eacc = 0.0;
+    const int half_chunks = (2 * d.FB) / 8;
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
-        // GEMM1: curl and own E traces
+        // GEMM1: curl (H-phase) or curl^T (E-phase) of the input field
         if (tid == 0) {
             GemmDesc G{};
-            G.gA = A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4;
-            G.gB = A.B1H;
-            G.brows = d.NC + d.NT;
-            G.nk = d.KE / 8;
-            add_mmas(G, 0, d.NC, 0);
-            add_mmas(G, d.NC, d.NT, (uint32_t)d.NC);
+            G.gA = in + (size_t)tile * (Kin / 4) * kTcRows * 4;
+            G.gB = Bc;
+            G.brows = Nout;
+            G.nk = Kin / 8;
+            add_mmas(G, 0, Nout, 0);
             if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        epi_flux(A, lane_tmem, d.NC, A.trE, t, false, r2);
-        epilogue_barrier();
-        // GEMM2: D_c += flux * LiftH^T
-        if (tid == 0) {
-            GemmDesc G{};
-            G.sA = tc::smem_u32(r2);
-            G.gB = A.BliftH;
-            G.brows = d.NC;
-            G.nk = d.NT / 8;
-            G.acc_first = 1;
-            add_mmas(G, 0, d.NC, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+        // flux and lift, two faces at a time
+        for (int h = 0; h < 2; ++h) {
+            epi_flux(A, 2 * h, tr_in, t, !IS_H, r2);
+            epilogue_barrier();
+            if (tid == 0) {
+                GemmDesc G{};
+                G.sA = tc::smem_u32(r2);
+                G.gB = Bl + (size_t)h * half_chunks * Nout * 8;
+                G.brows = Nout;
+                G.nk = half_chunks;
+                G.acc_first = 1;
+                add_mmas(G, 0, Nout, 0);
+                if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+            }
+            if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
+            __syncthreads();
+            if (ctl->abort) break;
         }
-        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
-        __syncthreads();
         if (ctl->abort) break;
-        // update: H += dt/mu G^{-1} r, r = -s_T D_c.  The element's energy
-        // partial is summed in FP32 (FP64 is scarce on this GPU) and added to
-        // the FP64 per-thread sum once per element.
+        // update of the output field
         {
             const double* gg = A.geo + t * kGeoStride;
             const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
                         gi4 = (float)gg[4], gi5 = (float)gg[5];
             const float G0 = (float)gg[6], G1 = (float)gg[7], G2 = (float)gg[8], G3 = (float)gg[9],
                         G4 = (float)gg[10], G5 = (float)gg[11];
-            const double mu = gg[kGeoMu];
-            const float sT = (float)gg[kGeoSign];
-            const float s = (float)(dt * gg[kGeoInvMu]);
+            const double mat = IS_H ? gg[kGeoMu] : gg[kGeoEps];
+            const float sT = IS_H ? -(float)gg[kGeoSign] : (float)gg[kGeoSign];   // r = -s_T D (H), s_T D (E)
+            const float s = (float)(dt * (IS_H ? gg[kGeoInvMu] : gg[kGeoInvEps]));
             const float co = (float)c_out, alo = (float)a_lo;
             float eloc = 0.f;
-            epi_update(lane_tmem, A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4, r2, d.NH, d.KH,
+            epi_update(lane_tmem, out + (size_t)tile * (Kout / 4) * kTcRows * 4, Nfield,
                        [&](float* h, const float* dd) {
-                           const float r0 = -sT * dd[0], r1 = -sT * dd[1], r2v = -sT * dd[2];
+                           const float r0 = sT * dd[0], r1 = sT * dd[1], r2v = sT * dd[2];
                            const float d0 = s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
                            const float d1 = s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
                            const float d2 = s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
-                           if (energy) {
-                               const float l0 = h[0] - alo * d0, l1 = h[1] - alo * d1, l2 = h[2] - alo * d2;
-                               const float u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
-                               eloc += l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
-                                       l2 * (G2 * u0 + G4 * u1 + G5 * u2);
+                           if (IS_H) {
+                               // staggered pair (H_lo, H_hi) of the modified energy
+                               if (energy) {
+                                   const float l0 = h[0] - alo * d0, l1 = h[1] - alo * d1, l2 = h[2] - alo * d2;
+                                   const float u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
+                                   eloc += l0 * (G0 * u0 + G1 * u1 + G2 * u2) + l1 * (G1 * u0 + G3 * u1 + G4 * u2) +
+                                           l2 * (G2 * u0 + G4 * u1 + G5 * u2);
+                               }
+                               h[0] += co * d0;
+                               h[1] += co * d1;
+                               h[2] += co * d2;
+                           } else {
+                               h[0] += d0;
+                               h[1] += d1;
+                               h[2] += d2;
+                               if (energy) {
+                                   const float x0 = h[0], x1 = h[1], x2 = h[2];
+                                   eloc += x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
+                                           x2 * (G2 * x0 + G4 * x1 + G5 * x2);
+                               }
                            }
-                           h[0] += co * d0;
-                           h[1] += co * d1;
-                           h[2] += co * d2;
                        });
-            eacc += 0.5 * mu * (double)eloc;
+            eacc += 0.5 * mat * (double)eloc;
         }
+        fence_global_async();
         epilogue_barrier();
-        // GEMM3: traces of the new H for the E-phase
+        // GEMM3: traces of the updated field for the other phase (A read back from L2)
         if (tid == 0) {
             GemmDesc G{};
-            G.sA = tc::smem_u32(r2);
-            G.gB = A.BtrH;
+            G.gA = out + (size_t)tile * (Kout / 4) * kTcRows * 4;
+            G.gB = Bt;
             G.brows = d.NT;
-            G.nk = d.KH / 8;
-            add_mmas(G, 0, d.NT, (uint32_t)d.NC);
+            G.nk = Kout / 8;
+            add_mmas(G, 0, d.NT, 0);
             if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        epi_traces(A, lane_tmem, d.NC, A.trH, t);
+        epi_traces(A, lane_tmem, 0, tr_out, t);
         epilogue_barrier();
     }
     if (ctl->abort && tid == 0) record_error(A.err);
-    if (energy) block_sum_store(eacc, A.partH);
-    teardown(ctl, warp);
-}
-
-__global__ void __launch_bounds__(128, 1) k_tc_phase_E(TCArgs A, double dt, int energy) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    Ctl* ctl = reinterpret_cast<Ctl*>(smem);
-    uint8_t* ring = smem + kHead;
-    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const TCDims d = A.d;
-    setup(ctl, warp);
-    const uint32_t tmem = ctl->tmem;
-    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t g = 0, done_cnt = 0;
-    double eacc = 0.0;
-    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
-        const int64_t t = (int64_t)tile * kTcRows + tid;
-        if (tid == 0) {
-            GemmDesc G{};
-            G.gA = A.H + (size_t)tile * (d.KH / 4) * kTcRows * 4;
-            G.gB = A.B1E;
-            G.brows = d.NCE + d.NT;
-            G.nk = d.KH / 8;
-            add_mmas(G, 0, d.NCE, 0);
-            add_mmas(G, d.NCE, d.NT, (uint32_t)d.NCE);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
-        }
-        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
-        __syncthreads();
-        if (ctl->abort) break;
-        epi_flux(A, lane_tmem, d.NCE, A.trH, t, true, r2);
-        epilogue_barrier();
-        if (tid == 0) {
-            GemmDesc G{};
-            G.sA = tc::smem_u32(r2);
-            G.gB = A.BliftE;
-            G.brows = d.NCE;
-            G.nk = d.NT / 8;
-            G.acc_first = 1;
-            add_mmas(G, 0, d.NCE, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
-        }
-        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
-        __syncthreads();
-        if (ctl->abort) break;
-        // update: E += dt/eps G^{-1} r, r = s_T D_c (energy partial as in the H-phase)
-        {
-            const double* gg = A.geo + t * kGeoStride;
-            const float gi0 = (float)gg[0], gi1 = (float)gg[1], gi2 = (float)gg[2], gi3 = (float)gg[3],
-                        gi4 = (float)gg[4], gi5 = (float)gg[5];
-            const float G0 = (float)gg[6], G1 = (float)gg[7], G2 = (float)gg[8], G3 = (float)gg[9],
-                        G4 = (float)gg[10], G5 = (float)gg[11];
-            const double eps = gg[kGeoEps];
-            const float sT = (float)gg[kGeoSign];
-            const float s = (float)(dt * gg[kGeoInvEps]);
-            float eloc = 0.f;
-            epi_update(lane_tmem, A.E + (size_t)tile * (d.KE / 4) * kTcRows * 4, r2, d.NE, d.KE,
-                       [&](float* e, const float* dd) {
-                           const float r0 = sT * dd[0], r1 = sT * dd[1], r2v = sT * dd[2];
-                           e[0] += s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
-                           e[1] += s * (gi1 * r0 + gi3 * r1 + gi4 * r2v);
-                           e[2] += s * (gi2 * r0 + gi4 * r1 + gi5 * r2v);
-                           if (energy) {
-                               const float x0 = e[0], x1 = e[1], x2 = e[2];
-                               eloc += x0 * (G0 * x0 + G1 * x1 + G2 * x2) + x1 * (G1 * x0 + G3 * x1 + G4 * x2) +
-                                       x2 * (G2 * x0 + G4 * x1 + G5 * x2);
-                           }
-                       });
-            eacc += 0.5 * eps * (double)eloc;
-        }
-        epilogue_barrier();
-        if (tid == 0) {
-            GemmDesc G{};
-            G.sA = tc::smem_u32(r2);
-            G.gB = A.BtrE;
-            G.brows = d.NT;
-            G.nk = d.KE / 8;
-            add_mmas(G, 0, d.NT, (uint32_t)d.NCE);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
-        }
-        if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
-        __syncthreads();
-        if (ctl->abort) break;
-        epi_traces(A, lane_tmem, d.NCE, A.trE, t);
-        epilogue_barrier();
-    }
-    if (ctl->abort && tid == 0) record_error(A.err);
-    if (energy) block_sum_store(eacc, A.partE);
-    teardown(ctl, warp);
+    if (energy) block_sum_store(eacc, part);
+    teardown(ctl, warp, A.tmem_cols);
 }
 
 // traces of E (which = 0, with the energy partials of E) or H (which = 1)
-__global__ void __launch_bounds__(128, 1) k_tc_traces(TCArgs A, int which) {
+__global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
     extern __shared__ __align__(1024) uint8_t smem[];
     Ctl* ctl = reinterpret_cast<Ctl*>(smem);
     uint8_t* ring = smem + kHead;
-    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
     const int tid = threadIdx.x, warp = tid >> 5;
     const TCDims d = A.d;
-    setup(ctl, warp);
+    setup(ctl, warp, A.tmem_cols);
     const uint32_t tmem = ctl->tmem;
     const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t g = 0, done_cnt = 0, load_cnt = 0;
+    uint32_t g = 0, done_cnt = 0;
     const int K = which == 0 ? d.KE : d.KH;
     const float* field = which == 0 ? A.E : A.H;
     double eacc = 0.0;
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
+        const float* ft = field + (size_t)tile * (K / 4) * kTcRows * 4;
         if (tid == 0) {
-            const uint32_t bytes = (uint32_t)(kTcRows * K * 4);
-            tc::mbar_expect_tx(&ctl->load, bytes);
-            tc::bulk_g2s(r2, field + (size_t)tile * (K / 4) * kTcRows * 4, bytes, &ctl->load);
+            GemmDesc G{};
+            G.gA = ft;
+            G.gB = which == 0 ? A.BtrE : A.BtrH;
+            G.brows = d.NT;
+            G.nk = K / 8;
+            add_mmas(G, 0, d.NT, 0);
+            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
-        if (!tc::mbar_wait(&ctl->load, load_cnt & 1u, kLimit)) ctl->abort = 1;
-        ++load_cnt;
-        __syncthreads();
-        if (ctl->abort) break;
         if (which == 0) {
             const double* gg = A.geo + t * kGeoStride;
             const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
@@ -509,32 +450,22 @@ __global__ void __launch_bounds__(128, 1) k_tc_traces(TCArgs A, int which) {
                 double x[3];
                 for (int m = 0; m < 3; ++m) {
                     const int k = 3 * a + m;
-                    x[m] = r2[((size_t)(k >> 2) * kTcRows + tid) * 4 + (k & 3)];
+                    x[m] = ft[((size_t)(k >> 2) * kTcRows + tid) * 4 + (k & 3)];
                 }
                 eacc += 0.5 * gg[kGeoEps] *
                         (x[0] * (G0 * x[0] + G1 * x[1] + G2 * x[2]) + x[1] * (G1 * x[0] + G3 * x[1] + G4 * x[2]) +
                          x[2] * (G2 * x[0] + G4 * x[1] + G5 * x[2]));
             }
         }
-        if (tid == 0) {
-            GemmDesc G{};
-            G.sA = tc::smem_u32(r2);
-            G.gB = which == 0 ? A.BtrE : A.BtrH;
-            G.brows = d.NT;
-            G.nk = K / 8;
-            add_mmas(G, 0, d.NT, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
-        }
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
         epi_traces(A, lane_tmem, 0, which == 0 ? A.trE : A.trH, t);
-        tc::tc_fence_before();
-        __syncthreads();   // r2 is overwritten by the next tile's load
+        epilogue_barrier();
     }
     if (ctl->abort && tid == 0) record_error(A.err);
     if (which == 0) block_sum_store(eacc, A.partE);
-    teardown(ctl, warp);
+    teardown(ctl, warp, A.tmem_cols);
 }
 
 // 1/2 (eps E, E) and 1/2 (mu H, H) partials of the tiled state
@@ -635,28 +566,36 @@ TCDims tc_dims(int NE, int NH, int N2H) {
     return d;
 }
 
+uint32_t tc_tmem_cols(const TCDims& d) {
+    const int need = std::max(std::max(d.NC, d.NCE), d.NT);
+    uint32_t c = 32;
+    while ((int)c < need) c <<= 1;
+    return c;
+}
+
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset) {
-    const int maxB = std::max(d.NC + d.NT, d.NCE + d.NT);
-    const uint32_t stage = (uint32_t)(kTcRows + maxB) * 32u;
-    const int maxK = std::max(std::max(d.KE, d.KH), d.NT);
-    const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)maxK * 4u;
+    const int maxB = std::max(std::max(d.NC, d.NCE), d.NT);
+    const uint32_t stage = (uint32_t)(kTcRows + maxB) * 32u;   // A slice (128 x 8) + B slice (rows x 8)
+    const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)(2 * d.FB) * 4u;   // flux of two faces
     *stage_bytes = stage;
     *r2_offset = kHead + kStages * stage;
-    // at least 116 KB so that one CTA (and its 512 TMEM columns) occupies an SM
-    return std::max<size_t>((size_t)kHead + kStages * stage + r2, 116 * 1024);
+    const size_t bytes = (size_t)kHead + kStages * stage + r2;
+    // with more than 256 TMEM columns a CTA must have its SM to itself: ask for
+    // enough shared memory that a second CTA cannot be resident
+    return tc_tmem_cols(d) > 256 ? std::max<size_t>(bytes, 116 * 1024) : bytes;
 }
 
 int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
     const size_t sm = smem_of(a);
-    if (set_smem((const void*)k_tc_phase_H, sm)) return -1;
-    k_tc_phase_H<<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
+    if (set_smem((const void*)k_tc_phase<true>, sm)) return -1;
+    k_tc_phase<true><<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s) {
     const size_t sm = smem_of(a);
-    if (set_smem((const void*)k_tc_phase_E, sm)) return -1;
-    k_tc_phase_E<<<grid, 128, sm, s>>>(a, dt, energy);
+    if (set_smem((const void*)k_tc_phase<false>, sm)) return -1;
+    k_tc_phase<false><<<grid, 128, sm, s>>>(a, dt, 0.0, 1.0, energy);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

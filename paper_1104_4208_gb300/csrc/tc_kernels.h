@@ -33,10 +33,10 @@ struct TCArgs {
     float* trH;                // [ntiles*128][NT]
     const double* geo;         // [ntiles*128][kGeoStride] (padding rows benign)
     const int32_t* nbr;        // [ntiles*128][4]
-    const float* B1H;          // [KE/4][NC+NT][4]   curl | E trace
+    const float* B1H;          // [KE/4][NC][4]      curl
     const float* BliftH;       // [NT/4][NC][4]
     const float* BtrH;         // [KH/4][NT][4]
-    const float* B1E;          // [KH/4][NCE+NT][4]  curl^T | H trace
+    const float* B1E;          // [KH/4][NCE][4]     curl^T
     const float* BliftE;       // [NT/4][NCE][4]
     const float* BtrE;         // [KE/4][NT][4]
     double* partE;             // [grid] energy partials, E part
@@ -44,10 +44,12 @@ struct TCArgs {
     int* err;                  // device error word (0 = ok)
     float sigma_hat[4];        // reference face orientation signs
     uint32_t stage_bytes;      // bytes of one ring stage
+    uint32_t tmem_cols;        // TMEM columns allocated per CTA (power of two)
     uint32_t r2_offset;        // offset of the resident tile region
 };
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset);
+uint32_t tc_tmem_cols(const TCDims& d);
 
 int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s);
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s);
