@@ -69,6 +69,10 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
         set_error("precision TC32 supports p <= 6");
         return DGM_ERR_UNSUPPORTED;
     }
+    if (tc_tmem_reach(d) > tc_tmem_cols(d)) {
+        set_error("TC32 epilogue would read past its TMEM allocation");
+        return DGM_ERR_UNSUPPORTED;
+    }
     if (P->opt.flux != DGM_FLUX_CENTRAL) {
         set_error("precision TC32 supports the central flux only");
         return DGM_ERR_UNSUPPORTED;

@@ -252,13 +252,18 @@ __device__ void epi_update(uint32_t lane_tmem, float* field_tile, int N, Op op) 
 #pragma unroll 1
     for (int g0 = 0; g0 < ngroups; g0 += 4) {
         const int nq = 3 * min(4, ngroups - g0);
+        // 16-column loads covering the batch's 4 nq columns only: the last one
+        // ends at the padded output width (a multiple of 16), never past the
+        // CTA's TMEM allocation
+        const int nld = (4 * nq + 15) / 16;
         float4 hv[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q)
             if (q < nq) hv[q] = F4[(size_t)(3 * g0 + q) * kTcRows + tid];
         float dd[48];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) tc::tmem_ld16(lane_tmem + (uint32_t)(12 * g0 + 16 * s), dd + 16 * s);
+        for (int s = 0; s < 3; ++s)
+            if (s < nld) tc::tmem_ld16(lane_tmem + (uint32_t)(12 * g0 + 16 * s), dd + 16 * s);
         float* h = reinterpret_cast<float*>(hv);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -571,6 +576,18 @@ uint32_t tc_tmem_cols(const TCDims& d) {
     uint32_t c = 32;
     while ((int)c < need) c <<= 1;
     return c;
+}
+
+uint32_t tc_tmem_reach(const TCDims& d) {
+    int reach = std::max(std::max(d.NC, d.NCE), d.NT);   // GEMM outputs and trace reads
+    for (int N : {d.NE, d.NH}) {                          // update epilogue batches
+        const int ngroups = (N + 3) / 4;
+        for (int g0 = 0; g0 < ngroups; g0 += 4) {
+            const int nq = 3 * std::min(4, ngroups - g0);
+            reach = std::max(reach, 12 * g0 + 16 * ((4 * nq + 15) / 16));
+        }
+    }
+    return (uint32_t)reach;
 }
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset) {

@@ -50,6 +50,8 @@ struct TCArgs {
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset);
 uint32_t tc_tmem_cols(const TCDims& d);
+// one past the highest TMEM column any GEMM or epilogue of the phase kernels touches
+uint32_t tc_tmem_reach(const TCDims& d);
 
 int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s);
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s);
