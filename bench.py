@@ -132,9 +132,11 @@ def measured_peak_hbm():
 
 def profile_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (sha256 recorded beside the numbers)."""
+    taken on the current kernel source (sha256 of the file that defines it,
+    recorded beside the numbers)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_1104_4208_gb300", "csrc", "kernels.cu")
+    src = os.path.join(ROOT, "paper_1104_4208_gb300", "csrc",
+                       "tc_kernels.cu" if kernel.startswith("k_tc") else "kernels.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(path):
