@@ -33,6 +33,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DoF-steps/s at p=4/6 (mixed vs FP64 plain, same GB300); % HBM roofline; err"
+DTYPE = {"tc32": "tf32", "tc16": "f16", "fp32": "f32", "fp64": "f64"}
+ARITH = {"tc32": "fp32 state, TF32 tensor-core operators (tcgen05), fp32 accumulate, fp64 geometry and energy",
+         "tc16": "fp32 state with fp16 operand copies, fp16 tables and trace buffers, fp16 tensor-core operators "
+                 "(tcgen05 kind::f16), fp32 accumulate, fp64 geometry and energy",
+         "fp32": "fp32 state and CUDA-core arithmetic, fp64 geometry and energy",
+         "fp64": "fp64 throughout"}
 UNIT = "DoF-steps/s"
 
 
@@ -51,7 +57,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="planewave_n32_p6")
-    ap.add_argument("--precision", default="tc32", choices=["tc32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tc16", choices=["tc16", "tc32", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="nonzero: also run the FP64 path over the same steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
@@ -318,7 +324,8 @@ def run_gpu(args, rank, world, local):
     bytes_E = w.nt * (b * (6 * NE + 3 * NH) + 64 + 20)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
-    kpre = "k_tc_phase" if args.precision == "tc32" else "k_phase"
+    tcp = args.precision in ("tc32", "tc16")
+    kpre = "k_tc_phase" if tcp else "k_phase"
     if stats.h_phase_ms >= stats.e_phase_ms:
         kname, kbytes, kms = kpre + "_H", bytes_H, tH
     else:
@@ -327,7 +334,7 @@ def run_gpu(args, rank, world, local):
     achieved = kbytes / (kms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
-            "traffic": profile_traffic(kname if args.precision == "tc32" else f"{kname}<{'float' if b == 4 else 'double'}>"),
+            "traffic": profile_traffic(f"{kname}/{args.precision}" if tcp else f"{kname}<{'float' if b == 4 else 'double'}>"),
             "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
             "share": {kpre + "_H": stats.h_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms),
                       kpre + "_E": stats.e_phase_ms / (stats.h_phase_ms + stats.e_phase_ms + stats.other_ms)}}
@@ -389,15 +396,12 @@ def run_gpu(args, rank, world, local):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": {"tc32": "tf32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+               "dtype": DTYPE[args.precision], "data": "synthetic",
                "config": {"workload": w.name, "tets": w.nt, "p": w.p, "dof": dofs, "precision": args.precision,
                           "flux": "central", "dt": dt, "parallelism": f"replicas{world}",
                           "l2": "state larger than L2 (no flush needed)",
                           "state_mb": dofs * (8 if args.precision == 'fp64' else 4) / 1e6,
-                          "arithmetic": {"tc32": "fp32 state, TF32 tensor-core operators (tcgen05), fp32 accumulate, "
-                                                 "fp64 geometry and energy",
-                                         "fp32": "fp32 state and CUDA-core arithmetic, fp64 geometry and energy",
-                                         "fp64": "fp64 throughout"}[args.precision]},
+                          "arithmetic": ARITH[args.precision]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks,
                "err": {"l2_rel_E_vs_analytic": err, "l2_rel_E_initial_projection": err0,
@@ -460,7 +464,7 @@ def run_batched(args, rank, world, local):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": {"tc32": "tf32", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+               "dtype": DTYPE[args.precision], "data": "synthetic",
                "config": {"workload": "batched_64", "runs": len(solvers), "dof_total": dofs,
                           "precision": args.precision, "graph": "one CUDA graph, one branch per run",
                           "l2": "runs small, partly L2 resident; no flush (time loop reuses state)"},

@@ -73,8 +73,12 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
  * elements on the tensor cores with TF32 operands (10-bit mantissa) and FP32
  * accumulation; one rounded table serves C_h and C_h^T, so the discrete
  * operator stays skew; geometry in double, per-element energy partials in float
- * summed in double.  Central flux, p <= 6. */
-enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2 };
+ * summed in double.  Central flux, p <= 6.
+ * TC16: as TC32, but the tensor-core operands are fp16 (also 10-bit mantissa,
+ * range 6e-8 .. 65504): fp16 copies of E and H written next to the float
+ * state, fp16 tables and face-trace buffers, fp16 MMAs with K = 16 and FP32
+ * accumulation; the update and the energy use the float state. */
+enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2, DGM_PREC_TC16 = 3 };
 
 typedef struct dgm_options {
     int flux;           /* dgm_flux */

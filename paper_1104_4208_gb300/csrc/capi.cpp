@@ -297,7 +297,8 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         set_error("dgm_problem_create: alpha0 must be positive");
         return DGM_ERR_INVALID_ARG;
     }
-    if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32 && o.precision != DGM_PREC_TC32) {
+    if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32 && o.precision != DGM_PREC_TC32 &&
+        o.precision != DGM_PREC_TC16) {
         set_error("dgm_problem_create: unknown precision");
         return DGM_ERR_INVALID_ARG;
     }
@@ -338,7 +339,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaSetDevice"));
     const size_t rs = P->fp32 ? sizeof(float) : sizeof(double);
     const int64_t nE = m.nt * 3 * P->NE, nH = m.nt * 3 * P->NH;
-    const bool tc = o.precision == DGM_PREC_TC32;
+    const bool tc = o.precision == DGM_PREC_TC32 || o.precision == DGM_PREC_TC16;
     cudaError_t e;
     if (!tc) {
         if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc E"));
@@ -1007,6 +1008,10 @@ void set_state_ptrs(dgm_problem* P, void* E, void* H) {
     if (P->tc) {
         P->tca.E = (float*)E;
         P->tca.H = (float*)H;
+        if (!P->tca.d.f16) {   // TF32: the operand is the state itself; fp16 copies follow via the refresh
+            P->tca.Eop = E;
+            P->tca.Hop = H;
+        }
     } else if (P->fp32) {
         P->kf.E = (float*)E;
         P->kf.H = (float*)H;

@@ -33,14 +33,21 @@ float round_tf32(float x) {
     return r;
 }
 
+// One table in the MMA operand layout [K/VPC][rows][VPC].  TF32 values are
+// rounded here; fp16 values are rounded on the device when the fp32 staging
+// copy is converted.
 struct TableWriter {
     std::vector<float>& buf;
     size_t base;
     int rows;
+    int vpc;
     void put(int row, int k, double v) {
-        buf[base + ((size_t)(k / 4) * rows + row) * 4 + (k % 4)] = round_tf32((float)v);
+        const float x = (float)v;
+        buf[base + ((size_t)(k / vpc) * rows + row) * vpc + (k % vpc)] = vpc == 4 ? round_tf32(x) : x;
     }
 };
+
+size_t round_up(size_t n, size_t a) { return (n + a - 1) / a * a; }
 
 // (curl E)_m[b] = sum_{a, m'} curl_entry(b, m, a, m') E_{m'}[a]  (Sec. 3.2.2: curl from gradients)
 double curl_entry(const RefTables& t, int b, int m, int a, int mp) {
@@ -62,38 +69,49 @@ int cuda_err(cudaError_t e, const char* what) {
 int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
                     const std::vector<int32_t>& nbr) {
     const RefTables& T = P->tab;
-    const TCDims d = tc_dims(T.NE, T.NH, T.N2H);
+    const bool f16 = P->opt.precision == DGM_PREC_TC16;
+    const char* name = f16 ? "TC16" : "TC32";
+    const TCDims d = tc_dims(T.NE, T.NH, T.N2H, f16);
     uint32_t stage = 0, r2 = 0;
     const size_t smem = tc_smem_bytes(d, &stage, &r2);
     if (P->p > 6 || smem + 1024 > 227 * 1024 || tc_tmem_cols(d) > 512) {
-        set_error("precision TC32 supports p <= 6");
+        set_error(std::string("precision ") + name + " supports p <= 6");
         return DGM_ERR_UNSUPPORTED;
     }
     if (tc_tmem_reach(d) > tc_tmem_cols(d)) {
-        set_error("TC32 epilogue would read past its TMEM allocation");
+        set_error(std::string(name) + " epilogue would read past its TMEM allocation");
         return DGM_ERR_UNSUPPORTED;
     }
     if (P->opt.flux != DGM_FLUX_CENTRAL) {
-        set_error("precision TC32 supports the central flux only");
+        set_error(std::string("precision ") + name + " supports the central flux only");
         return DGM_ERR_UNSUPPORTED;
     }
     const int64_t ntiles = (m.nt + kTcRows - 1) / kTcRows;
     const int64_t nrow = ntiles * kTcRows;
-    // sizes in floats
-    const size_t nE = (size_t)nrow * d.KE, nH = (size_t)nrow * d.KH, nTr = (size_t)nrow * d.NT;
-    const size_t b1h = (size_t)d.KE * d.NC, blh = (size_t)d.NT * d.NC, bth = (size_t)d.KH * d.NT;
-    const size_t b1e = (size_t)d.KH * d.NCE, ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KE * d.NT;
+    const size_t esz = f16 ? 2 : 4;   // bytes per operand value
+    // one allocation, regions 1 KB aligned: fp32 state E, H; (fp16) operand
+    // copies of E, H; trace buffers; tables
+    const size_t bE = round_up((size_t)nrow * d.KE * 4, 1024), bH = round_up((size_t)nrow * d.KH * 4, 1024);
+    const size_t bEo = f16 ? round_up((size_t)nrow * d.KEo * esz, 1024) : 0;
+    const size_t bHo = f16 ? round_up((size_t)nrow * d.KHo * esz, 1024) : 0;
+    const size_t bTr = round_up((size_t)nrow * d.NT * esz, 1024);
+    // table sizes in values
+    const size_t b1h = (size_t)d.KEo * d.NC, blh = (size_t)d.NT * d.NC, bth = (size_t)d.KHo * d.NT;
+    const size_t b1e = (size_t)d.KHo * d.NCE, ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KEo * d.NT;
     const size_t ntab = b1h + blh + bth + b1e + ble + bte;
-    const size_t total = nE + nH + 2 * nTr + ntab;
+    const size_t o_state = 0, o_Eo = bE + bH, o_Ho = o_Eo + bEo, o_tr = o_Ho + bHo, o_tab = o_tr + 2 * bTr;
+    const size_t total = o_tab + ntab * esz;
     cudaError_t e;
-    if ((e = cudaMalloc(&P->dTc, total * sizeof(float))) != cudaSuccess) return cuda_err(e, "alloc");
-    if ((e = cudaMemset(P->dTc, 0, (nE + nH + 2 * nTr) * sizeof(float))) != cudaSuccess) return cuda_err(e, "memset");
+    if ((e = cudaMalloc(&P->dTc, total)) != cudaSuccess) return cuda_err(e, "alloc");
+    if ((e = cudaMemset(P->dTc, 0, o_tab)) != cudaSuccess) return cuda_err(e, "memset");
+    uint8_t* base8 = static_cast<uint8_t*>(P->dTc);
 
     std::vector<float> tab(ntab, 0.0f);
     const size_t o_b1h = 0, o_blh = o_b1h + b1h, o_bth = o_blh + blh, o_b1e = o_bth + bth, o_ble = o_b1e + b1e,
                  o_bte = o_ble + ble;
-    TableWriter B1H{tab, o_b1h, d.NC}, BLH{tab, o_blh, d.NC}, BTH{tab, o_bth, d.NT};
-    TableWriter B1E{tab, o_b1e, d.NCE}, BLE{tab, o_ble, d.NCE}, BTE{tab, o_bte, d.NT};
+    const int V = d.VPC;
+    TableWriter B1H{tab, o_b1h, d.NC, V}, BLH{tab, o_blh, d.NC, V}, BTH{tab, o_bth, d.NT, V};
+    TableWriter B1E{tab, o_b1e, d.NCE, V}, BLE{tab, o_ble, d.NCE, V}, BTE{tab, o_bte, d.NT, V};
     const int NE = T.NE, NH = T.NH, N2H = T.N2H;
     for (int b = 0; b < NH; ++b)
         for (int mo = 0; mo < 3; ++mo)
@@ -129,10 +147,20 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
                     }
                 }
             }
-    float* base = (float*)P->dTc;
-    float* dtab = base + nE + nH + 2 * nTr;
-    if ((e = cudaMemcpy(dtab, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_err(e, "tables");
+    uint8_t* dtab = base8 + o_tab;
+    if (!f16) {
+        if ((e = cudaMemcpy(dtab, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_err(e, "tables");
+    } else {
+        // fp32 staging copy, rounded to fp16 on the device
+        float* stage32 = nullptr;
+        if ((e = cudaMalloc(&stage32, ntab * sizeof(float))) != cudaSuccess) return cuda_err(e, "alloc tables");
+        e = cudaMemcpy(stage32, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && tc_launch_to_half(stage32, dtab, ntab, 0)) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(stage32);
+        if (e != cudaSuccess) return cuda_err(e, "tables");
+    }
 
     // padded geometry and topology (padding elements: identity metric, PEC faces, zero fields)
     std::vector<double> g2((size_t)nrow * kGeoStride, 0.0);
@@ -166,18 +194,20 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     A.nt = m.nt;
     A.ntiles = (int)ntiles;
     A.d = d;
-    A.E = base;
-    A.H = base + nE;
-    A.trE = base + nE + nH;
-    A.trH = base + nE + nH + nTr;
+    A.E = reinterpret_cast<float*>(base8 + o_state);
+    A.H = reinterpret_cast<float*>(base8 + bE);
+    A.Eop = f16 ? static_cast<void*>(base8 + o_Eo) : static_cast<void*>(A.E);
+    A.Hop = f16 ? static_cast<void*>(base8 + o_Ho) : static_cast<void*>(A.H);
+    A.trE = base8 + o_tr;
+    A.trH = base8 + o_tr + bTr;
     A.geo = P->dTcGeo;
     A.nbr = P->dTcNbr;
-    A.B1H = dtab + o_b1h;
-    A.BliftH = dtab + o_blh;
-    A.BtrH = dtab + o_bth;
-    A.B1E = dtab + o_b1e;
-    A.BliftE = dtab + o_ble;
-    A.BtrE = dtab + o_bte;
+    A.B1H = dtab + o_b1h * esz;
+    A.BliftH = dtab + o_blh * esz;
+    A.BtrH = dtab + o_bth * esz;
+    A.B1E = dtab + o_b1e * esz;
+    A.BliftE = dtab + o_ble * esz;
+    A.BtrE = dtab + o_bte * esz;
     A.partE = part;
     A.partH = part + P->tc_grid;
     A.err = P->dErr;

@@ -6,24 +6,30 @@
 // as a GEMM on the 5th-generation tensor cores:
 //
 //   H-phase (tile of E, H):
-//     GEMM1  D_c = E * Curl^T,  D_t = E * TrE^T        (K = 3 N3(p))
-//     flux   a~ = -sigma_hat (J - J_nbr)/2   (PEC: -sigma_hat J), J from D_t,
+//     GEMM1  D = E * Curl^T                                (K = 3 N3(p))
+//     flux   a~ = -sigma_hat (J - J_nbr)/2   (PEC: -sigma_hat J), J and
 //            J_nbr from the trace buffer the previous E-phase wrote
-//     GEMM2  D_c += a~ * LiftH^T                        (K = 8 N2(p-1))
-//     update H += dt/mu G^{-1} (-s_T D_c), FP64 energy partial
-//     GEMM3  D_t = H_new * TrH^T -> H trace buffer (for the E-phase)
+//     GEMM2  D += a~ * LiftH^T                             (K = 8 N2(p-1))
+//     update H += dt/mu G^{-1} (-s_T D), energy partial
+//     GEMM3  D = H_new * TrH^T -> H trace buffer (for the E-phase)
 //   E-phase: the transposed operators with {{H}}, the same rounded numbers, so
 //   the discrete operator stays exactly skew.
 //
-// Operands are TF32 (fp32 storage, 10-bit mantissa in the multiplier), the
-// accumulators FP32 in tensor memory (TMEM), one thread per element in the
-// epilogues (element = TMEM lane).  State tiles and reference tables are
+// Two operand types share the code (template parameter OP): TF32 (the fp32
+// state itself is the operand; the multiplier uses 10 mantissa bits, K = 8
+// per MMA) and FP16 (an fp16 copy of each field, written by the update
+// epilogue next to the fp32 state, fp16 tables and trace buffers; K = 16 per
+// MMA, so a ring slot of the same bytes carries twice the K range).  The
+// state, the update and the energy stay fp32 in both.  The accumulators are
+// FP32 in tensor memory (TMEM), one thread per element in the epilogues
+// (element = TMEM lane).  State tiles and reference tables are
 // stored in global memory in the MMA's shared-memory layout, so each K slice
 // arrives with one bulk asynchronous copy into a 4-stage ring; one thread
 // issues copies and MMAs, mbarriers track both.  Every wait is bounded: on
 // timeout the kernel records an error code, lets its copies drain, frees its
 // tensor memory and returns.
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +51,54 @@ constexpr int kErrTimeout = 1;
 
 int padto(int x, int m) { return (x + m - 1) / m * m; }
 
+// Operand types: values per 16-byte chunk, the MMA, and chunk <-> floats.
+struct OpTf32 {
+    using T = float;
+    static constexpr int VPC = 4;
+    static constexpr int MAXC = 11;   // 16-byte chunks of a face block for p <= 6 (FB = 44)
+    static __device__ __forceinline__ void unpack(const uint4& c, float* v) {
+        v[0] = __uint_as_float(c.x);
+        v[1] = __uint_as_float(c.y);
+        v[2] = __uint_as_float(c.z);
+        v[3] = __uint_as_float(c.w);
+    }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int n, uint32_t acc) {
+        tc::mma_tf32(d, a, b, tc::idesc_tf32(kTcRows, n), acc);
+    }
+    static __device__ __forceinline__ uint4 pack(const float* v) {
+        return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+    }
+};
+
+struct OpF16 {
+    using T = __half;
+    static constexpr int VPC = 8;
+    static constexpr int MAXC = 6;    // FB = 48
+    static __device__ __forceinline__ void unpack(const uint4& c, float* v) {
+        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, int n, uint32_t acc) {
+        tc::mma_f16(d, a, b, tc::idesc_f16(kTcRows, n), acc);
+    }
+    static __device__ __forceinline__ uint4 pack(const float* v) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            memcpy(&w[i], &h, 4);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+
 struct Ctl {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -55,11 +109,11 @@ struct Ctl {
 };
 
 struct GemmDesc {
-    const float* gA;   // A K-slices in global memory (tile base) or nullptr: A resident in shared memory
-    uint32_t sA;       // shared address of the resident A tile
-    const float* gB;   // B K-slices in global memory, [K/4][brows][4]
+    const uint8_t* gA;   // A K-slices in global memory (tile base) or nullptr: A resident in shared memory
+    uint32_t sA;         // shared address of the resident A tile
+    const uint8_t* gB;   // B K-slices in global memory, [K/VPC][brows][VPC]
     int brows;
-    int nk;            // number of 8-wide K steps
+    int nk;            // number of MMA K-steps (32 bytes of every row each)
     int nmma;          // MMAs per K step (B row ranges)
     int row0[3];
     int n[3];
@@ -67,7 +121,9 @@ struct GemmDesc {
     int acc_first;     // accumulate onto D from the first step
 };
 
-// Producer + MMA issuer (thread 0).  g counts ring uses across GEMMs.
+// Producer + MMA issuer (thread 0).  g counts ring uses across GEMMs.  A
+// K-step is 32 bytes of every row of A (4 KB) and of B, whatever the type.
+template <typename OP>
 __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_t& g, const GemmDesc& G,
                           uint32_t tmem) {
     const uint32_t a_bytes = G.gA ? (uint32_t)(kTcRows * 32) : 0u;
@@ -81,8 +137,8 @@ __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_
         if (use > 0 && !tc::mbar_wait(&ctl->empty[st], (use - 1) & 1u, kLimit)) return false;
         uint8_t* sp = ring + (size_t)st * stage_bytes;
         tc::mbar_expect_tx(&ctl->full[st], a_bytes + b_bytes);
-        if (G.gA) tc::bulk_g2s(sp, G.gA + (size_t)c * kTcRows * 8, a_bytes, &ctl->full[st]);
-        tc::bulk_g2s(sp + a_bytes, G.gB + (size_t)c * G.brows * 8, b_bytes, &ctl->full[st]);
+        if (G.gA) tc::bulk_g2s(sp, G.gA + (size_t)c * kTcRows * 32, a_bytes, &ctl->full[st]);
+        tc::bulk_g2s(sp + a_bytes, G.gB + (size_t)c * G.brows * 32, b_bytes, &ctl->full[st]);
         ++produced;
         return true;
     };
@@ -97,8 +153,7 @@ __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_
         const uint32_t baddr = tc::smem_u32(sp + a_bytes);
         for (int j = 0; j < G.nmma; ++j) {
             const uint64_t bd = tc::sdesc(baddr + (uint32_t)G.row0[j] * 16u, (uint32_t)G.brows * 16u, 128u);
-            tc::mma_tf32(tmem + G.dcol[j], ad, bd, tc::idesc_tf32(kTcRows, G.n[j]),
-                         (c > 0 || G.acc_first) ? 1u : 0u);
+            OP::mma(tmem + G.dcol[j], ad, bd, G.n[j], (c > 0 || G.acc_first) ? 1u : 0u);
         }
         tc::mma_commit(&ctl->empty[st]);
         ++consumed;
@@ -179,26 +234,29 @@ __device__ void block_sum_store(double v, double* out) {
 }
 
 // flux of a tile's faces [f0, f0+2) into the resident region: thread =
-// element; the element's own trace block and its neighbour's (FB floats each,
-// 16-B aligned, written by the previous phase) are loaded with vector loads
-// issued together.  Jump (H-phase, avg = false) or average (E-phase); PEC
-// faces use the ghost state.  A2 column = (f - f0) FB + r.
-constexpr int kMaxFaceChunks = 11;   // FB / 4 for p <= 6
-
-__device__ void epi_flux(const TCArgs& A, int f0, const float* tr, int64_t t, bool avg, float* a2) {
+// element; the element's own trace block and its neighbour's (FB values each,
+// 16-B aligned, written by the previous phase in the operand type) are loaded
+// with 16-byte loads issued together.  Jump (H-phase, avg = false) or average
+// (E-phase) formed in fp32 and rounded to the operand type; PEC faces use the
+// ghost state.  A2 column = (f - f0) FB + r.
+template <typename OP>
+__device__ void epi_flux(const TCArgs& A, int f0, const typename OP::T* tr, int64_t t, bool avg,
+                         typename OP::T* a2) {
+    constexpr int V = OP::VPC, kMaxFaceChunks = OP::MAXC;
     const TCDims& d = A.d;
     const int tid = threadIdx.x;
-    const int FB = d.FB, nvalid = 2 * d.N2H, nchunk = FB / 4;
+    const int FB = d.FB, nvalid = 2 * d.N2H, nchunk = FB / V;
     const int4 nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
     const int32_t nbf[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
+    uint4* A2 = reinterpret_cast<uint4*>(a2);
 #pragma unroll 1
     for (int f = f0; f < f0 + 2; ++f) {
         const int32_t nb = nbf[f];
         const float sh = A.sigma_hat[f];
-        const float4* own = reinterpret_cast<const float4*>(tr + (size_t)t * d.NT + f * FB);
-        const float4* src = reinterpret_cast<const float4*>(tr + (size_t)(nb >= 0 ? nb >> 2 : t) * d.NT +
-                                                            (nb >= 0 ? (nb & 3) : f) * FB);
-        float4 ov[kMaxFaceChunks], nv[kMaxFaceChunks];
+        const uint4* own = reinterpret_cast<const uint4*>(tr + (size_t)t * d.NT + f * FB);
+        const uint4* src = reinterpret_cast<const uint4*>(tr + (size_t)(nb >= 0 ? nb >> 2 : t) * d.NT +
+                                                          (nb >= 0 ? (nb & 3) : f) * FB);
+        uint4 ov[kMaxFaceChunks], nv[kMaxFaceChunks];
 #pragma unroll
         for (int c = 0; c < kMaxFaceChunks; ++c)
             if (c < nchunk) {
@@ -208,12 +266,12 @@ __device__ void epi_flux(const TCArgs& A, int f0, const float* tr, int64_t t, bo
 #pragma unroll
         for (int c = 0; c < kMaxFaceChunks; ++c) {
             if (c >= nchunk) break;
-            const float v[4] = {ov[c].x, ov[c].y, ov[c].z, ov[c].w};
-            const float n4[4] = {nv[c].x, nv[c].y, nv[c].z, nv[c].w};
-            float o[4];
+            float v[V], n4[V], o[V];
+            OP::unpack(ov[c], v);
+            OP::unpack(nv[c], n4);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = 4 * c + q;
+            for (int q = 0; q < V; ++q) {
+                const int r = V * c + q;
                 if (r >= nvalid) {
                     o[q] = 0.f;
                 } else if (nb >= 0) {
@@ -222,30 +280,35 @@ __device__ void epi_flux(const TCArgs& A, int f0, const float* tr, int64_t t, bo
                     o[q] = avg ? sh * v[q] : -sh * v[q];
                 }
             }
-            *reinterpret_cast<float4*>(a2 + ((size_t)(((f - f0) * FB >> 2) + c) * kTcRows + tid) * 4) =
-                make_float4(o[0], o[1], o[2], o[3]);
+            A2[(size_t)((f - f0) * nchunk + c) * kTcRows + tid] = OP::pack(o);
         }
     }
 }
 
-// trace columns of D_t -> trace buffer row of element t
-__device__ void epi_traces(const TCArgs& A, uint32_t lane_tmem, int ct0, float* tr, int64_t t) {
+// trace columns of D -> trace buffer row of element t (operand type)
+template <typename OP>
+__device__ void epi_traces(const TCArgs& A, uint32_t lane_tmem, typename OP::T* tr, int64_t t) {
+    constexpr int V = OP::VPC;
     const int NT = A.d.NT;
-    float4* row = reinterpret_cast<float4*>(tr + (size_t)t * NT);
+    uint4* row = reinterpret_cast<uint4*>(tr + (size_t)t * NT);
     for (int j0 = 0; j0 < NT; j0 += 16) {
         float v[16];
-        tc::tmem_ld16(lane_tmem + (uint32_t)(ct0 + j0), v);
+        tc::tmem_ld16(lane_tmem + (uint32_t)j0, v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) row[(j0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 16 / V; ++q) row[j0 / V + q] = OP::pack(v + V * q);
     }
 }
 
 // The update epilogue: per batch of up to 16 coefficients (48 values) the old
-// field values are loaded first (12 float4, one per 4 values), then the 48
+// fp32 field values are loaded first (12 float4, one per 4 values), then the
 // accumulator columns; `op` applies the per-coefficient update (and energy
-// partial); the new values are stored back to the tiled field in HBM.
-template <typename Op>
-__device__ void epi_update(uint32_t lane_tmem, float* field_tile, int N, Op op) {
+// partial); the new values are stored back to the tiled fp32 field in HBM and,
+// with fp16 operands, to the fp16 operand copy of row length Kop (8 values per
+// 16-byte chunk; values past the batch in its last chunk are padding, stored
+// as 0; a batch of whole 4-coefficient groups may reach past Kop, those values
+// are padding too and are not stored).
+template <typename OP, typename Op>
+__device__ void epi_update(uint32_t lane_tmem, float* field_tile, typename OP::T* op_tile, int N, int Kop, Op op) {
     const int tid = threadIdx.x;
     float4* F4 = reinterpret_cast<float4*>(field_tile);
     const int ngroups = (N + 3) / 4;
@@ -274,6 +337,19 @@ __device__ void epi_update(uint32_t lane_tmem, float* field_tile, int N, Op op) 
 #pragma unroll
         for (int q = 0; q < 12; ++q)
             if (q < nq) F4[(size_t)(3 * g0 + q) * kTcRows + tid] = hv[q];
+        if constexpr (OP::VPC == 8) {
+            // values [12 g0, 12 g0 + 4 nq) -> fp16 chunks from 12 g0 / 8 on
+            uint4* O = reinterpret_cast<uint4*>(op_tile);
+            const int nval = min(4 * nq, Kop - 12 * g0), nch = (nval + 7) / 8, ch0 = 3 * g0 / 2;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (i >= nch) break;
+                float w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) w[q] = 8 * i + q < nval ? h[8 * i + q] : 0.f;
+                O[(size_t)(ch0 + i) * kTcRows + tid] = OP::pack(w);
+            }
+        }
     }
 }
 
@@ -299,58 +375,62 @@ __device__ __forceinline__ void fence_global_async() { asm volatile("fence.proxy
 //   2 x    flux of two faces -> A2,  D += A2 * Lift^T
 //   update out (= H or E) in HBM, FP32 energy partial
 //   GEMM3  D = out_new * Tr^T  (A streamed back from L2) -> trace buffer of `out`
-template <bool IS_H>
+template <bool IS_H, typename OP>
 __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double a_lo, double c_out, int energy) {
+    using T = typename OP::T;
     extern __shared__ __align__(1024) uint8_t smem[];
     Ctl* ctl = reinterpret_cast<Ctl*>(smem);
     uint8_t* ring = smem + kHead;
-    float* r2 = reinterpret_cast<float*>(smem + A.r2_offset);
+    T* r2 = reinterpret_cast<T*>(smem + A.r2_offset);
     const int tid = threadIdx.x, warp = tid >> 5;
     const TCDims d = A.d;
-    const int Kin = IS_H ? d.KE : d.KH, Kout = IS_H ? d.KH : d.KE;
+    const int Kin = IS_H ? d.KEo : d.KHo;    // operand row length of the input field
+    const int Kout = IS_H ? d.KH : d.KE;     // fp32 row length of the output field
+    const int Kop = IS_H ? d.KHo : d.KEo;    // operand row length of the output field
     const int Nout = IS_H ? d.NC : d.NCE, Nfield = IS_H ? d.NH : d.NE;
-    const float* in = IS_H ? A.E : A.H;
+    const uint8_t* in = static_cast<const uint8_t*>(IS_H ? A.Eop : A.Hop);
     float* out = IS_H ? A.H : A.E;
-    const float* tr_in = IS_H ? A.trE : A.trH;
-    float* tr_out = IS_H ? A.trH : A.trE;
-    const float* Bc = IS_H ? A.B1H : A.B1E;
-    const float* Bl = IS_H ? A.BliftH : A.BliftE;
-    const float* Bt = IS_H ? A.BtrH : A.BtrE;
+    T* out_op = static_cast<T*>(IS_H ? A.Hop : A.Eop);   // TF32: the fp32 field itself
+    const T* tr_in = static_cast<const T*>(IS_H ? A.trE : A.trH);
+    T* tr_out = static_cast<T*>(IS_H ? A.trH : A.trE);
+    const uint8_t* Bc = static_cast<const uint8_t*>(IS_H ? A.B1H : A.B1E);
+    const uint8_t* Bl = static_cast<const uint8_t*>(IS_H ? A.BliftH : A.BliftE);
+    const uint8_t* Bt = static_cast<const uint8_t*>(IS_H ? A.BtrH : A.BtrE);
     double* part = IS_H ? A.partH : A.partE;
     setup(ctl, warp, A.tmem_cols);
     const uint32_t tmem = ctl->tmem;
     const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t g = 0, done_cnt = 0;
     double eacc = 0.0;
-    const int half_chunks = (2 * d.FB) / 8;
+    const int half_steps = d.FB / OP::VPC;   // MMA K-steps of two faces (2 FB values)
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
         // GEMM1: curl (H-phase) or curl^T (E-phase) of the input field
         if (tid == 0) {
             GemmDesc G{};
-            G.gA = in + (size_t)tile * (Kin / 4) * kTcRows * 4;
+            G.gA = in + (size_t)tile * Kin * kTcRows * sizeof(T);
             G.gB = Bc;
             G.brows = Nout;
-            G.nk = Kin / 8;
+            G.nk = Kin / (2 * OP::VPC);
             add_mmas(G, 0, Nout, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+            if (!ring_gemm<OP>(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
         // flux and lift, two faces at a time
         for (int h = 0; h < 2; ++h) {
-            epi_flux(A, 2 * h, tr_in, t, !IS_H, r2);
+            epi_flux<OP>(A, 2 * h, tr_in, t, !IS_H, r2);
             epilogue_barrier();
             if (tid == 0) {
                 GemmDesc G{};
                 G.sA = tc::smem_u32(r2);
-                G.gB = Bl + (size_t)h * half_chunks * Nout * 8;
+                G.gB = Bl + (size_t)h * half_steps * Nout * 32;
                 G.brows = Nout;
-                G.nk = half_chunks;
+                G.nk = half_steps;
                 G.acc_first = 1;
                 add_mmas(G, 0, Nout, 0);
-                if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+                if (!ring_gemm<OP>(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
             }
             if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
             __syncthreads();
@@ -369,7 +449,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
             const float s = (float)(dt * (IS_H ? gg[kGeoInvMu] : gg[kGeoInvEps]));
             const float co = (float)c_out, alo = (float)a_lo;
             float eloc = 0.f;
-            epi_update(lane_tmem, out + (size_t)tile * (Kout / 4) * kTcRows * 4, Nfield,
+            epi_update<OP>(lane_tmem, out + (size_t)tile * Kout * kTcRows, out_op + (size_t)tile * Kop * kTcRows, Nfield, Kop,
                        [&](float* h, const float* dd) {
                            const float r0 = sT * dd[0], r1 = sT * dd[1], r2v = sT * dd[2];
                            const float d0 = s * (gi0 * r0 + gi1 * r1 + gi2 * r2v);
@@ -404,17 +484,17 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
         // GEMM3: traces of the updated field for the other phase (A read back from L2)
         if (tid == 0) {
             GemmDesc G{};
-            G.gA = out + (size_t)tile * (Kout / 4) * kTcRows * 4;
+            G.gA = reinterpret_cast<const uint8_t*>(out_op + (size_t)tile * Kop * kTcRows);
             G.gB = Bt;
             G.brows = d.NT;
-            G.nk = Kout / 8;
+            G.nk = Kop / (2 * OP::VPC);
             add_mmas(G, 0, d.NT, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+            if (!ring_gemm<OP>(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        epi_traces(A, lane_tmem, 0, tr_out, t);
+        epi_traces<OP>(A, lane_tmem, tr_out, t);
         epilogue_barrier();
     }
     if (ctl->abort && tid == 0) record_error(A.err);
@@ -422,8 +502,13 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
     teardown(ctl, warp, A.tmem_cols);
 }
 
-// traces of E (which = 0, with the energy partials of E) or H (which = 1)
+// traces of E (which = 0, with the energy partials of E) or H (which = 1).
+// With fp16 operands each thread first rewrites its element's fp16 copy of
+// the field from the fp32 state (the state may have been changed from
+// outside: import, sources, checkpoints); the copy then feeds the GEMM.
+template <typename OP>
 __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
+    using T = typename OP::T;
     extern __shared__ __align__(1024) uint8_t smem[];
     Ctl* ctl = reinterpret_cast<Ctl*>(smem);
     uint8_t* ring = smem + kHead;
@@ -433,20 +518,36 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
     const uint32_t tmem = ctl->tmem;
     const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t g = 0, done_cnt = 0;
-    const int K = which == 0 ? d.KE : d.KH;
+    const int K = which == 0 ? d.KE : d.KH, Ko = which == 0 ? d.KEo : d.KHo;
     const float* field = which == 0 ? A.E : A.H;
+    T* field_op = static_cast<T*>(which == 0 ? A.Eop : A.Hop);
     double eacc = 0.0;
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
-        const float* ft = field + (size_t)tile * (K / 4) * kTcRows * 4;
+        const float* ft = field + (size_t)tile * K * kTcRows;
+        T* fo = field_op + (size_t)tile * Ko * kTcRows;
+        if constexpr (OP::VPC == 8) {
+            uint4* O = reinterpret_cast<uint4*>(fo);
+            for (int q = 0; q < Ko / 8; ++q) {
+                float w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k = 8 * q + i;
+                    w[i] = k < K ? ft[((size_t)(k >> 2) * kTcRows + tid) * 4 + (k & 3)] : 0.f;
+                }
+                O[(size_t)q * kTcRows + tid] = OP::pack(w);
+            }
+            fence_global_async();
+            __syncthreads();
+        }
         if (tid == 0) {
             GemmDesc G{};
-            G.gA = ft;
-            G.gB = which == 0 ? A.BtrE : A.BtrH;
+            G.gA = reinterpret_cast<const uint8_t*>(fo);
+            G.gB = static_cast<const uint8_t*>(which == 0 ? A.BtrE : A.BtrH);
             G.brows = d.NT;
-            G.nk = K / 8;
+            G.nk = Ko / (2 * OP::VPC);
             add_mmas(G, 0, d.NT, 0);
-            if (!ring_gemm(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
+            if (!ring_gemm<OP>(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
         if (which == 0) {
             const double* gg = A.geo + t * kGeoStride;
@@ -465,7 +566,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
         if (!wait_done(ctl, done_cnt)) ctl->abort = 1;
         __syncthreads();
         if (ctl->abort) break;
-        epi_traces(A, lane_tmem, 0, which == 0 ? A.trE : A.trH, t);
+        epi_traces<OP>(A, lane_tmem, static_cast<T*>(which == 0 ? A.trE : A.trH), t);
         epilogue_barrier();
     }
     if (ctl->abort && tid == 0) record_error(A.err);
@@ -546,6 +647,11 @@ __global__ void k_tc_unpack(const float* __restrict__ src, double* __restrict__ 
     }
 }
 
+__global__ void k_to_half(const float* __restrict__ src, __half* __restrict__ dst, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
 int set_smem(const void* fn, size_t bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess ? 0 : -1;
 }
@@ -557,14 +663,18 @@ size_t smem_of(const TCArgs& a) {
 
 }  // namespace
 
-TCDims tc_dims(int NE, int NH, int N2H) {
+TCDims tc_dims(int NE, int NH, int N2H, bool f16) {
     TCDims d;
     d.NE = NE;
     d.NH = NH;
     d.N2H = N2H;
+    d.f16 = f16 ? 1 : 0;
+    d.VPC = f16 ? 8 : 4;
     d.KE = padto(3 * NE, 24);
     d.KH = padto(3 * NH, 24);
-    d.FB = padto(2 * N2H, 4);
+    d.KEo = f16 ? padto(3 * NE, 16) : d.KE;
+    d.KHo = f16 ? padto(3 * NH, 16) : d.KH;
+    d.FB = padto(2 * N2H, d.VPC);   // whole 16-byte chunks, two faces = whole K-steps
     d.NT = 4 * d.FB;
     d.NC = padto(12 * ((NH + 3) / 4), 16);
     d.NCE = padto(12 * ((NE + 3) / 4), 16);
@@ -593,7 +703,7 @@ uint32_t tc_tmem_reach(const TCDims& d) {
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset) {
     const int maxB = std::max(std::max(d.NC, d.NCE), d.NT);
     const uint32_t stage = (uint32_t)(kTcRows + maxB) * 32u;   // A slice (128 x 8) + B slice (rows x 8)
-    const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)(2 * d.FB) * 4u;   // flux of two faces
+    const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)(2 * d.FB) * (d.f16 ? 2u : 4u);   // flux of two faces
     *stage_bytes = stage;
     *r2_offset = kHead + kStages * stage;
     const size_t bytes = (size_t)kHead + kStages * stage + r2;
@@ -602,24 +712,44 @@ size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset
     return tc_tmem_cols(d) > 256 ? std::max<size_t>(bytes, 116 * 1024) : bytes;
 }
 
-int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
+namespace {
+
+template <bool IS_H, typename OP>
+int launch_phase(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
     const size_t sm = smem_of(a);
-    if (set_smem((const void*)k_tc_phase<true>, sm)) return -1;
-    k_tc_phase<true><<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
+    if (set_smem((const void*)k_tc_phase<IS_H, OP>, sm)) return -1;
+    k_tc_phase<IS_H, OP><<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename OP>
+int launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
+    const size_t sm = smem_of(a);
+    if (set_smem((const void*)k_tc_traces<OP>, sm)) return -1;
+    k_tc_traces<OP><<<grid, 128, sm, s>>>(a, which);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
+    return a.d.f16 ? launch_phase<true, OpF16>(a, grid, dt, a_lo, c_out, energy, s)
+                   : launch_phase<true, OpTf32>(a, grid, dt, a_lo, c_out, energy, s);
 }
 
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s) {
-    const size_t sm = smem_of(a);
-    if (set_smem((const void*)k_tc_phase<false>, sm)) return -1;
-    k_tc_phase<false><<<grid, 128, sm, s>>>(a, dt, 0.0, 1.0, energy);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return a.d.f16 ? launch_phase<false, OpF16>(a, grid, dt, 0.0, 1.0, energy, s)
+                   : launch_phase<false, OpTf32>(a, grid, dt, 0.0, 1.0, energy, s);
 }
 
 int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
-    const size_t sm = smem_of(a);
-    if (set_smem((const void*)k_tc_traces, sm)) return -1;
-    k_tc_traces<<<grid, 128, sm, s>>>(a, which);
+    return a.d.f16 ? launch_traces<OpF16>(a, grid, which, s) : launch_traces<OpTf32>(a, grid, which, s);
+}
+
+int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s) {
+    if (n == 0) return 0;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    k_to_half<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(dst), n);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, TF32 operands, FP32 accumulation) phase kernels.
+// Tensor-core (tcgen05) phase kernels: TF32 or FP16 operands, FP32 accumulation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,35 +10,42 @@ namespace dgm {
 
 constexpr int kTcRows = 128;   // elements per tile = MMA M
 
-// Dimensions of the tensor-core path for one p (all counts in fp32 values).
+// Dimensions of the tensor-core path for one p and operand type.  State
+// values are fp32; operand values are fp32 (TF32, 4 per 16-byte chunk) or
+// fp16 (8 per chunk).
 struct TCDims {
     int NE, NH, N2H;
-    int KE, KH;      // padded state row lengths (multiples of 24): E, H
-    int FB;          // trace columns per face: 2 N2(p-1) padded to 4 (16-byte blocks)
-    int NT;          // face-trace columns 4 FB (multiple of 16)
+    int f16;         // operands in fp16 (else TF32)
+    int VPC;         // operand values per 16-byte chunk: 4 (TF32) or 8 (fp16)
+    int KE, KH;      // padded fp32 state row lengths (multiples of 24): E, H
+    int KEo, KHo;    // padded operand row lengths (whole MMA K-steps of 2 VPC): E, H
+    int FB;          // trace columns per face: 2 N2(p-1) padded to VPC
+    int NT;          // face-trace columns 4 FB
     int NC;          // H-output columns (12 ceil(NH/4) padded to 16)
     int NCE;         // E-output columns (12 ceil(NE/4) padded to 16)
 };
 
-TCDims tc_dims(int NE, int NH, int N2H);
+TCDims tc_dims(int NE, int NH, int N2H, bool f16);
 
 struct TCArgs {
     int64_t nt;
     int ntiles;
     TCDims d;
-    float* E;                  // [ntiles][KE/4][128][4]
-    float* H;                  // [ntiles][KH/4][128][4]
-    float* trE;                // [ntiles*128][NT] tangential E traces (degree <= p-1 face modes),
-                               // column f FB + i N2(p-1) + g
-    float* trH;                // [ntiles*128][NT]
+    float* E;                  // fp32 state [ntiles][KE/4][128][4]
+    float* H;                  // fp32 state [ntiles][KH/4][128][4]
+    void* Eop;                 // MMA operand copy of E [ntiles][KEo/VPC][128][VPC] (TF32: E itself)
+    void* Hop;                 // MMA operand copy of H (TF32: H itself)
+    void* trE;                 // [ntiles*128][NT] tangential E traces (degree <= p-1 face modes),
+                               // column f FB + i N2(p-1) + g, operand type
+    void* trH;                 // [ntiles*128][NT]
     const double* geo;         // [ntiles*128][kGeoStride] (padding rows benign)
     const int32_t* nbr;        // [ntiles*128][4]
-    const float* B1H;          // [KE/4][NC][4]      curl
-    const float* BliftH;       // [NT/4][NC][4]
-    const float* BtrH;         // [KH/4][NT][4]
-    const float* B1E;          // [KH/4][NCE][4]     curl^T
-    const float* BliftE;       // [NT/4][NCE][4]
-    const float* BtrE;         // [KE/4][NT][4]
+    const void* B1H;           // [KEo/VPC][NC][VPC]    curl
+    const void* BliftH;        // [NT/VPC][NC][VPC]
+    const void* BtrH;          // [KHo/VPC][NT][VPC]
+    const void* B1E;           // [KHo/VPC][NCE][VPC]   curl^T
+    const void* BliftE;        // [NT/VPC][NCE][VPC]
+    const void* BtrE;          // [KEo/VPC][NT][VPC]
     double* partE;             // [grid] energy partials, E part
     double* partH;             // [grid] energy partials, H part
     int* err;                  // device error word (0 = ok)
@@ -55,12 +62,15 @@ uint32_t tc_tmem_reach(const TCDims& d);
 
 int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s);
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s);
-// traces (and, for E, the energy partials of E) of the current field: which = 0 E, 1 H
+// traces (and, for E, the energy partials of E) of the current field: which = 0 E, 1 H;
+// with fp16 operands the operand copy of the field is refreshed from the state first
 int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s);
 // energy partials of the state (no staggering)
 int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s);
 // canonical (or orthonormal) [t][3][N] doubles <-> tiled floats, scaled by nrm[a] (import) / 1/nrm[a] (export)
 int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s);
 int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s);
+// fp32 -> fp16, round to nearest even (tables of the fp16 operand path)
+int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s);
 
 }  // namespace dgm

@@ -1,15 +1,17 @@
 // Inline-PTX wrappers for the sm_103a tensor-core path: tcgen05 (TMEM
-// allocation, MMA with TF32 operands from shared memory and FP32 accumulators
-// in tensor memory, loads from tensor memory), mbarriers and bulk async copies.
+// allocation, MMA with TF32 or FP16 operands from shared memory and FP32
+// accumulators in tensor memory, loads from tensor memory), mbarriers and bulk
+// async copies.
 //
 // Shared-memory operand layout used throughout ("core-matrix" K-major layout
 // without swizzle): a tile of R rows x K fp32 values is stored as
 // [K/4][R][4] -- 16-byte rows of 4 consecutive K values, the R rows of one
-// 4-wide K slice contiguous.  An 8-row x 16-byte core matrix is then 128
-// contiguous bytes; neighbouring core matrices are 128 B apart along the rows
-// (stride byte offset, SBO) and R*16 B apart along K (leading byte offset,
-// LBO).  Global arrays that feed the MMA are stored in the same order, so a
-// bulk copy of a K slice lands directly in MMA layout.
+// 4-wide K slice contiguous (fp16 operands: [K/8][R][8], the same bytes).  An
+// 8-row x 16-byte core matrix is then 128 contiguous bytes; neighbouring core
+// matrices are 128 B apart along the rows (stride byte offset, SBO) and R*16 B
+// apart along K (leading byte offset, LBO).  Global arrays that feed the MMA
+// are stored in the same order, so a bulk copy of a K slice lands directly in
+// MMA layout.
 #pragma once
 
 #include <cstdint>
@@ -107,6 +109,23 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 // Instruction descriptor of kind::tf32: D fp32, A = B = tf32, both K-major, dense.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with fp16 A and B (same type on both
+// sides), fp32 D, both K-major, dense.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T with fp16 operands (K = 16), one thread.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

@@ -18,7 +18,7 @@ class Solver:
         self.nt, self.nfaces, self.nboundary = capi.dgm_mesh_info(self.mesh)
         opt = capi.dgm_default_options()
         opt.precision = {"fp64": capi.DGM_PREC_FP64, "fp32": capi.DGM_PREC_FP32,
-                         "tc32": capi.DGM_PREC_TC32}[precision]
+                         "tc32": capi.DGM_PREC_TC32, "tc16": capi.DGM_PREC_TC16}[precision]
         opt.flux = {"central": capi.DGM_FLUX_CENTRAL, "stabilized": capi.DGM_FLUX_STABILIZED}[flux]
         opt.alpha0 = alpha0
         eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.nt,))
