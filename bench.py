@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     return ap.parse_args()
 
 
@@ -304,6 +305,10 @@ def run_gpu(args, rank, world, local):
     maps, xh = project_initial(S, w, torch, q1d)
     err0 = l2_rel_error(S, w, torch, q1d, maps, xh, 0.0)
     dt = w.dt
+    tune = None
+    if not args.no_autotune:   # launch configuration picked by measurement (fields unchanged)
+        cfg, tms, ch = S.autotune(3)
+        tune = {"per_sm": cfg, "ms_per_step": [round(x, 4) for x in tms], "chosen": cfg[ch]}
 
     with ClockSampler(local) as clk:
         ms, stats, W = timed_run(S, torch, dt, args.steps, args.warmup)
@@ -401,7 +406,9 @@ def run_gpu(args, rank, world, local):
                           "flux": "central", "dt": dt, "parallelism": f"replicas{world}",
                           "l2": "state larger than L2 (no flush needed)",
                           "state_mb": dofs * (8 if args.precision == 'fp64' else 4) / 1e6,
-                          "arithmetic": ARITH[args.precision]},
+                          "arithmetic": ARITH[args.precision],
+                          "launch": ({"autotuned": tune, "unit": "CTAs per SM" if tcp else "blocks per SM"}
+                                     if tune else "default")},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks,
                "err": {"l2_rel_E_vs_analytic": err, "l2_rel_E_initial_projection": err0,

@@ -165,6 +165,21 @@ int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* 
  * start vector is a fixed pseudo-random H.  Blocks; allocates temporaries. */
 int dgm_estimate_dt(dgm_problem* prob, int iters, double* rho, double* dt_max);
 
+/* Launch-configuration autotuner of the per-step kernels (the time loop of
+ * Sec. 3).  Each candidate configuration is timed (CUDA events, `steps` steps
+ * after one warm-up step) on this problem's own fields with dt = 0, which
+ * leaves the fields unchanged; the fastest is kept for all later calls.
+ * Candidates: CUDA-core kernels (FP64, FP32) -- 4, 8, 16 or 24 blocks per SM;
+ * tensor-core kernels (TC32, TC16) -- 1 or 2 CTAs per SM (2 only where the
+ * TMEM columns and shared memory of a CTA allow it).  Every candidate computes
+ * each element with the same operations, so the fields of later runs do not
+ * depend on the choice; the energy's last bits can (block partial sums).
+ * Outputs (nullable): *ncand (<= DGM_AUTOTUNE_MAX), per candidate its
+ * configuration value (blocks or CTAs per SM) and ms per step, and the index
+ * of the chosen one.  Errors: DGM_ERR_INVALID_ARG for steps < 1. */
+#define DGM_AUTOTUNE_MAX 8
+int dgm_autotune(dgm_problem* prob, int steps, int* ncand, int* cand_config, double* cand_ms, int* chosen);
+
 /* Point dipole current J(x, t) = dir delta(x - xs) f(t) with the zero-mean
  * pulse f(t) = -amp ((t - t0)/tau) exp(-((t - t0)/tau)^2): the E-equation of
  * Sec. 2 gains -(J, e), applied in every E-kick of dgm_run (and of the forward

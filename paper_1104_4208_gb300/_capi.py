@@ -70,6 +70,7 @@ _SIGS = {
     "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
     "dgm_energy": ([_vp, _pd], C.c_int),
     "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
+    "dgm_autotune": ([_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_set_materials": ([_vp, _pd, _pd], C.c_int),
     "dgm_set_source": ([_vp, _pd, _pd, C.c_double, C.c_double, C.c_double], C.c_int),
     "dgm_set_time": ([_vp, C.c_double], C.c_int),
@@ -207,6 +208,20 @@ def dgm_estimate_dt(prob, iters=50):
     rho, dt = C.c_double(), C.c_double()
     _check(_lib.dgm_estimate_dt(prob, int(iters), C.byref(rho), C.byref(dt)))
     return rho.value, dt.value
+
+
+AUTOTUNE_MAX = 8
+
+
+def dgm_autotune(prob, steps=5):
+    """-> (configs, ms_per_step, chosen index): blocks (CUDA-core) or CTAs
+    (tensor-core) per SM of each candidate, its time per step, the one kept."""
+    n = C.c_int()
+    cfg = (C.c_int * AUTOTUNE_MAX)()
+    ms = (C.c_double * AUTOTUNE_MAX)()
+    ch = C.c_int()
+    _check(_lib.dgm_autotune(prob, int(steps), C.byref(n), cfg, ms, C.byref(ch)))
+    return list(cfg[:n.value]), list(ms[:n.value]), ch.value
 
 
 def dgm_set_source(prob, xs, direction, t0, tau, amp):

@@ -26,6 +26,10 @@ using dgm::set_error;
 
 namespace {
 
+// largest blocks per SM the autotuner tries for the CUDA-core kernels (the
+// allocation-free energy entry point holds at most 4096 block partial sums)
+constexpr int kAutotuneMaxBlocksPerSm = 24;
+
 int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? DGM_ERR_OOM : DGM_ERR_CUDA;
@@ -330,6 +334,8 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     const int wpb = dgm::phase_warps_per_block();
     const int64_t want = (m.nt + wpb - 1) / wpb;
     P->grid = (int)std::min<int64_t>(want, (int64_t)ctx->num_sms * 16);
+    // partial sums sized for the largest grid the autotuner may choose
+    P->grid_cap = (int)std::min<int64_t>(want, (int64_t)ctx->num_sms * kAutotuneMaxBlocksPerSm);
 
     auto fail = [&](int code) {
         free_problem(P);
@@ -407,7 +413,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     }
     if ((e = cudaMalloc(&P->dStage, std::max(std::max(nE, nH), nK) * sizeof(double))) != cudaSuccess)
         return fail(cuda_fail(e, "alloc staging"));
-    if ((e = cudaMalloc(&P->dPartials, (size_t)P->grid * sizeof(double))) != cudaSuccess)
+    if ((e = cudaMalloc(&P->dPartials, (size_t)std::max(P->grid, P->grid_cap) * sizeof(double))) != cudaSuccess)
         return fail(cuda_fail(e, "alloc partials"));
 
     // geometry records
@@ -921,6 +927,70 @@ int axpby(const StateView& v, int64_t n, double a, const void* x, double b, void
 }
 
 }  // namespace
+
+int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, double* cand_ms, int* chosen_out) {
+    if (!P || steps < 1) {
+        set_error("dgm_autotune: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const int sms = P->ctx->num_sms;
+    std::vector<int> cand;
+    if (P->tc) {
+        cand.push_back(1);
+        if (P->tc_grid_cap > sms) cand.push_back(2);   // two CTAs per SM allowed
+    } else {
+        for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b);
+    }
+    auto apply = [&](int c) {
+        if (P->tc) {
+            P->tc_grid = std::min(P->tc_grid_cap, sms * c);
+            P->tca.partH = P->tca.partE + P->tc_grid;   // the reduction sums 2 tc_grid contiguous partials
+        } else {
+            P->grid = std::min(P->grid_cap, sms * c);
+        }
+    };
+    const int keep_grid = P->grid, keep_tc = P->tc_grid;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DGM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "dgm_autotune events");
+    }
+    std::vector<double> ms(cand.size(), 0.0);
+    int rc = DGM_OK;
+    for (size_t i = 0; i < cand.size() && !rc; ++i) {
+        apply(cand[i]);
+        // one warm-up step, then `steps` timed steps, dt = 0 (fields unchanged)
+        for (int n = 0; n <= steps && !rc; ++n) {
+            if (n == 1 && cudaEventRecord(e0, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "event");
+            if (!rc) rc = phase_E(P, 0.0, 0);
+            if (!rc) rc = phase_H(P, 0.0, 0.0, 1.0, nullptr, 0);
+        }
+        if (!rc && cudaEventRecord(e1, 0) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "event");
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "autotune run");
+        float t = 0.f;
+        if (!rc) cudaEventElapsedTime(&t, e0, e1);
+        ms[i] = t / steps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc && P->tc) rc = dgm::tc_check_error(P);
+    if (rc) {
+        P->grid = keep_grid;
+        P->tc_grid = keep_tc;
+        if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
+        return rc;
+    }
+    const int best = (int)(std::min_element(ms.begin(), ms.end()) - ms.begin());
+    apply(cand[best]);
+    if (ncand_out) *ncand_out = (int)cand.size();
+    for (size_t i = 0; i < cand.size(); ++i) {
+        if (cand_config) cand_config[i] = cand[i];
+        if (cand_ms) cand_ms[i] = ms[i];
+    }
+    if (chosen_out) *chosen_out = best;
+    return DGM_OK;
+}
 
 int dgm_estimate_dt(dgm_problem* P, int iters, double* rho_out, double* dt_out) {
     if (!P || iters < 1) {

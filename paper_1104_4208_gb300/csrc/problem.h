@@ -26,7 +26,8 @@ struct dgm_problem {
     int64_t nt = 0, nfaces = 0;
     int NE = 0, NH = 0, N2E = 0, N2H = 0;
     bool fp32 = false;
-    int grid = 0;
+    int grid = 0;                        // blocks of the CUDA-core phase kernels (autotuned)
+    int grid_cap = 0;                    // largest grid the partial sums are sized for
     void* dE = nullptr;
     void* dH = nullptr;
     void* dTables = nullptr;
@@ -51,9 +52,10 @@ struct dgm_problem {
     double* dFaceGeo = nullptr;          // [nfaces][kFaceGeoStride]
     int32_t* dFid = nullptr;             // [nt][4]
     double* dNrmF = nullptr;             // [N2E] ||psi_g||
-    // tensor-core path (precision TC32)
+    // tensor-core path (precisions TC32, TC16)
     bool tc = false;
-    int tc_grid = 0;
+    int tc_grid = 0;                     // CTAs of the tensor-core kernels (autotuned)
+    int tc_grid_cap = 0;                 // largest tc_grid the partial sums are sized for
     dgm::TCArgs tca{};
     void* dTc = nullptr;                 // one allocation: tiled state, traces, tables, partials
     double* dTcGeo = nullptr;

@@ -185,10 +185,11 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     const uint32_t tcols = tc_tmem_cols(d);
     const int per_sm = (tcols <= 256 && 2 * (smem + 1024) <= 227 * 1024) ? 2 : 1;
     P->tc_grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+    P->tc_grid_cap = P->tc_grid;   // the autotuner may lower it to one CTA per SM
     double* part = nullptr;
-    if ((e = cudaMalloc(&part, 2 * (size_t)P->tc_grid * sizeof(double))) != cudaSuccess)
+    if ((e = cudaMalloc(&part, 2 * (size_t)P->tc_grid_cap * sizeof(double))) != cudaSuccess)
         return cuda_err(e, "alloc partials");
-    cudaMemset(part, 0, 2 * (size_t)P->tc_grid * sizeof(double));
+    cudaMemset(part, 0, 2 * (size_t)P->tc_grid_cap * sizeof(double));
 
     TCArgs& A = P->tca;
     A.nt = m.nt;
@@ -209,7 +210,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     A.BliftE = dtab + o_ble * esz;
     A.BtrE = dtab + o_bte * esz;
     A.partE = part;
-    A.partH = part + P->tc_grid;
+    A.partH = part + P->tc_grid;   // contiguous with partE for the reduction; moves with tc_grid
     A.err = P->dErr;
     for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
     A.stage_bytes = stage;

@@ -47,6 +47,11 @@ class Solver:
         capi.dgm_run(self.prob, dt, nsteps, stream, out)
         return out
 
+    def autotune(self, steps=5):
+        """Time the launch-configuration candidates on this problem (fields
+        unchanged) and keep the fastest; -> (configs, ms_per_step, chosen)."""
+        return capi.dgm_autotune(self.prob, steps)
+
     def energy(self):
         return capi.dgm_energy(self.prob)
 

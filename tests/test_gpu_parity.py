@@ -555,3 +555,37 @@ def test_batch_graph_matches_individual_runs(capi):
     for pair, _ in made:
         for S in pair:
             S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])
+def test_autotune_leaves_results_unchanged(capi, precision):
+    """dgm_autotune times its launch candidates with dt = 0 on the problem's own
+    fields (which it leaves unchanged) and keeps the fastest; a run after it
+    gives bitwise the fields of a run with the default configuration (24,576
+    tets, 192 tiles: both tensor-core candidates are real)."""
+    m = kuhn_cube_mesh(16, jitter=0.1, seed=81)
+    p, dt = 2, 0.2 / 16 / 4
+    eps = np.random.default_rng(82).uniform(1, 4, m.nt)
+    A = _solver(capi, m, p, eps, 1.0, precision)
+    B = _solver(capi, m, p, eps, 1.0, precision)
+    rng = np.random.default_rng(83)
+    E0, H0 = rng.standard_normal(A.nE), rng.standard_normal(A.nH)
+    for S in (A, B):
+        S.set_fields(E0, H0)
+    E1, H1 = A.get_fields()[:2]
+    cfg, ms, chosen = A.autotune(3)
+    _log("autotune", precision=precision, configs=cfg, ms=ms, chosen=chosen)
+    assert 1 <= len(cfg) <= capi.AUTOTUNE_MAX and 0 <= chosen < len(cfg)
+    assert all(t > 0 for t in ms) and ms[chosen] == min(ms)
+    if precision.startswith("tc"):
+        assert cfg == [1, 2]
+    E2, H2 = A.get_fields()[:2]
+    assert np.array_equal(E1, E2) and np.array_equal(H1, H2)          # dt = 0: fields untouched
+    WA = A.run(dt, 20, energies=True)
+    WB = B.run(dt, 20, energies=True)
+    EA, HA = A.get_fields()[:2]
+    EB, HB = B.get_fields()[:2]
+    assert np.array_equal(EA, EB) and np.array_equal(HA, HB)
+    assert np.allclose(WA, WB, rtol=1e-12, atol=0)
+    A.close()
+    B.close()
