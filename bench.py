@@ -419,9 +419,11 @@ def run_gpu(args, rank, world, local):
 
 def run_batched(args, rank, world, local):
     """Workload batched_64: 64 independent runs (n in {8,12,16}, jitter 0.1h,
-    p in {2..6}, eps ~ U[1,4], a seeded z-dipole Gaussian-derivative source each,
-    TC32) advanced together by one CUDA graph (dgm_batch_run); compared with one
-    dgm_run call per run on the same problems."""
+    p in {2..6}, eps ~ U[1,4], a seeded z-dipole Gaussian-derivative source each)
+    in the chosen precision, each launch configuration autotuned, advanced
+    together by one CUDA graph (dgm_batch_run); compared with one dgm_run call
+    per run on the same problems, and with one dgm_run call per run of the
+    plain FP64 path."""
     import torch
     torch.cuda.set_device(local)
     from workloads.configs import batched_runs
@@ -429,19 +431,26 @@ def run_batched(args, rank, world, local):
     from paper_1104_4208_gb300 import _capi as capi
     from paper_1104_4208_gb300.solver import Solver
     runs = batched_runs(64)
-    solvers, dts, dofs = [], [], 0
-    for (n, p, seed) in runs:
-        m = kuhn_cube_mesh(n, jitter=0.1, seed=seed)
-        rng = np.random.Generator(np.random.PCG64([seed, 1]))
-        eps = rng.uniform(1, 4, m.nt)
-        S = Solver(m.xyz, m.tets, p, eps, 1.0, precision=args.precision)
-        dt = 0.2 / n / p ** 2
-        tau = 500 * dt / 20
-        capi.dgm_set_source(S.prob, rng.uniform(0.25, 0.75, 3), [0.0, 0.0, 1.0], 4 * tau, tau, 1.0)
-        solvers.append(S)
-        dts.append(dt)
-        dofs += m.nt * dof_per_elem(p)
-    dts = np.array(dts)
+
+    def make_runs(precision, tune):
+        out, dts, dofs, tuned = [], [], 0, []
+        for (n, p, seed) in runs:
+            m = kuhn_cube_mesh(n, jitter=0.1, seed=seed)
+            rng = np.random.Generator(np.random.PCG64([seed, 1]))
+            eps = rng.uniform(1, 4, m.nt)
+            S = Solver(m.xyz, m.tets, p, eps, 1.0, precision=precision)
+            dt = 0.2 / n / p ** 2
+            tau = 500 * dt / 20
+            capi.dgm_set_source(S.prob, rng.uniform(0.25, 0.75, 3), [0.0, 0.0, 1.0], 4 * tau, tau, 1.0)
+            if tune:
+                cfg, _, ch = S.autotune(2)
+                tuned.append(cfg[ch])
+            out.append(S)
+            dts.append(dt)
+            dofs += m.nt * dof_per_elem(p)
+        return out, np.array(dts), dofs, tuned
+
+    solvers, dts, dofs, tuned = make_runs(args.precision, not args.no_autotune)
     B = capi.dgm_batch_create(solvers[0].ctx, [S.prob for S in solvers])
     stream = torch.cuda.current_stream()
     K = args.steps
@@ -466,20 +475,38 @@ def run_batched(args, rank, world, local):
     W = np.empty((len(solvers), 2))
     capi.dgm_batch_run(B, dts, 1, stream.cuda_stream, W)
     capi.dgm_batch_destroy(B)
+    for S in solvers:
+        S.close()
+    # plain FP64 path, one launch sequence per run
+    s64, dts64, _, _ = make_runs("fp64", False)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for S, dt in zip(s64, dts64):
+        capi.dgm_run(S.prob, dt, K, stream.cuda_stream, None)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = ev0.elapsed_time(ev1)
+    for S in s64:
+        S.close()
     value = world * dofs * K / (ms * 1e-3)
+    # kernels per run and step: E-phase, source, H-phase (+ the source tile's trace refresh on the
+    # tensor-core path); per run once: opening trace pass and closing half kick
+    per_step = 3 + (1 if args.precision in ("tc16", "tc32") else 0)
+    launches = len(runs) * (per_step * K + 2)
     out = None
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": DTYPE[args.precision], "data": "synthetic",
-               "config": {"workload": "batched_64", "runs": len(solvers), "dof_total": dofs,
+               "config": {"workload": "batched_64", "runs": len(runs), "dof_total": dofs,
                           "precision": args.precision, "graph": "one CUDA graph, one branch per run",
+                          "launch": {"autotuned_per_sm": tuned} if tuned else "default",
                           "l2": "runs small, partly L2 resident; no flush (time loop reuses state)"},
                "one_launch_sequence_per_run": {"value": world * dofs * K / (ms_seq * 1e-3), "ms": ms_seq,
                                                 "batched_speedup": ms_seq / ms},
-               "clocks": clk.summary(), "gpu_launches": None}
-    for S in solvers:
-        S.close()
+               "plain_fp64_one_launch_sequence_per_run": {"value": world * dofs * K / (ms64 * 1e-3), "ms": ms64,
+                                                          "batched_speedup": ms64 / ms},
+               "clocks": clk.summary(), "gpu_launches": launches}
     return out
 
 

@@ -658,10 +658,8 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
         if (r) return r;
         if (P->tc) {
             // the tensor-core H-phase writes its partials; the reduction is timed separately below
-            if (!P->trE_valid) {
-                r = dgm::tc_traces(P, 0, s);
-                if (r) return r;
-            }
+            r = dgm::tc_ensure_traces_E(P, slot != nullptr, s);
+            if (r) return r;
             r = dgm::tc_launch_phase_H(P->tca, P->tc_grid, dt, a_lo, c_out, slot ? 1 : 0, s);
             if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
             P->trH_valid = true;
@@ -821,7 +819,14 @@ int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s) 
                                                      P->dSrcF, n, dt, s)
                       : dgm::add_point_source<double>((double*)E, P->NE, K, tiled, P->src_elem, P->dSrc + 3, P->dSrc,
                                                       P->dSrcF, n, dt, s);
-    if (P->tc) P->trE_valid = false;
+    if (P->tc) {
+        // the source changes E in one element: only its tile's E traces are stale
+        const int tile = (int)(P->src_elem / dgm::kTcRows);
+        if (P->trE_valid && (P->trE_dirty_tile < 0 || P->trE_dirty_tile == tile))
+            P->trE_dirty_tile = tile;
+        else
+            P->trE_valid = false;
+    }
     return r ? cuda_fail(cudaGetLastError(), "source launch") : DGM_OK;
 }
 

@@ -56,6 +56,7 @@ struct dgm_problem {
     bool tc = false;
     int tc_grid = 0;                     // CTAs of the tensor-core kernels (autotuned)
     int tc_grid_cap = 0;                 // largest tc_grid the partial sums are sized for
+    int trE_dirty_tile = -1;             // with trE_valid: the one tile whose E traces are stale (point source)
     dgm::TCArgs tca{};
     void* dTc = nullptr;                 // one allocation: tiled state, traces, tables, partials
     double* dTcGeo = nullptr;
@@ -98,6 +99,10 @@ int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const 
 int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s);
 int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s);
 int tc_traces(dgm_problem* P, int which, cudaStream_t s);
+// make the E traces current before an H-phase: all tiles if they are invalid
+// (or if the H-phase needs E's energy partials), else the one tile a point
+// source changed
+int tc_ensure_traces_E(dgm_problem* P, bool energy, cudaStream_t s);
 int tc_state_energy(dgm_problem* P, double* slot, cudaStream_t s);
 int tc_check_error(dgm_problem* P);
 }  // namespace dgm

@@ -249,12 +249,22 @@ int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const 
 int tc_traces(dgm_problem* P, int which, cudaStream_t s) {
     if (tc_launch_traces(P->tca, P->tc_grid, which, s)) return cuda_err(cudaGetLastError(), "traces launch");
     (which == 0 ? P->trE_valid : P->trH_valid) = true;
+    if (which == 0) P->trE_dirty_tile = -1;
+    return DGM_OK;
+}
+
+int tc_ensure_traces_E(dgm_problem* P, bool energy, cudaStream_t s) {
+    if (!P->trE_valid || (P->trE_dirty_tile >= 0 && energy)) return tc_traces(P, 0, s);
+    if (P->trE_dirty_tile >= 0) {
+        if (tc_launch_traces_tile(P->tca, 0, P->trE_dirty_tile, s)) return cuda_err(cudaGetLastError(), "traces launch");
+        P->trE_dirty_tile = -1;
+    }
     return DGM_OK;
 }
 
 int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s) {
-    if (!P->trE_valid) {
-        int rc = tc_traces(P, 0, s);
+    {
+        int rc = tc_ensure_traces_E(P, energy_slot != nullptr, s);
         if (rc) return rc;
     }
     if (tc_launch_phase_H(P->tca, P->tc_grid, dt, a_lo, c_out, energy_slot ? 1 : 0, s))
@@ -273,6 +283,7 @@ int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s) {
     if (tc_launch_phase_E(P->tca, P->tc_grid, dt, energy ? 1 : 0, s))
         return cuda_err(cudaGetLastError(), "E-phase launch");
     P->trE_valid = true;
+    P->trE_dirty_tile = -1;
     return DGM_OK;
 }
 

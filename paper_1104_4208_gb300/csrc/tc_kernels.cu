@@ -502,12 +502,13 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
     teardown(ctl, warp, A.tmem_cols);
 }
 
-// traces of E (which = 0, with the energy partials of E) or H (which = 1).
+// traces of E (which = 0; with `energy` also the energy partials of E) or H
+// (which = 1) on tiles [tile0, tile1).
 // With fp16 operands each thread first rewrites its element's fp16 copy of
 // the field from the fp32 state (the state may have been changed from
 // outside: import, sources, checkpoints); the copy then feeds the GEMM.
 template <typename OP>
-__global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
+__global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which, int tile0, int tile1, int energy) {
     using T = typename OP::T;
     extern __shared__ __align__(1024) uint8_t smem[];
     Ctl* ctl = reinterpret_cast<Ctl*>(smem);
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
     const float* field = which == 0 ? A.E : A.H;
     T* field_op = static_cast<T*>(which == 0 ? A.Eop : A.Hop);
     double eacc = 0.0;
-    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    for (int tile = tile0 + (int)blockIdx.x; tile < tile1; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
         const float* ft = field + (size_t)tile * K * kTcRows;
         T* fo = field_op + (size_t)tile * Ko * kTcRows;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
             add_mmas(G, 0, d.NT, 0);
             if (!ring_gemm<OP>(ctl, ring, A.stage_bytes, g, G, tmem)) ctl->abort = 1;
         }
-        if (which == 0) {
+        if (which == 0 && energy) {
             const double* gg = A.geo + t * kGeoStride;
             const double G0 = gg[6], G1 = gg[7], G2 = gg[8], G3 = gg[9], G4 = gg[10], G5 = gg[11];
             for (int a = 0; a < d.NE; ++a) {
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which) {
         epilogue_barrier();
     }
     if (ctl->abort && tid == 0) record_error(A.err);
-    if (which == 0) block_sum_store(eacc, A.partE);
+    if (which == 0 && energy) block_sum_store(eacc, A.partE);
     teardown(ctl, warp, A.tmem_cols);
 }
 
@@ -723,10 +724,10 @@ int launch_phase(const TCArgs& a, int grid, double dt, double a_lo, double c_out
 }
 
 template <typename OP>
-int launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
+int launch_traces(const TCArgs& a, int grid, int which, int tile0, int tile1, int energy, cudaStream_t s) {
     const size_t sm = smem_of(a);
     if (set_smem((const void*)k_tc_traces<OP>, sm)) return -1;
-    k_tc_traces<OP><<<grid, 128, sm, s>>>(a, which);
+    k_tc_traces<OP><<<grid, 128, sm, s>>>(a, which, tile0, tile1, energy);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -743,7 +744,13 @@ int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStre
 }
 
 int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
-    return a.d.f16 ? launch_traces<OpF16>(a, grid, which, s) : launch_traces<OpTf32>(a, grid, which, s);
+    return a.d.f16 ? launch_traces<OpF16>(a, grid, which, 0, a.ntiles, which == 0, s)
+                   : launch_traces<OpTf32>(a, grid, which, 0, a.ntiles, which == 0, s);
+}
+
+int tc_launch_traces_tile(const TCArgs& a, int which, int tile, cudaStream_t s) {
+    return a.d.f16 ? launch_traces<OpF16>(a, 1, which, tile, tile + 1, 0, s)
+                   : launch_traces<OpTf32>(a, 1, which, tile, tile + 1, 0, s);
 }
 
 int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s) {

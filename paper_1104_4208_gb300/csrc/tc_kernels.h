@@ -65,6 +65,8 @@ int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStre
 // traces (and, for E, the energy partials of E) of the current field: which = 0 E, 1 H;
 // with fp16 operands the operand copy of the field is refreshed from the state first
 int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s);
+// the same for one tile, without energy partials (one CTA)
+int tc_launch_traces_tile(const TCArgs& a, int which, int tile, cudaStream_t s);
 // energy partials of the state (no staggering)
 int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s);
 // canonical (or orthonormal) [t][3][N] doubles <-> tiled floats, scaled by nrm[a] (import) / 1/nrm[a] (export)
