@@ -441,35 +441,51 @@ def observation_matrix(dg, pts):
 
 
 def adjoint_grad_eps(dg, E0, H0, dt, nsteps, pts):
+    """J and dJ/d eps of adjoint_grad (the permittivity part)."""
+    J, geps, _ = adjoint_grad(dg, E0, H0, dt, nsteps, pts)
+    return J, geps
+
+
+def adjoint_grad(dg, E0, H0, dt, nsteps, pts):
     """J = sum_{n=1..N} sum_o |E^n(x_o)|^2 for the leapfrog of OracleDG.run (central
-    flux) and dJ/d eps_T by the discrete adjoint:
-      e^m = 2 P^T P E^m + dt A^T g^m + e^{m+1},   g^{m-1} = g^m - dt B^T e^m,
-      dJ/d eps_T = -(1/eps_T) sum_m e^m_T . (E^m - E^{m-1})_T,
-    with A = M_mu^{-1} C_H (H-kick), B = -M_eps^{-1} C_E (E-kick), e^{N+1} = 0, g^N = 0."""
+    flux; G^n = H^{n+1/2}) and its gradients by the discrete adjoint.  Forward:
+      G^0 = H^0 + dt/2 A E^0,  E^{n+1} = E^n + dt B G^n,  G^{n+1} = G^n + dt A E^{n+1},
+    A = M_mu^{-1} C_H (H-kick), B = M_eps^{-1} C_E (E-kick).  Multipliers e^m of the
+    E-updates and g^m of the G-updates (Lagrangian J - sum e.R_E - sum g.R_G):
+      e^m = 2 P^T P E^m + dt A^T g^m + e^{m+1},   g^{m-1} = g^m + dt B^T e^m,
+    e^{N+1} = 0, g^N = 0.  Since d M^{-1}/d c_T = -M^{-1}|_T / c_T (c = eps, mu):
+      dJ/d eps_T = -(1/eps_T) sum_{m=1..N} e^m_T . (E^m - E^{m-1})_T,
+      dJ/d mu_T  = -(1/mu_T) [sum_{m=1..N} g^m_T . (G^m - G^{m-1})_T + g^0_T . (G^0 - H^0)_T]."""
     A_ = dg.assemble()
     P = observation_matrix(dg, pts)
     PtP = (P.T @ P).tocsr()
     E = np.array(E0, dtype=float)
     H = np.array(H0, dtype=float)
     G = H + 0.5 * dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
-    Es = [E.copy()]
+    Es, Gs = [E.copy()], [G.copy()]
     J = 0.0
     for n in range(nsteps):
         E = E + dt * dg._blockmul(A_["MEinv"], A_["CE"] @ G)
         Es.append(E.copy())
         J += float(E @ (PtP @ E))
         G = G + dt * dg._blockmul(A_["MHinv"], A_["CH"] @ E)
-    # transposes of A = MHinv CH and B = -MEinv CE  (block inverses are symmetric)
+        Gs.append(G.copy())
+    # transposes of A = MHinv CH and B = MEinv CE (block inverses are symmetric)
     e_next = np.zeros(dg.sizeE)
     g = np.zeros(dg.sizeH)
-    grad = np.zeros(dg.nt)
+    geps = np.zeros(dg.nt)
+    gmu = np.zeros(dg.nt)
     for m in range(nsteps, 0, -1):
         e = 2 * (PtP @ Es[m]) + dt * (A_["CH"].T @ dg._blockmul(A_["MHinv"], g)) + e_next
         dE = (Es[m] - Es[m - 1]).reshape(dg.nt, -1)
-        grad -= np.einsum("ti,ti->t", e.reshape(dg.nt, -1), dE) / dg.eps
+        geps -= np.einsum("ti,ti->t", e.reshape(dg.nt, -1), dE) / dg.eps
+        dG = (Gs[m] - Gs[m - 1]).reshape(dg.nt, -1)
+        gmu -= np.einsum("ti,ti->t", g.reshape(dg.nt, -1), dG) / dg.mu
         g = g + dt * (A_["CE"].T @ dg._blockmul(A_["MEinv"], e))
         e_next = e
-    return J, grad
+    dG0 = (Gs[0] - np.asarray(H0, dtype=float)).reshape(dg.nt, -1)
+    gmu -= np.einsum("ti,ti->t", g.reshape(dg.nt, -1), dG0) / dg.mu
+    return J, geps, gmu
 
 
 def objective(dg, E0, H0, dt, nsteps, pts):
