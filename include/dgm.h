@@ -196,15 +196,19 @@ int dgm_get_time(const dgm_problem* prob, double* t);
 int dgm_set_materials(dgm_problem* prob, const double* eps, const double* mu);
 
 /* Gradient of a field observable with respect to the per-element permittivity
- * by the discrete adjoint of the leapfrog (Sec. 3; central flux):
+ * and permeability by the discrete adjoint of the leapfrog (Sec. 3; central
+ * flux):
  *   J = sum_{n=1..nsteps} sum_o |E^n(x_o)|^2,  x_o = xobs[o][0..2],
  * E^n the fields of dgm_run started from the current state.  The adjoint runs
  * the same E- and H-kicks backward in time (negative step) with point sources
- * 2 P^T P E^n; E^n is recomputed segment by segment from checkpoints taken every
- * ckpt_every steps.  dJdeps[nt] (host) receives dJ/d eps_T, J_out (host) J.
- * The state is restored.  Points must lie in the mesh.  Blocks; allocates. */
+ * 2 P^T P E^n; E^n and the staggered H^{n+1/2} are recomputed segment by
+ * segment from checkpoints taken every ckpt_every steps.  dJdeps[nt] (host)
+ * receives dJ/d eps_T, dJdmu[nt] (host, nullable) dJ/d mu_T (the H-kicks'
+ * multipliers against the H increments, the opening half kick included),
+ * J_out (host) J.  The state is restored.  Points must lie in the mesh.
+ * Blocks; allocates. */
 int dgm_adjoint_grad(dgm_problem* prob, double dt, int64_t nsteps, int nobs, const double* xobs,
-                     int ckpt_every, double* J_out, double* dJdeps);
+                     int ckpt_every, double* J_out, double* dJdeps, double* dJdmu);
 
 /* Batches: many independent problems on one device advanced together.  The
  * whole time loop of every run is captured once into a CUDA graph -- a fork,

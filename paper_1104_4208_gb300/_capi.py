@@ -75,7 +75,7 @@ _SIGS = {
     "dgm_set_source": ([_vp, _pd, _pd, C.c_double, C.c_double, C.c_double], C.c_int),
     "dgm_set_time": ([_vp, C.c_double], C.c_int),
     "dgm_get_time": ([_vp, _pd], C.c_int),
-    "dgm_adjoint_grad": ([_vp, C.c_double, _i64, C.c_int, _pd, C.c_int, _pd, _pd], C.c_int),
+    "dgm_adjoint_grad": ([_vp, C.c_double, _i64, C.c_int, _pd, C.c_int, _pd, _pd, _pd], C.c_int),
     "dgm_energy_noalloc": ([_vp, _vp, _vp], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
@@ -246,13 +246,15 @@ def dgm_set_materials(prob, eps, mu):
     _check(_lib.dgm_set_materials(prob, _dptr(eps), _dptr(mu)))
 
 
-def dgm_adjoint_grad(prob, dt, nsteps, xobs, ckpt_every, nt):
+def dgm_adjoint_grad(prob, dt, nsteps, xobs, ckpt_every, nt, mu_grad=False):
+    """-> (J, dJ/d eps) or, with mu_grad, (J, dJ/d eps, dJ/d mu)."""
     xobs = np.ascontiguousarray(xobs, dtype=np.float64).reshape(-1, 3)
     J = C.c_double()
     g = np.empty(nt)
+    gm = np.empty(nt) if mu_grad else None
     _check(_lib.dgm_adjoint_grad(prob, float(dt), int(nsteps), xobs.shape[0], _dptr(xobs), int(ckpt_every),
-                                 C.byref(J), _dptr(g)))
-    return J.value, g
+                                 C.byref(J), _dptr(g), _dptr(gm) if mu_grad else None))
+    return (J.value, g, gm) if mu_grad else (J.value, g)
 
 
 def dgm_energy(prob):

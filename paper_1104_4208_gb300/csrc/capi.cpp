@@ -1107,7 +1107,7 @@ struct DevBuf {
 }  // namespace
 
 int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const double* xobs, int ckpt_every,
-                     double* J_out, double* dJdeps) {
+                     double* J_out, double* dJdeps, double* dJdmu) {
     if (!P || !xobs || nobs < 1 || nobs > 1024 || nsteps < 1 || ckpt_every < 1 || !std::isfinite(dt)) {
         set_error("dgm_adjoint_grad: bad argument");
         return DGM_ERR_INVALID_ARG;
@@ -1168,8 +1168,8 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     const size_t sE = v.nE * es, sH = v.nH * es;
     // one allocation: obs data, J, grad, saved state, checkpoints, segment, adjoint state
     const size_t obs_bytes = ((nobs * sizeof(int32_t) + 255) / 256) * 256 + (ophi.size() + oFi.size() + ogi.size()) * 8;
-    const size_t total = obs_bytes + 256 + (size_t)P->nt * 8 + 256 + (sE + sH) * (1 + nck) + sE * (ckpt_every + 1) +
-                         sE + sH + 1024;
+    const size_t total = obs_bytes + 256 + 2 * ((size_t)P->nt * 8 + 256) + (sE + sH) * (1 + nck) +
+                         (sE + sH) * (ckpt_every + 1) + sE + sH + 2048;
     DevBuf buf;
     DGM_CUDA(cudaMalloc(&buf.p, total));
     char* q = (char*)buf.p;
@@ -1184,9 +1184,11 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     double* dGi = (double*)take(ogi.size() * 8);
     double* dJ = (double*)take(8);
     double* dGrad = (double*)take((size_t)P->nt * 8);
+    double* dGradMu = (double*)take((size_t)P->nt * 8);
     char* save = take(sE + sH);
     char* ck = take((sE + sH) * nck);
     char* seg = take(sE * (ckpt_every + 1));
+    char* segG = take(sH * (ckpt_every + 1));   // G^n = H^{n+1/2} of the segment (dJ/d mu)
     char* aE = take(sE);
     char* aH = take(sH);
     cudaMemcpy(dElem, oe.data(), nobs * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -1195,6 +1197,7 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     cudaMemcpy(dGi, ogi.data(), ogi.size() * 8, cudaMemcpyHostToDevice);
     cudaMemset(dJ, 0, 8);
     cudaMemset(dGrad, 0, (size_t)P->nt * 8);
+    cudaMemset(dGradMu, 0, (size_t)P->nt * 8);
     cudaMemset(aE, 0, sE);
     cudaMemset(aH, 0, sH);
     const dgm::ObsDev O{nobs, dElem, dPhi, dFi, dGi};
@@ -1229,12 +1232,19 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
         cudaMemcpy(v.E, ck + s * (sE + sH), sE, cudaMemcpyDeviceToDevice);
         cudaMemcpy(v.H, ck + s * (sE + sH) + sE, sH, cudaMemcpyDeviceToDevice);
         cudaMemcpy(seg, v.E, sE, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(segG, v.H, sH, cudaMemcpyDeviceToDevice);
         for (int64_t n = n0; n < n1 && !rc; ++n) {
             rc = phase_E(P, dt, 0);
             if (!rc) rc = apply_source(P, v.E, n, dt, 0);
             cudaMemcpyAsync(seg + (n - n0 + 1) * sE, v.E, sE, cudaMemcpyDeviceToDevice, 0);
-            if (!rc && n < n1 - 1) rc = phase_H(P, dt, 0.0, 1.0, nullptr, 0);
+            if (!rc && n < n1 - 1) {
+                rc = phase_H(P, dt, 0.0, 1.0, nullptr, 0);
+                cudaMemcpyAsync(segG + (n - n0 + 1) * sH, v.H, sH, cudaMemcpyDeviceToDevice, 0);
+            }
         }
+        // G^{n1}: the next segment's checkpoint (not needed at n1 = N, where g^ = 0)
+        if (n1 < nsteps)
+            cudaMemcpy(segG + (n1 - n0) * sH, ck + (s + 1) * (sE + sH) + sE, sH, cudaMemcpyDeviceToDevice);
         set_state_ptrs(P, aE, aH);
         for (int64_t m = n1; m > n0 && !rc; --m) {
             const char* Em = seg + (m - n0) * sE;
@@ -1252,8 +1262,33 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
                 rc = cuda_fail(cudaGetLastError(), "adjoint kernels");
                 break;
             }
+            // dJ/d mu_T -= g^m . (G (x) I)(G^m - G^{m-1})_T  (g^N = 0: nothing at m = N)
+            if (dJdmu && m < nsteps) {
+                const char* Gm = segG + (m - n0) * sH;
+                const char* Gmm = segG + (m - n0 - 1) * sH;
+                const int KH = P->tc ? P->tca.d.KH : 0;
+                const int rr = v.f32 ? dgm::adj_grad<float>(P->nt, geo, (const float*)aH, (const float*)Gm,
+                                                             (const float*)Gmm, P->NH, KH, tiled, dGradMu, 0)
+                                     : dgm::adj_grad<double>(P->nt, geo, (const double*)aH, (const double*)Gm,
+                                                              (const double*)Gmm, P->NH, KH, tiled, dGradMu, 0);
+                if (rr) {
+                    rc = cuda_fail(cudaGetLastError(), "adjoint kernels");
+                    break;
+                }
+            }
             rc = phase_H(P, -dt, 0.0, 1.0, nullptr, 0);   // g^ -= dt M_mu^{-1} C e^
         }
+    }
+    // opening half kick: dJ/d mu_T -= g^0 . (G (x) I)(G^0 - H^0)_T
+    if (!rc && dJdmu) {
+        const int KH = P->tc ? P->tca.d.KH : 0;
+        const char* G0 = ck + sE;          // checkpoint 0: (E^0, G^0)
+        const char* H0 = save + sE;        // the state before the run
+        const int rr = v.f32 ? dgm::adj_grad<float>(P->nt, geo, (const float*)aH, (const float*)G0, (const float*)H0,
+                                                     P->NH, KH, tiled, dGradMu, 0)
+                             : dgm::adj_grad<double>(P->nt, geo, (const double*)aH, (const double*)G0,
+                                                      (const double*)H0, P->NH, KH, tiled, dGradMu, 0);
+        if (rr) rc = cuda_fail(cudaGetLastError(), "adjoint kernels");
     }
     set_state_ptrs(P, E0p, H0p);
     cudaMemcpy(v.E, save, sE, cudaMemcpyDeviceToDevice);
@@ -1264,6 +1299,7 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     if (P->tc && (rc = dgm::tc_check_error(P))) return rc;
     if (J_out) DGM_CUDA(cudaMemcpy(J_out, dJ, 8, cudaMemcpyDeviceToHost));
     if (dJdeps) DGM_CUDA(cudaMemcpy(dJdeps, dGrad, (size_t)P->nt * 8, cudaMemcpyDeviceToHost));
+    if (dJdmu) DGM_CUDA(cudaMemcpy(dJdmu, dGradMu, (size_t)P->nt * 8, cudaMemcpyDeviceToHost));
     return DGM_OK;
 }
 

@@ -424,28 +424,31 @@ def test_stability_bound_power_iteration(capi, precision, flux):
 
 @pytest.mark.parametrize("precision", ["fp64", "tc32", "tc16"])
 def test_adjoint_gradient_vs_oracle(capi, precision):
-    """dJ/d eps by the library's checkpointed discrete adjoint (4 segments of 10
-    steps, 8 observation points, 162 tets, p=3) vs the oracle's adjoint."""
-    from oracle.dg import OracleDG, adjoint_grad_eps
+    """dJ/d eps and dJ/d mu by the library's checkpointed discrete adjoint (4
+    segments of 10 steps, 8 observation points, 162 tets, p=3, eps and mu varying
+    per element) vs the oracle's adjoint."""
+    from oracle.dg import OracleDG, adjoint_grad
     from workloads.fields import random_points
     m = kuhn_cube_mesh(3, jitter=0.1, seed=51, shuffle_local=True)
     rng = np.random.default_rng(52)
     eps = rng.uniform(1, 4, m.nt)
+    mu = rng.uniform(1, 2, m.nt)
     p, dt, N = 3, 0.2 / 3 / 9, 40
-    dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+    dg = OracleDG(m.xyz, m.tets, p, eps, mu)
     E0 = rng.standard_normal(dg.sizeE) * 0.1
     H0 = rng.standard_normal(dg.sizeH) * 0.1
     pts = random_points(5005, 8, 0.1, 0.9)
-    Jo, go = adjoint_grad_eps(dg, E0, H0, dt, N, pts)
-    S = _solver(capi, m, p, eps, 1.0, precision)
+    Jo, go, gmo = adjoint_grad(dg, E0, H0, dt, N, pts)
+    S = _solver(capi, m, p, eps, mu, precision)
     S.set_fields(E0, H0)
-    J, g = capi.dgm_adjoint_grad(S.prob, dt, N, pts, 10, m.nt)
+    J, g, gm = capi.dgm_adjoint_grad(S.prob, dt, N, pts, 10, m.nt, mu_grad=True)
     E1, H1 = S.get_fields()
-    assert _rel(E1, E0) < 1e-6                              # state restored
+    assert _rel(E1, E0) < 1e-6 and _rel(H1, H0) < 1e-6      # state restored
     tol = 1e-10 if precision == "fp64" else 3e-2
-    _log("adjoint", precision=precision, errJ=abs(J - Jo) / Jo, errg=_rel(g, go))
+    _log("adjoint", precision=precision, errJ=abs(J - Jo) / Jo, errg=_rel(g, go), errgmu=_rel(gm, gmo))
     assert abs(J - Jo) <= tol * Jo
     assert _rel(g, go) < tol
+    assert _rel(gm, gmo) < tol
     S.close()
 
 
@@ -483,8 +486,28 @@ def test_adjoint_full_workload_finite_differences(capi):
             vals.append(capi.dgm_adjoint_grad(S.prob, w.dt, w.steps, pts, 50, m.nt)[0])
         fd = (vals[0] - vals[1]) / (2 * d)
         errs.append(abs(fd - g[T]) / max(abs(g).max(), 1e-300))
-    _log("adjoint_fd", J=float(J), errs=[float(e) for e in errs])
+    # dJ/d mu through the same autograd function, finite differences on 4 elements
+    eps_t = torch.tensor(w.eps, dtype=torch.float64, requires_grad=True)
+    mu_t = torch.tensor(np.broadcast_to(w.mu, (m.nt,)).copy(), dtype=torch.float64, requires_grad=True)
+    J2 = ObservationObjective.apply(eps_t, S, E0, H0, w.dt, w.steps, pts, 50, mu_t)
+    J2.backward()
+    gmu = mu_t.grad.numpy()
+    assert float(J2) == pytest.approx(float(J), rel=1e-12)
+    errs_mu = []
+    for T in rng.choice(m.nt, 4, replace=False):
+        d = 1e-6 * mu_t.detach().numpy()[T]
+        vals = []
+        for sgn in (1, -1):
+            m2 = mu_t.detach().numpy().copy()
+            m2[T] += sgn * d
+            capi.dgm_set_materials(S.prob, w.eps, m2)
+            S.set_fields(E0, H0)
+            vals.append(capi.dgm_adjoint_grad(S.prob, w.dt, w.steps, pts, 50, m.nt)[0])
+        fd = (vals[0] - vals[1]) / (2 * d)
+        errs_mu.append(abs(fd - gmu[T]) / max(abs(gmu).max(), 1e-300))
+    _log("adjoint_fd", J=float(J), errs=[float(e) for e in errs], errs_mu=[float(e) for e in errs_mu])
     assert max(errs) < 1e-6
+    assert max(errs_mu) < 1e-6
     S.close()
 
 
