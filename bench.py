@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--ref-seconds", type=float, default=100.0,
+                    help="CPU budget of the whole --impl reference run (split over its steps)")
     return ap.parse_args()
 
 
@@ -510,12 +512,12 @@ def run_batched(args, rank, world, local):
     return out
 
 
-def run_reference(args, rank):
+def run_reference(args, rank, world):
     if rank != 0:
         return None
     from workloads.configs import make_workload
     w = make_workload(args.workload)
-    per_step = max(1.0, 100.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
     total_el = 0
     t_total = 0.0
     D = dof_per_elem(w.p)
@@ -527,7 +529,7 @@ def run_reference(args, rank):
             total_el += r["elements"]
             t_total += r["seconds"]
     value = total_el * D / t_total
-    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "tets": w.nt, "p": w.p, "precision": "fp64"},
@@ -551,7 +553,7 @@ def main():
         dist.init_process_group("nccl" if nccl else "gloo")
         _DIST.update(on=True, nccl=nccl)
     if args.impl == "reference":
-        out = run_reference(args, rank)
+        out = run_reference(args, rank, world)
     elif args.workload == "batched_64":
         out = run_batched(args, rank, world, local)
     else:
