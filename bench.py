@@ -50,6 +50,29 @@ def dof_per_elem(p):
     return 3 * n3(p) + 3 * n3(p - 1)
 
 
+# nominal FP64 rate of one GB300 (no measured FP64 peak is available); the FP64
+# path is bound by it, not by HBM
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def n2(q):
+    return (q + 1) * (q + 2) // 2
+
+
+def flops_per_elem_step(p):
+    """Flops of one element and time step in the dense-operator form: curl and
+    curl^T (2 x 3 x 2 N3(p-1) N3(p) mult-adds) plus traces and lifts of both
+    fields on four faces (2 components x 2 x 2 N2 N3 each)."""
+    return 24 * n3(p - 1) * n3(p) + 32 * (n2(p) * n3(p) + n2(p - 1) * n3(p - 1))
+
+
+def alu_roofline(w, ms_per_step):
+    achieved = w.nt * flops_per_elem_step(w.p) / (ms_per_step * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 FP64 rate",
+            "flops_per_element_step": flops_per_elem_step(w.p), "traffic": None}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,7 +362,8 @@ def run_gpu(args, rank, world, local):
         kname, kbytes, kms = kpre + "_E", bytes_E, tE
     peak, peak_src = measured_peak_hbm()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof = alu_roofline(w, ms / args.steps) if args.precision == "fp64" else \
+        {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
             "traffic": profile_traffic(f"{kname}/{args.precision}" if tcp else f"{kname}<{'float' if b == 4 else 'double'}>"),
             "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
@@ -362,7 +386,8 @@ def run_gpu(args, rank, world, local):
         del kept, kept64, Em, E64
         fp64 = {"value": v64, "ms_per_step": ms64 / args.steps, "speedup_of_mixed": value / v64,
                 "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0]),
-                "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev}
+                "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev,
+                "roofline": alu_roofline(w, ms64 / args.steps)}
         S64.close()
         S = make_solver(w, args.precision)
         project_initial(S, w, torch, q1d)
