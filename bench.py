@@ -86,6 +86,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples in this file (per rank)")
     ap.add_argument("--ref-seconds", type=float, default=100.0,
                     help="CPU budget of the whole --impl reference run (split over its steps)")
     return ap.parse_args()
@@ -108,11 +109,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/dgm_clocks_{os.getpid()}.csv"
+        # kept where --clocks-csv says (rank suffix added), else a temporary file
+        self.path = (f"{path}.rank{index}" if path else f"/tmp/dgm_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
@@ -335,7 +336,7 @@ def run_gpu(args, rank, world, local):
         cfg, tms, ch = S.autotune(3)
         tune = {"per_sm": cfg, "ms_per_step": [round(x, 4) for x in tms], "chosen": cfg[ch]}
 
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         ms, stats, W = timed_run(S, torch, dt, args.steps, args.warmup)
     clocks = clk.summary()
     T = (args.warmup + args.steps) * dt
@@ -485,7 +486,7 @@ def run_batched(args, rank, world, local):
         capi.dgm_batch_run(B, dts, K, stream.cuda_stream, None)   # first call captures the graph
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         ev0.record(stream)
         capi.dgm_batch_run(B, dts, K, stream.cuda_stream, None)
         ev1.record(stream)
