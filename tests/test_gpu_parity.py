@@ -140,7 +140,7 @@ def test_energy_of_state(capi):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])
 def test_sampled_parity_full_pulse_workload(capi, precision):
     """Workload pulse_n16_p4 at full size (24,576 tets, p=4, eps~U[1,4], jitter 0.15h):
     one H-kick and one E-kick from the projected Gaussian pulse plus seeded noise,
@@ -173,24 +173,35 @@ def test_sampled_parity_full_pulse_workload(capi, precision):
     S.close()
 
 
-def test_sampled_parity_full_planewave_workload(capi):
-    """Workload planewave_n32_p6 at full size (196,608 tets, periodic, p=6), FP32:
-    one H-kick on sampled elements vs the oracle."""
+@pytest.mark.parametrize("precision", ["fp32", "tc32", "tc16"])
+def test_sampled_parity_full_planewave_workload(capi, precision):
+    """Workload planewave_n32_p6 at full size (196,608 tets, periodic, p=6) in the
+    launch configuration the benchmark times (autotuned first): one H-kick and
+    one E-kick on sampled elements (first and last tile included) vs the oracle."""
     from oracle.dg import OracleDG
     w = make_workload("planewave_n32_p6")
     m = w.mesh
     dg = OracleDG(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key)
     rng = np.random.default_rng(78)
-    S = _solver(capi, m, w.p, w.eps, w.mu, "fp32")
+    S = _solver(capi, m, w.p, w.eps, w.mu, precision)
     E0 = rng.standard_normal(S.nE) * 0.1
     H0 = rng.standard_normal(S.nH) * 0.1
-    sample = np.unique(np.concatenate([rng.choice(m.nt, 24, replace=False), [0, m.nt - 1]]))
+    sample = np.unique(np.concatenate([rng.choice(m.nt, 24, replace=False), [0, 127, 128, m.nt - 1]]))
     S.set_fields(E0, H0)
+    S.autotune(2)
     S.kick(0, w.dt)
     _, H = S.get_fields()
     ref = dg.local_kick_H(E0, sample, w.dt)
     got = H.reshape(m.nt, -1)[sample] - H0.reshape(m.nt, -1)[sample]
-    assert _rel(got, ref) < TOL["fp32"]
+    errH = _rel(got, ref)
+    S.set_fields(E0, H0)
+    S.kick(1, w.dt)
+    E, _ = S.get_fields()
+    ref = dg.local_kick_E(H0, sample, w.dt)
+    got = E.reshape(m.nt, -1)[sample] - E0.reshape(m.nt, -1)[sample]
+    errE = _rel(got, ref)
+    _log("full_planewave_kick", precision=precision, errH=errH, errE=errE)
+    assert errH < TOL[precision] and errE < TOL[precision]
     S.close()
 
 
@@ -249,6 +260,20 @@ def test_invalid_arguments(capi):
         S.kick(0, float("nan"))
     with pytest.raises(capi.DgmError):
         S.set_fields(np.zeros(S.nE), np.zeros(S.nH), np.zeros(4))
+    S.close()
+    # tensor-core paths: p <= 6 and the central flux only, refused cleanly otherwise
+    for prec in ("tc32", "tc16"):
+        with pytest.raises(capi.DgmError) as e:
+            Solver(m.xyz, m.tets, 7, 1.0, 1.0, precision=prec)
+        assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+        with pytest.raises(capi.DgmError) as e:
+            Solver(m.xyz, m.tets, 3, 1.0, 1.0, precision=prec, flux="stabilized")
+        assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+    # autotune needs at least one timed step
+    S = Solver(m.xyz, m.tets, 2, 1.0, 1.0, precision="tc16")
+    with pytest.raises(capi.DgmError) as e:
+        S.autotune(0)
+    assert e.value.code == -1
     S.close()
 
 
