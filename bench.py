@@ -6,9 +6,13 @@ mesh) of the named workload.  The metric is DoF-steps/s = elements * D_e *
 steps / time with D_e = 3 N3(p) + 3 N3(p-1) volume coefficients per element.
 
 Default workload: planewave_n32_p6 (periodic unit box, n = 32, 196,608 tets,
-p = 6, plane wave k = 2 pi (1,2,3)), FP32 path; the FP64 path is timed on the
-same workload and reported beside it.  The field state (330 MB in FP32) is
-larger than the 129 MB L2, so no L2 flush is needed between steps.
+p = 6, plane wave k = 2 pi (1,2,3)), TC16 path (fp16 tensor-core operands, fp32
+state); the FP64 path is timed on the same workload and reported beside it.
+The field state (330 MB in fp32) is larger than the 129 MB L2, so no L2 flush
+is needed between steps.  Smaller workloads (cavity_n4_p3, pulse_n16_p4) are
+L2-resident and say so in `config.l2`.  --workload batched_64 times 64 runs in
+one CUDA graph; --workload adjoint_n16_p4 times the checkpointed adjoint
+gradient (one bench step = one gradient over the workload's 500 time steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -243,6 +247,15 @@ def l2_rel_error(S, w, torch, q1d, maps, xh, T, keep=None):
     return float(np.sqrt(err2 / ref2))
 
 
+def l2_note(state_bytes):
+    import torch
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    if state_bytes > l2:
+        return f"state {state_bytes / 1e6:.0f} MB larger than the {l2 / 1e6:.0f} MB L2 (no flush needed)"
+    return (f"state {state_bytes / 1e6:.1f} MB fits in the {l2 / 1e6:.0f} MB L2: an L2-resident figure "
+            "(the time loop reuses the state; no flush)")
+
+
 def timed_run(S, torch, dt, steps, warmup):
     from paper_1104_4208_gb300 import _capi as capi
     stream = torch.cuda.current_stream()
@@ -432,7 +445,7 @@ def run_gpu(args, rank, world, local):
                "dtype": DTYPE[args.precision], "data": "synthetic",
                "config": {"workload": w.name, "tets": w.nt, "p": w.p, "dof": dofs, "precision": args.precision,
                           "flux": "central", "dt": dt, "parallelism": f"replicas{world}",
-                          "l2": "state larger than L2 (no flush needed)",
+                          "l2": l2_note(dofs * (8 if args.precision == "fp64" else 4)),
                           "state_mb": dofs * (8 if args.precision == 'fp64' else 4) / 1e6,
                           "arithmetic": ARITH[args.precision],
                           "launch": ({"autotuned": tune, "unit": "CTAs per SM" if tcp else "blocks per SM"}
@@ -538,6 +551,68 @@ def run_batched(args, rank, world, local):
     return out
 
 
+def run_adjoint(args, rank, world, local):
+    """Workload adjoint_n16_p4: J = sum of |E(x_o)|^2 over 8 seeded observation
+    points and all 500 steps from the projected Gaussian pulse; one bench step is
+    one dgm_adjoint_grad call (forward run with checkpoints every 50 steps,
+    backward sweep recomputing each segment, dJ/d eps and dJ/d mu).  The metric
+    counts the forward DoF-steps of the horizon, so value/forward-run value is
+    the cost ratio of a gradient to a plain run."""
+    import torch
+    torch.cuda.set_device(local)
+    from workloads.configs import make_workload
+    from workloads.fields import random_points
+    from paper_1104_4208_gb300 import _capi as capi
+    w = make_workload(args.workload)
+    dofs = w.nt * dof_per_elem(w.p)
+    S = make_solver(w, args.precision)
+    project_initial(S, w, torch, w.p + 1)
+    E0, H0 = S.get_fields()
+    pts = random_points(5000, 8, 0.1, 0.9)
+    ckpt = 50
+    tune = None
+    if not args.no_autotune:
+        cfg, tms, ch = S.autotune(3)
+        tune = {"per_sm": cfg, "chosen": cfg[ch]}
+    for _ in range(args.warmup):
+        S.set_fields(E0, H0)
+        capi.dgm_adjoint_grad(S.prob, w.dt, w.steps, pts, ckpt, w.nt, mu_grad=True)
+    # the gradient call is synchronous (it returns host arrays): host timer around
+    # K calls, after a device synchronize
+    torch.cuda.synchronize()
+    dist_barrier()
+    t = 0.0
+    with ClockSampler(local, args.clocks_csv) as clk:
+        for _ in range(args.steps):
+            S.set_fields(E0, H0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J, g, gm = capi.dgm_adjoint_grad(S.prob, w.dt, w.steps, pts, ckpt, w.nt, mu_grad=True)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+    t = dist_max(t)
+    # a plain forward run over the same horizon, for the cost ratio
+    S.set_fields(E0, H0)
+    ms_fwd, _, _ = timed_run(S, torch, w.dt, w.steps, 0)
+    S.close()
+    value = world * dofs * w.steps * args.steps / t
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+               "config": {"workload": w.name, "tets": w.nt, "p": w.p, "dof": dofs, "precision": args.precision,
+                          "horizon_steps": w.steps, "checkpoint_every": ckpt, "observation_points": 8,
+                          "step": "one dJ/d eps + dJ/d mu evaluation over the horizon",
+                          "l2": l2_note(dofs * (8 if args.precision == "fp64" else 4)),
+                          "launch": {"autotuned": tune} if tune else "default"},
+               "forward_run": {"ms": ms_fwd, "value": world * dofs * w.steps / (ms_fwd * 1e-3),
+                               "gradient_cost_in_forward_runs": 1e3 * t / args.steps / ms_fwd},
+               "J": J, "grad_eps_norm": float(np.linalg.norm(g)), "grad_mu_norm": float(np.linalg.norm(gm)),
+               "clocks": clk.summary(), "timer": "host clock around each synchronous gradient call"}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -582,6 +657,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "batched_64":
         out = run_batched(args, rank, world, local)
+    elif args.workload == "adjoint_n16_p4":
+        out = run_adjoint(args, rank, world, local)
     else:
         out = run_gpu(args, rank, world, local)
     if rank == 0 and out is not None:

@@ -517,3 +517,26 @@ def dipole_source_vector(dg, xs, direction, fval):
         coef = Finv[mm] @ d
         out[(t * 3 + mm) * dg.NE:(t * 3 + mm + 1) * dg.NE] = -fval * coef * vals[:, 0]
     return out
+
+
+def resonances(dg, zero_rel=1e-8):
+    """Resonance frequencies of the cavity (the frequency-domain problem of Sec. 2.2,
+    i omega eps E = curl H, i omega mu H = -curl E, PEC), discretised by the DG
+    operator of Sec. 2.1.  Eliminating H (and H^F) from the semi-discrete system
+      M_eps E' = C_E H + C_EK K,  M_mu H' = C_H E,  M_F K' = S E
+    gives E'' = -M_eps^{-1} Kc E with Kc = -(C_E M_mu^{-1} C_H + C_EK M_F^{-1} S),
+    symmetric positive semi-definite because C_E = -C_H^T and C_EK = -S^T (Sec. 2.1,
+    skew-adjointness).  A time-harmonic field gives omega^2 M_eps e = Kc e; the
+    generalized symmetric eigenproblem is solved densely (small meshes only).
+    Returns (omega of the eigenvalues above zero_rel * the largest, ascending; the
+    number of eigenvalues at or below it: the discrete null space)."""
+    import scipy.linalg as sl
+    A_ = dg.assemble()
+    CE, CH = A_["CE"].toarray(), A_["CH"].toarray()
+    Kc = -(CE @ sl.block_diag(*A_["MHinv"]) @ CH)
+    if dg.flux == "stabilized":
+        Kc -= A_["CEK"].toarray() @ sl.block_diag(*A_["MFinv"]) @ A_["S"].toarray()
+    Kc = 0.5 * (Kc + Kc.T)     # exactly symmetric in exact arithmetic; remove rounding
+    lam = np.sort(sl.eigh(Kc, sl.block_diag(*A_["ME"]), eigvals_only=True))
+    zero = lam <= zero_rel * lam.max()
+    return np.sqrt(lam[~zero]), int(zero.sum())

@@ -368,6 +368,44 @@ def test_spurious_modes_removed_by_stabilization():
     assert counts["central"] > counts["stabilized"] + 500
 
 
+def cube_cavity_frequencies(count):
+    """Closed form for the PEC unit cube: omega = pi sqrt(l^2 + m^2 + n^2), l, m, n >= 0
+    with at most one of them zero; two independent polarisations when all three are
+    nonzero, one otherwise.  The `count` smallest, with multiplicity."""
+    w = []
+    for l in range(8):
+        for m in range(8):
+            for n in range(8):
+                nz = (l > 0) + (m > 0) + (n > 0)
+                if nz >= 2:
+                    w += [math.pi * math.sqrt(l * l + m * m + n * n)] * (2 if nz == 3 else 1)
+    return np.sort(w)[:count]
+
+
+def test_cavity_resonances_converge_under_p_refinement():
+    """Sec. 2.2 (Fig. 1): on a fixed coarse mesh the resonance frequencies converge
+    as p grows.  PEC unit cube as one Kuhn cube (6 tets), stabilized central flux:
+    the 8 smallest discrete frequencies approach the closed-form cavity values
+    (pi sqrt 2 x3, pi sqrt 3 x2, pi sqrt 5 x3 of 6), the error falls at every step
+    p = 3..6 (below 1e-3 at p = 6), and the discrete null space is the gradient
+    space of continuous P^{p+1} with zero tangential trace, (p (n=1) )^3 = p^3."""
+    from oracle.dg import resonances
+    m = kuhn_cube_mesh(1)
+    exact = cube_cavity_frequencies(8)
+    errs = []
+    for p in (3, 4, 5, 6):
+        om, nnull = resonances(OracleDG(m.xyz, m.tets, p, 1.0, 1.0, flux="stabilized"))
+        assert nnull == p ** 3
+        errs.append(float(np.max(np.abs(om[:8] - exact) / exact)))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-3 and errs[0] < 3e-2
+    # h-refinement at fixed p agrees: n = 2, p = 3
+    m2 = kuhn_cube_mesh(2)
+    om, nnull = resonances(OracleDG(m2.xyz, m2.tets, 3, 1.0, 1.0, flux="stabilized"))
+    assert nnull == (4 * 2 - 1) ** 3
+    assert np.max(np.abs(om[:8] - exact) / exact) < 2e-3
+
+
 def test_adjoint_gradient_matches_finite_differences():
     """Discrete adjoint of the leapfrog (objective J = sum_n sum_o |E^n(x_o)|^2,
     derivative with respect to per-element eps) vs central finite differences with

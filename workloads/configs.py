@@ -5,6 +5,8 @@ pulse_n16_p4      unit cube PEC, n=16 (24,576 tets), jitter 0.15h, p=4, eps~U[1,
                   Gaussian pulse (width 0.1, centre ~U[0.3,0.7]^3), H=0, 1,000 steps
 planewave_n32_p6  periodic [0,1]^3, n=32 (196,608 tets), p=6, eps=mu=1,
                   plane wave k = 2 pi (1,2,3), 2,000 steps
+pulse_n32_p4      the pulse_n16_p4 recipe on n=32 (196,608 tets, p=4): its state
+                  (130 MB in fp32) no longer fits in the 129 MB L2
 batched_64        64 runs, n in {8,12,16}, jitter 0.1h, p in {2..6}, eps~U[1,4], dipole source, 500 steps
 adjoint_n16_p4    mesh/p of pulse_n16_p4, 8 observation points, 500 steps, checkpoint every 50
 
@@ -65,6 +67,8 @@ def make_workload(name, n=None, p=None, steps=None, shuffle_local=False):
         "cavity_n4_p3": dict(n=4, p=3, steps=100, periodic=False, jitter=0.0, seed=1001,
                              init="te110"),
         "pulse_n16_p4": dict(n=16, p=4, steps=1000, periodic=False, jitter=0.15, seed=1002,
+                             init="pulse", eps_range=(1.0, 4.0)),
+        "pulse_n32_p4": dict(n=32, p=4, steps=1000, periodic=False, jitter=0.15, seed=1002,
                              init="pulse", eps_range=(1.0, 4.0)),
         "planewave_n32_p6": dict(n=32, p=6, steps=2000, periodic=True, jitter=0.0, seed=1003,
                                  init="plane"),
