@@ -158,9 +158,9 @@ int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* 
 
 /* Stability bound of the explicit scheme (Sec. 3): dt <= 2 / sqrt(rho) with rho
  * the spectral radius of M_mu^{-1} C_h M_eps^{-1} C_h^T (face unknowns included
- * for the stabilized flux), estimated by `iters` power iterations (Sec. 3:
- * "estimated once by an iterative method like the power iteration") that apply
- * the library's own E- and H-kicks.  The printed bound 2 rho^{-1} is read as
+ * for the stabilized flux), estimated by `iters` power iterations (Sec. 3
+ * leaves the estimate to an iterative eigenvalue method) that apply the
+ * library's own E- and H-kicks.  The printed bound 2 rho^{-1} is read as
  * 2 rho^{-1/2} (dimensionally a time).  The state is saved and restored; the
  * start vector is a fixed pseudo-random H.  Blocks; allocates temporaries. */
 int dgm_estimate_dt(dgm_problem* prob, int iters, double* rho, double* dt_max);

@@ -6,8 +6,8 @@
 // elements then share the face frame, and because the covariant transform
 // preserves tangential components (Sec. 3.2.1: u . t = u_hat . t_hat for
 // t = F t_hat), the tangential trace coefficients of a face agree between the
-// two sides without any re-orientation.  Only the geometric transformations
-// and the local topology are kept (Sec. 3.4).
+// two sides without any re-orientation.  Per element the mesh keeps nothing
+// but its affine map and its neighbours (Sec. 3.4).
 
 #include <algorithm>
 #include <array>
