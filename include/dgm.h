@@ -165,6 +165,41 @@ int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* 
  * start vector is a fixed pseudo-random H.  Blocks; allocates temporaries. */
 int dgm_estimate_dt(dgm_problem* prob, int iters, double* rho, double* dt_max);
 
+/* Resonance frequencies of the cavity: the frequency-domain problem of Sec. 2.2
+ * (i omega eps E = curl H, i omega mu H = -curl E, PEC walls) discretised by the
+ * DG operator of Sec. 2.1.  Eliminating H (and, for the stabilized flux, H^F)
+ * gives omega^2 M_eps e = K e with K = C_H^T M_mu^{-1} C_H (+ S^T M_F^{-1} S),
+ * symmetric positive semi-definite by the skew-adjointness of the scheme.
+ * The smallest omega are found by `m` Lanczos steps on A = M_eps^{-1} K in the
+ * M_eps inner product, with full reorthogonalisation (Gram-Schmidt twice per
+ * step); each step applies A by one H-kick and one E-kick of the library's own
+ * kernels with dt = 1 from E = v, H = 0.  Ritz values at or below
+ * zero_rel * (the largest Ritz value) belong to the discrete null space
+ * (gradient fields; for the central flux also its spurious modes of exactly
+ * zero frequency) and are skipped; the next up to `nev` are returned.
+ *   m         Lanczos steps, >= 2 (clipped to the number of E coefficients)
+ *   nev       frequencies wanted, >= 1
+ *   zero_rel  in [0, 1), e.g. 1e-8
+ *   omega_out [nev] ascending frequencies (host); *nfound how many were filled
+ *   resid_out [nev] (nullable) relative residual ||A u - th u||_M / (th ||u||_M)
+ *             of each Ritz pair (th = omega^2, u its Ritz vector), computed on
+ *             the device: small values mark converged frequencies
+ * A degenerate eigenvalue is found once per Krylov direction it gains, so a
+ * multiplicity is not resolved.  FP64 precision only (DGM_ERR_UNSUPPORTED
+ * otherwise).  The fields are saved and restored.  Allocates (m + 4) x (number
+ * of E coefficients) doubles of device memory (DGM_ERR_OOM if unavailable).
+ * Blocks until the results are on the host. */
+int dgm_resonances(dgm_problem* prob, int m, int nev, double zero_rel, double* omega_out, double* resid_out,
+                   int* nfound);
+
+/* Host-only helper of dgm_resonances (no device use): eigenvalues with indices
+ * [i0, i1) in ascending order of the symmetric tridiagonal matrix with diagonal
+ * d[k] and off-diagonal e[k-1] (e may be NULL for k = 1), by bisection on Sturm
+ * counts, into vals[i1 - i0]; with vecs != NULL also unit eigenvectors
+ * [i1 - i0][k] by inverse iteration.  DGM_ERR_INVALID_ARG unless
+ * 0 <= i0 < i1 <= k. */
+int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, double* vals, double* vecs);
+
 /* Launch-configuration autotuner of the per-step kernels (the time loop of
  * Sec. 3).  Each candidate configuration is timed (CUDA events, `steps` steps
  * after one warm-up step) on this problem's own fields with dt = 0, which

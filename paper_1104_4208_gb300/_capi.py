@@ -72,6 +72,8 @@ _SIGS = {
     "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
     "dgm_energy": ([_vp, _pd], C.c_int),
     "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
+    "dgm_resonances": ([_vp, C.c_int, C.c_int, C.c_double, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
+    "dgm_tridiag_eig": ([C.c_int, _pd, _pd, C.c_int, C.c_int, _pd, _pd], C.c_int),
     "dgm_autotune": ([_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_set_materials": ([_vp, _pd, _pd], C.c_int),
     "dgm_set_source": ([_vp, _pd, _pd, C.c_double, C.c_double, C.c_double], C.c_int),
@@ -210,6 +212,27 @@ def dgm_estimate_dt(prob, iters=50):
     rho, dt = C.c_double(), C.c_double()
     _check(_lib.dgm_estimate_dt(prob, int(iters), C.byref(rho), C.byref(dt)))
     return rho.value, dt.value
+
+
+def dgm_resonances(prob, m=300, nev=8, zero_rel=1e-8):
+    """-> (omega, relative residuals): up to nev smallest nonzero resonance frequencies."""
+    om = np.empty(int(nev))
+    res = np.empty(int(nev))
+    nf = C.c_int()
+    _check(_lib.dgm_resonances(prob, int(m), int(nev), float(zero_rel), _dptr(om), _dptr(res), C.byref(nf)))
+    return om[:nf.value].copy(), res[:nf.value].copy()
+
+
+def dgm_tridiag_eig(d, e, i0, i1, vectors=False):
+    """Host-only: eigenvalues [i0, i1) of the symmetric tridiagonal (d, e), optionally unit eigenvectors."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    k = d.shape[0]
+    vals = np.empty(int(i1) - int(i0))
+    vecs = np.empty((int(i1) - int(i0), k)) if vectors else None
+    _check(_lib.dgm_tridiag_eig(k, _dptr(d), _dptr(e) if k > 1 else None, int(i0), int(i1), _dptr(vals),
+                                _dptr(vecs) if vectors else None))
+    return (vals, vecs) if vectors else vals
 
 
 AUTOTUNE_MAX = 8

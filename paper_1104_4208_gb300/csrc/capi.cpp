@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,6 +14,7 @@
 #include "kernels.h"
 #include "problem.h"
 #include "adjoint.h"
+#include "eigen.h"
 
 namespace dgm {
 
@@ -1301,6 +1303,167 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     if (dJdeps) DGM_CUDA(cudaMemcpy(dJdeps, dGrad, (size_t)P->nt * 8, cudaMemcpyDeviceToHost));
     if (dJdmu) DGM_CUDA(cudaMemcpy(dJdmu, dGradMu, (size_t)P->nt * 8, cudaMemcpyDeviceToHost));
     return DGM_OK;
+}
+
+int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, double* vals, double* vecs) {
+    if (k < 1 || !d || (k > 1 && !e) || i0 < 0 || i1 > k || i0 >= i1 || !vals) {
+        set_error("dgm_tridiag_eig: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const std::vector<double> dv(d, d + k), ev(e ? e : d, e ? e + (k - 1) : d);
+    const std::vector<double> th = dgm::tridiag_eigenvalues(dv, ev, i0, i1);
+    for (int i = 0; i < i1 - i0; ++i) {
+        vals[i] = th[i];
+        if (vecs) {
+            const std::vector<double> y = dgm::tridiag_eigenvector(dv, ev, th[i]);
+            std::copy(y.begin(), y.end(), vecs + (size_t)i * k);
+        }
+    }
+    return DGM_OK;
+}
+
+int dgm_resonances(dgm_problem* P, int m, int nev, double zero_rel, double* omega_out, double* resid_out,
+                   int* nfound_out) {
+    if (!P || m < 2 || nev < 1 || !omega_out || !nfound_out || !(zero_rel >= 0.0 && zero_rel < 1.0)) {
+        set_error("dgm_resonances: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    *nfound_out = 0;
+    if (P->tc || P->fp32) {
+        set_error("dgm_resonances: FP64 precision only");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    const StateView v = state_view(P);
+    const int64_t n = v.nE;
+    m = (int)std::min<int64_t>(m, n);
+    // one allocation: saved state (E, H, K), Lanczos basis V[m+1][n], two work vectors,
+    // coefficient vector, scalars
+    const size_t sE = n * 8, sH = v.nH * 8, sK = v.nK * 8;
+    const size_t total = sE + sH + sK + (size_t)(m + 1) * sE + 2 * sE + (size_t)(m + 1) * 8 + 64 + 8 * 256;
+    DevBuf buf;
+    DGM_CUDA(cudaMalloc(&buf.p, total));
+    char* q = (char*)buf.p;
+    auto take = [&](size_t bytes) {
+        char* r = q;
+        q += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    char* saveE = take(sE);
+    char* saveH = take(sH);
+    char* saveK = take(sK);
+    double* V = (double*)take((size_t)(m + 1) * sE);
+    double* Z = (double*)take(sE);
+    double* U = (double*)take(sE);
+    double* dh = (double*)take((size_t)(m + 1) * 8);
+    double* dsc = (double*)take(64);
+    double* E = (double*)v.E;
+    const double* geo = P->dGeo;
+    const int N = P->NE;
+    cudaMemcpy(saveE, v.E, sE, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(saveH, v.H, sH, cudaMemcpyDeviceToDevice);
+    if (sK) cudaMemcpy(saveK, v.K, sK, cudaMemcpyDeviceToDevice);
+    int rc = DGM_OK;
+    auto fin = [&](int code) {
+        cudaMemcpy(v.E, saveE, sE, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(v.H, saveH, sH, cudaMemcpyDeviceToDevice);
+        if (sK) cudaMemcpy(v.K, saveK, sK, cudaMemcpyDeviceToDevice);
+        P->trE_valid = P->trH_valid = false;
+        return code;
+    };
+    auto fail = [&](const char* what) { return fin(cuda_fail(cudaGetLastError(), what)); };
+    // y = A x = M_eps^{-1} K x: E = x, H = 0 (H^F = 0), one H-kick and one E-kick with
+    // dt = 1 leave E = x - A x
+    auto apply = [&](const double* x, double* y) -> int {
+        cudaMemcpy(E, x, sE, cudaMemcpyDeviceToDevice);
+        cudaMemset(v.H, 0, sH);
+        if (sK) cudaMemset(v.K, 0, sK);
+        P->trE_valid = P->trH_valid = false;
+        int r = phase_H(P, 1.0, 0.0, 1.0, nullptr, 0);
+        if (!r) r = phase_E(P, 1.0, 0);
+        if (r) return r;
+        if (dgm::launch_axpby<double>(n, 1.0, x, -1.0, E, 0)) return cuda_fail(cudaGetLastError(), "axpby");
+        if (y != E) cudaMemcpy(y, E, sE, cudaMemcpyDeviceToDevice);
+        return DGM_OK;
+    };
+    auto mnorm2 = [&](const double* x, double* out) -> int {
+        if (dgm::eig_mass_apply(P->nt, N, geo, x, Z, 0) || dgm::eig_dots(x, 0, 1, Z, n, dsc, 0)) return -1;
+        return cudaMemcpy(out, dsc, 8, cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : -1;
+    };
+    // start vector: fixed pseudo-random canonical E through the normal import
+    {
+        std::vector<double> h(n);
+        uint64_t st = 0xD1B54A32D192ED03ull;
+        for (int64_t i = 0; i < n; ++i) {
+            st ^= st << 13;
+            st ^= st >> 7;
+            st ^= st << 17;
+            h[i] = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        }
+        if (cudaMemcpy(P->dStage, h.data(), sE, cudaMemcpyHostToDevice) != cudaSuccess) return fail("resonances init");
+        if ((rc = import_fields(P, P->dStage, nullptr, 0))) return fin(rc);
+        double nx = 0.0;
+        if (mnorm2(E, &nx) || !(nx > 0.0)) return fail("resonances start");
+        if (dgm::launch_axpby<double>(n, 1.0 / std::sqrt(nx), E, 0.0, V, 0)) return fail("axpby");
+    }
+    // Lanczos with full reorthogonalisation (classical Gram-Schmidt, twice) in <.,.>_M
+    std::vector<double> alpha, beta;
+    std::vector<double> hh(m + 1);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        double* vj = V + (size_t)j * n;
+        double* w = U;
+        if ((rc = apply(vj, w))) return fin(rc);
+        double a = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (dgm::eig_mass_apply(P->nt, N, geo, w, Z, 0) || dgm::eig_dots(V, n, j + 1, Z, n, dh, 0) ||
+                dgm::eig_sub_combination(w, V, n, j + 1, dh, n, 0))
+                return fail("reorthogonalisation");
+            if (cudaMemcpy(hh.data(), dh, (j + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail("reorthogonalisation");
+            a += hh[j];
+        }
+        alpha.push_back(a);
+        k = j + 1;
+        double b2 = 0.0;
+        if (mnorm2(w, &b2)) return fail("norm");
+        const double b = std::sqrt(std::max(b2, 0.0));
+        // invariant subspace found (or the basis is complete)
+        if (!(b > 1e-13 * std::max(std::fabs(a), 1.0)) || j == m - 1) {
+            beta.push_back(b);
+            break;
+        }
+        beta.push_back(b);
+        if (dgm::launch_axpby<double>(n, 1.0 / b, w, 0.0, V + (size_t)(j + 1) * n, 0)) return fail("axpby");
+    }
+    // Ritz values: skip the discrete null space (at or below zero_rel * the largest)
+    const std::vector<double> ev(beta.begin(), beta.begin() + (k - 1));
+    const double top = dgm::tridiag_eigenvalues(alpha, ev, k - 1, k)[0];
+    const int c0 = dgm::tridiag_count_below(alpha, ev, zero_rel * top * (1.0 + 1e-12) + DBL_MIN);
+    const int c1 = std::min(k, c0 + nev);
+    const std::vector<double> th = dgm::tridiag_eigenvalues(alpha, ev, c0, c1);
+    int found = 0;
+    for (size_t i = 0; i < th.size(); ++i) {
+        if (!(th[i] > zero_rel * top)) continue;
+        omega_out[found] = std::sqrt(th[i]);
+        if (resid_out) {
+            // Ritz vector u = V y; relative residual ||A u - theta u||_M / (theta ||u||_M)
+            const std::vector<double> y = dgm::tridiag_eigenvector(alpha, ev, th[i]);
+            for (int j = 0; j < k; ++j) hh[j] = -y[j];
+            cudaMemset(U, 0, sE);
+            if (cudaMemcpy(dh, hh.data(), k * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+                dgm::eig_sub_combination(U, V, n, k, dh, n, 0))
+                return fail("Ritz vector");
+            double uu = 0.0, rr = 0.0;
+            if (mnorm2(U, &uu)) return fail("norm");
+            if ((rc = apply(U, E))) return fin(rc);
+            if (dgm::launch_axpby<double>(n, -th[i], U, 1.0, E, 0)) return fail("axpby");
+            if (mnorm2(E, &rr)) return fail("norm");
+            resid_out[found] = std::sqrt(std::max(rr, 0.0)) / (th[i] * std::sqrt(uu));
+        }
+        ++found;
+    }
+    *nfound_out = found;
+    return fin(DGM_OK);
 }
 
 int dgm_set_materials(dgm_problem* P, const double* eps, const double* mu) {

@@ -52,6 +52,11 @@ class Solver:
         unchanged) and keep the fastest; -> (configs, ms_per_step, chosen)."""
         return capi.dgm_autotune(self.prob, steps)
 
+    def resonances(self, m=300, nev=8, zero_rel=1e-8):
+        """Smallest nonzero cavity resonance frequencies by Lanczos on the GPU
+        operator (FP64); -> (omega, relative residuals)."""
+        return capi.dgm_resonances(self.prob, m, nev, zero_rel)
+
     def energy(self):
         return capi.dgm_energy(self.prob)
 

@@ -128,3 +128,33 @@ def test_mesh_validation_errors(capi):
     key = np.array([0, 1, 2, 3, 3, 5])          # vertices 3 and 4 share a key
     with pytest.raises(capi.DgmError):
         capi.dgm_mesh_create(None, xyz, np.array([[0, 1, 3, 4]]), key)
+
+
+def test_tridiagonal_eigen_helper(capi):
+    """Host helper of dgm_resonances: eigenvalues by Sturm bisection and unit
+    eigenvectors by inverse iteration, against a dense symmetric eigensolver on
+    matrices of the Lanczos kind (wide spread, clustered pairs, tiny couplings)."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(11)
+    cases = [(rng.uniform(0, 1e4, 60), rng.uniform(0.1, 50, 59)),
+             (np.repeat(rng.uniform(1, 10, 20), 2), np.tile([1e-9, 3.0], 20)[:39]),
+             (np.array([2.5]), np.array([]))]
+    for d, e in cases:
+        k = d.shape[0]
+        T = np.diag(d) + (np.diag(e, 1) + np.diag(e, -1) if k > 1 else 0)
+        ref, vref = np.linalg.eigh(T)
+        vals, vecs = capi.dgm_tridiag_eig(d, e, 0, k, vectors=True)
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(vals - ref)) <= 1e-13 * scale
+        for i in range(k):
+            y = vecs[i]
+            assert abs(np.linalg.norm(y) - 1) < 1e-12
+            assert np.linalg.norm(T @ y - vals[i] * y) <= 1e-10 * scale
+        # a window of indices
+        mid = capi.dgm_tridiag_eig(d, e, k // 3, k // 3 + 1)
+        assert mid[0] == pytest.approx(ref[k // 3], abs=1e-13 * scale)
+        sel = sl.eigvalsh_tridiagonal(d, e) if k > 1 else d
+        assert np.allclose(np.sort(sel), ref, rtol=0, atol=1e-12 * scale)
+    with pytest.raises(capi.DgmError) as ex:
+        capi.dgm_tridiag_eig(np.ones(3), np.ones(2), 2, 2)
+    assert ex.value.code == capi.DGM_ERR_INVALID_ARG

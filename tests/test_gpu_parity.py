@@ -638,3 +638,71 @@ def test_autotune_leaves_results_unchanged(capi, precision):
     assert np.allclose(WA, WB, rtol=1e-12, atol=0)
     A.close()
     B.close()
+
+
+def _distinct(values, rel=1e-7):
+    out = []
+    for v in np.sort(values):
+        if not out or v > out[-1] * (1 + rel):
+            out.append(v)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name,p,flux,eps_range", [("jitter_n1", 5, "stabilized", None),
+                                                   ("jitter_n2", 3, "stabilized", (1.0, 4.0)),
+                                                   ("jitter_n2", 2, "central", None)])
+def test_resonances_vs_oracle(capi, name, p, flux, eps_range):
+    """Cavity resonance frequencies (Sec. 2.2 eigenproblem on the Sec. 2.1 operator):
+    Lanczos on the GPU operator vs the oracle's dense generalized eigenproblem.
+    Every returned frequency whose relative residual r is below 1e-6 lies within
+    r of an oracle frequency (the residual bound of a symmetric eigenproblem), and
+    the three smallest distinct oracle frequencies are found to 1e-8."""
+    from oracle.dg import OracleDG, resonances
+    m = _mesh(name)
+    eps = np.random.default_rng(9).uniform(*eps_range, m.nt) if eps_range else 1.0
+    ref, _ = resonances(OracleDG(m.xyz, m.tets, p, eps, 1.0, vertex_key=m.vertex_key, flux=flux))
+    S = _solver(capi, m, p, eps, 1.0, "fp64", flux=flux)
+    E_before, H_before = S.get_fields()
+    om, res = S.resonances(m=min(S.nE, 800), nev=12)
+    E_after, H_after = S.get_fields()
+    assert np.array_equal(E_before, E_after) and np.array_equal(H_before, H_after)
+    conv = res < 1e-6
+    assert conv.sum() >= 3
+    for w, r in zip(om[conv], res[conv]):
+        assert np.min(np.abs(ref - w)) / w <= r + 1e-12
+    for w in _distinct(ref)[:3]:
+        assert np.min(np.abs(om[conv] - w)) / w < 1e-8
+    _log("resonances_vs_oracle", mesh=name, p=p, flux=flux, omega=om[:6].tolist(), resid=res[:6].tolist())
+    S.close()
+
+
+def test_resonance_study_p_refinement(capi):
+    """Sec. 2.2 / Fig. 1 analogue on affine geometry: PEC unit cube as one Kuhn cube
+    (6 tets), stabilized flux, p = 2..6, frequencies by Lanczos on the GPU operator.
+    The error of the nearest converged frequency to each of the first three distinct
+    closed-form values pi sqrt(2), pi sqrt(3), pi sqrt(5) falls with every p from
+    3 to 6 and is below 1e-3 at p = 6 (p = 2 is logged: its error is about that of
+    p = 3 on this mesh, 1.9e-2 in the oracle)."""
+    m = _mesh("jitter_n1")
+    exact = np.pi * np.sqrt([2.0, 3.0, 5.0])
+    errs = []
+    for p in (2, 3, 4, 5, 6):
+        S = _solver(capi, m, p, 1.0, 1.0, "fp64", flux="stabilized")
+        om, res = S.resonances(m=min(S.nE, 800), nev=16)
+        S.close()
+        good = om[res < 1e-6]
+        errs.append([float(np.min(np.abs(good - w)) / w) for w in exact])
+    _log("resonance_study", p=[2, 3, 4, 5, 6], rel_err=errs)
+    e = np.max(np.array(errs), axis=1)[1:]
+    assert all(b < a for a, b in zip(e, e[1:])), e
+    assert e[-1] < 1e-3
+
+
+def test_resonances_reject_reduced_precision(capi):
+    m = _mesh("jitter_n1")
+    for prec in ("fp32", "tc16"):
+        S = _solver(capi, m, 3, 1.0, 1.0, prec)
+        with pytest.raises(capi.DgmError) as e:
+            S.resonances(m=50, nev=4)
+        assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+        S.close()
