@@ -1403,7 +1403,7 @@ int dgm_resonances(dgm_problem* P, int m, int nev, double zero_rel, double* omeg
         if ((rc = import_fields(P, P->dStage, nullptr, 0))) return fin(rc);
         double nx = 0.0;
         if (mnorm2(E, &nx) || !(nx > 0.0)) return fail("resonances start");
-        if (dgm::launch_axpby<double>(n, 1.0 / std::sqrt(nx), E, 0.0, V, 0)) return fail("axpby");
+        if (dgm::eig_scale(n, 1.0 / std::sqrt(nx), E, V, 0)) return fail("scale");
     }
     // Lanczos with full reorthogonalisation (classical Gram-Schmidt, twice) in <.,.>_M
     std::vector<double> alpha, beta;
@@ -1433,7 +1433,7 @@ int dgm_resonances(dgm_problem* P, int m, int nev, double zero_rel, double* omeg
             break;
         }
         beta.push_back(b);
-        if (dgm::launch_axpby<double>(n, 1.0 / b, w, 0.0, V + (size_t)(j + 1) * n, 0)) return fail("axpby");
+        if (dgm::eig_scale(n, 1.0 / b, w, V + (size_t)(j + 1) * n, 0)) return fail("scale");
     }
     // Ritz values: skip the discrete null space (at or below zero_rel * the largest)
     const std::vector<double> ev(beta.begin(), beta.begin() + (k - 1));

@@ -71,6 +71,11 @@ __global__ void k_sub_combination(double* __restrict__ w, const double* __restri
     }
 }
 
+__global__ void k_scale(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+
 int grid_for(int64_t n) {
     const int64_t b = (n + kThreads - 1) / kThreads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 8192));
@@ -81,6 +86,12 @@ int grid_for(int64_t n) {
 int eig_mass_apply(int64_t nt, int N, const double* geo, const double* x, double* z, cudaStream_t s) {
     if (nt <= 0) return 0;
     k_mass_apply<<<grid_for(nt * N), kThreads, 0, s>>>(nt, N, geo, x, z);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int eig_scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+    if (n <= 0) return 0;
+    k_scale<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -182,9 +193,23 @@ std::vector<double> tridiag_eigenvector(const std::vector<double>& d, const std:
                 b[i + 1] -= dl[i] * b[i];
             }
         }
+        // near-singular pivots (clustered Ritz values) can grow the solution past the
+        // double range: the system is linear, so rescale the whole vector (solved part
+        // and remaining right-hand side alike) when an entry gets large
+        auto guard = [&](int i) {
+            if (std::fabs(b[i]) > 1e100)
+                for (double& v : b) v *= 1e-100;
+        };
         b[k - 1] /= dd[k - 1];
-        if (k > 1) b[k - 2] = (b[k - 2] - du[k - 2] * b[k - 1]) / dd[k - 2];
-        for (int i = k - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+        guard(k - 1);
+        if (k > 1) {
+            b[k - 2] = (b[k - 2] - du[k - 2] * b[k - 1]) / dd[k - 2];
+            guard(k - 2);
+        }
+        for (int i = k - 3; i >= 0; --i) {
+            b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+            guard(i);
+        }
     };
     auto normalise = [&](std::vector<double>& b) {
         double s = 0.0;

@@ -12,6 +12,8 @@ namespace dgm {
 // z = M_eps x for an FP64 E-field in the element-major orthonormalised layout
 // [t][3][N]: per element z[:, a] = eps_t G_t x[:, a], G = |det F| F^{-1} F^{-T}
 int eig_mass_apply(int64_t nt, int N, const double* geo, const double* x, double* z, cudaStream_t s);
+// y = a x (y is only written, never read: it may hold stale bits)
+int eig_scale(int64_t n, double a, const double* x, double* y, cudaStream_t s);
 // out[j] = V[j] . z for j < k (rows of V ld apart), fixed-order sums
 int eig_dots(const double* V, int64_t ld, int k, const double* z, int64_t n, double* out, cudaStream_t s);
 // w -= sum_{j<k} h[j] V[j]

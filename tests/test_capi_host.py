@@ -138,7 +138,10 @@ def test_tridiagonal_eigen_helper(capi):
     rng = np.random.default_rng(11)
     cases = [(rng.uniform(0, 1e4, 60), rng.uniform(0.1, 50, 59)),
              (np.repeat(rng.uniform(1, 10, 20), 2), np.tile([1e-9, 3.0], 20)[:39]),
-             (np.array([2.5]), np.array([]))]
+             (np.array([2.5]), np.array([])),
+             # 40 decoupled copies of one 3x3 block: every eigenvalue 40-fold, so inverse
+             # iteration meets 40 near-zero pivots (the solve must not overflow)
+             (np.tile([1.0, 2.0, 3.0], 40), np.tile([0.5, 0.5, 0.0], 40)[:119])]
     for d, e in cases:
         k = d.shape[0]
         T = np.diag(d) + (np.diag(e, 1) + np.diag(e, -1) if k > 1 else 0)
