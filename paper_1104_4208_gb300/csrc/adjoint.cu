@@ -29,42 +29,64 @@ struct Lay {
     }
 };
 
-// E at observation point o: v = F^{-T} sum_a c[:, a] phi'_a
+// E at observation point o, v = F^{-T} sum_a c[:, a] phi'_a, summed by the 32 lanes
+// of one warp: lane-strided partial sums, a fixed shuffle tree, then lane 0's value
+// broadcast (every lane returns the same bits)
 template <typename real>
-__device__ void eval_point(const ObsDev& O, const real* E, Lay L, int o, double v[3]) {
+__device__ void eval_point_warp(const ObsDev& O, const real* E, Lay L, int o, int lane, double v[3]) {
     const int64_t t = O.elem[o];
     const double* ph = O.phi + (size_t)o * L.N;
     double c[3] = {0, 0, 0};
-    for (int a = 0; a < L.N; ++a)
+    for (int a = lane; a < L.N; a += 32)
         for (int m = 0; m < 3; ++m) c[m] += ph[a] * (double)E[L.at(t, m, a)];
+    for (int m = 0; m < 3; ++m) {
+        for (int off = 16; off > 0; off >>= 1) c[m] += __shfl_down_sync(0xffffffffu, c[m], off);
+        c[m] = __shfl_sync(0xffffffffu, c[m], 0);
+    }
     const double* Fi = O.Finv + 9 * o;   // F^{-1} row-major
     for (int i = 0; i < 3; ++i) v[i] = Fi[0 * 3 + i] * c[0] + Fi[1 * 3 + i] * c[1] + Fi[2 * 3 + i] * c[2];
 }
 
+constexpr int kObsWarps = 8;
+constexpr int kMaxObs = 1024;
+
+// J += sum_o |E(x_o)|^2: one warp per point, then the points summed in order
 template <typename real>
 __global__ void k_observe(ObsDev O, const real* E, Lay L, double* J) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int o = 0; o < O.nobs; ++o) {
+    __shared__ double val[kMaxObs];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = warp; o < O.nobs; o += kObsWarps) {
         double v[3];
-        eval_point(O, E, L, o, v);
-        s += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        eval_point_warp(O, E, L, o, lane, v);
+        if (lane == 0) val[o] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     }
-    *J += s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int o = 0; o < O.nobs; ++o) s += val[o];
+        *J += s;
+    }
 }
 
-// e^ += M_eps^{-1} 2 P^T P E, points handled in order (several may share an element)
+// e^ += M_eps^{-1} 2 P^T P E: all points evaluated first (one warp per point; E is
+// not changed by this kernel), then their contributions added in point order
+// (several points may share an element)
 template <typename real>
 __global__ void k_obs_source(ObsDev O, const real* E, real* adj, Lay L) {
-    for (int o = 0; o < O.nobs; ++o) {
-        __shared__ double w[3];
-        if (threadIdx.x == 0) {
-            double v[3];
-            eval_point(O, E, L, o, v);
+    __shared__ double wo[kMaxObs][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = warp; o < O.nobs; o += kObsWarps) {
+        double v[3];
+        eval_point_warp(O, E, L, o, lane, v);
+        if (lane == 0) {
             const double* Fi = O.Finv + 9 * o;
-            for (int m = 0; m < 3; ++m) w[m] = 2.0 * (Fi[m * 3 + 0] * v[0] + Fi[m * 3 + 1] * v[1] + Fi[m * 3 + 2] * v[2]);
+            for (int m = 0; m < 3; ++m)
+                wo[o][m] = 2.0 * (Fi[m * 3 + 0] * v[0] + Fi[m * 3 + 1] * v[1] + Fi[m * 3 + 2] * v[2]);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int o = 0; o < O.nobs; ++o) {
+        const double* w = wo[o];
         const int64_t t = O.elem[o];
         const double* gi = O.ginv_eps + 6 * o;   // G^{-1} / eps
         const double* ph = O.phi + (size_t)o * L.N;
@@ -78,14 +100,17 @@ __global__ void k_obs_source(ObsDev O, const real* E, real* adj, Lay L) {
     }
 }
 
-// grad[t] -= sum_a e^[:, a] . G (E1 - E0)[:, a]
+// grad[t] -= sum_a e^[:, a] . G (E1 - E0)[:, a]; one warp per element, lanes over a,
+// fixed shuffle tree
 template <typename real>
 __global__ void k_grad_accum(int64_t nt, const double* geo, const real* adj, const real* E1, const real* E0, Lay L,
                              double* grad) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += nwarps) {
         const double* g = geo + t * kGeoStride + 6;
         double s = 0.0;
-        for (int a = 0; a < L.N; ++a) {
+        for (int a = lane; a < L.N; a += 32) {
             double d[3], e[3];
             for (int m = 0; m < 3; ++m) {
                 const int64_t i = L.at(t, m, a);
@@ -95,7 +120,8 @@ __global__ void k_grad_accum(int64_t nt, const double* geo, const real* adj, con
             s += e[0] * (g[0] * d[0] + g[1] * d[1] + g[2] * d[2]) + e[1] * (g[1] * d[0] + g[3] * d[1] + g[4] * d[2]) +
                  e[2] * (g[2] * d[0] + g[4] * d[1] + g[5] * d[2]);
         }
-        grad[t] -= s;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) grad[t] -= s;
     }
 }
 
@@ -123,21 +149,23 @@ template int add_point_source<float>(float*, int, int, int, int64_t, const doubl
 
 template <typename real>
 int adj_observe(const ObsDev& O, const real* E, int N, int K, int tiled, double* J, cudaStream_t s) {
-    k_observe<real><<<1, 32, 0, s>>>(O, E, Lay{N, K, tiled}, J);
+    if (O.nobs > kMaxObs) return -1;
+    k_observe<real><<<1, kObsWarps * 32, 0, s>>>(O, E, Lay{N, K, tiled}, J);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
 int adj_source(const ObsDev& O, const real* E, real* adj, int N, int K, int tiled, cudaStream_t s) {
-    k_obs_source<real><<<1, 128, 0, s>>>(O, E, adj, Lay{N, K, tiled});
+    if (O.nobs > kMaxObs) return -1;
+    k_obs_source<real><<<1, kObsWarps * 32, 0, s>>>(O, E, adj, Lay{N, K, tiled});
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
 int adj_grad(int64_t nt, const double* geo, const real* adj, const real* E1, const real* E0, int N, int K, int tiled,
              double* grad, cudaStream_t s) {
-    const int64_t blocks = (nt + 127) / 128;
-    k_grad_accum<real><<<(int)(blocks < 4096 ? blocks : 4096), 128, 0, s>>>(nt, geo, adj, E1, E0, Lay{N, K, tiled},
+    const int64_t blocks = (nt + 7) / 8;   // 8 warps of 32 per block, one warp per element
+    k_grad_accum<real><<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(nt, geo, adj, E1, E0, Lay{N, K, tiled},
                                                                            grad);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

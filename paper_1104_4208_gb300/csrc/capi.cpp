@@ -823,11 +823,7 @@ int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s) 
                                                       P->dSrcF, n, dt, s);
     if (P->tc) {
         // the source changes E in one element: only its tile's E traces are stale
-        const int tile = (int)(P->src_elem / dgm::kTcRows);
-        if (P->trE_valid && (P->trE_dirty_tile < 0 || P->trE_dirty_tile == tile))
-            P->trE_dirty_tile = tile;
-        else
-            P->trE_valid = false;
+        dgm::tc_mark_tile_dirty(P, P->src_elem / dgm::kTcRows);
     }
     return r ? cuda_fail(cudaGetLastError(), "source launch") : DGM_OK;
 }
@@ -1255,7 +1251,9 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
             if (rc) break;
             int r = v.f32 ? dgm::adj_source<float>(O, (const float*)Em, (float*)aE, N, K, tiled, 0)
                           : dgm::adj_source<double>(O, (const double*)Em, (double*)aE, N, K, tiled, 0);
-            P->trE_valid = false;
+            // the observation sources change e^ only in the observed elements' tiles
+            if (P->tc)
+                for (int o = 0; o < nobs; ++o) dgm::tc_mark_tile_dirty(P, oe[o] / dgm::kTcRows);
             r |= v.f32 ? dgm::adj_grad<float>(P->nt, geo, (const float*)aE, (const float*)Em, (const float*)Emm, N,
                                               K, tiled, dGrad, 0)
                        : dgm::adj_grad<double>(P->nt, geo, (const double*)aE, (const double*)Em, (const double*)Emm,

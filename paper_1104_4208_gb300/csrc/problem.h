@@ -56,7 +56,13 @@ struct dgm_problem {
     bool tc = false;
     int tc_grid = 0;                     // CTAs of the tensor-core kernels (autotuned)
     int tc_grid_cap = 0;                 // largest tc_grid the partial sums are sized for
-    int trE_dirty_tile = -1;             // with trE_valid: the one tile whose E traces are stale (point source)
+    // with trE_valid: tiles whose E traces are stale (point sources, adjoint observation
+    // sources); more than kMaxDirtyTiles of them clear trE_valid instead (one-tile
+    // refreshes are separate launches: beyond two, one pass over all tiles was faster
+    // on a 192-tile mesh)
+    static constexpr int kMaxDirtyTiles = 2;
+    int trE_dirty[kMaxDirtyTiles] = {};
+    int trE_ndirty = 0;
     dgm::TCArgs tca{};
     void* dTc = nullptr;                 // one allocation: tiled state, traces, tables, partials
     double* dTcGeo = nullptr;
@@ -100,9 +106,11 @@ int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* ene
 int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s);
 int tc_traces(dgm_problem* P, int which, cudaStream_t s);
 // make the E traces current before an H-phase: all tiles if they are invalid
-// (or if the H-phase needs E's energy partials), else the one tile a point
-// source changed
+// (or if the H-phase needs E's energy partials), else the tiles that point
+// sources changed
 int tc_ensure_traces_E(dgm_problem* P, bool energy, cudaStream_t s);
+// record that E changed inside one tile only (its traces are stale)
+void tc_mark_tile_dirty(dgm_problem* P, int64_t tile);
 int tc_state_energy(dgm_problem* P, double* slot, cudaStream_t s);
 int tc_check_error(dgm_problem* P);
 }  // namespace dgm

@@ -249,16 +249,25 @@ int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const 
 int tc_traces(dgm_problem* P, int which, cudaStream_t s) {
     if (tc_launch_traces(P->tca, P->tc_grid, which, s)) return cuda_err(cudaGetLastError(), "traces launch");
     (which == 0 ? P->trE_valid : P->trH_valid) = true;
-    if (which == 0) P->trE_dirty_tile = -1;
+    if (which == 0) P->trE_ndirty = 0;
     return DGM_OK;
 }
 
+void tc_mark_tile_dirty(dgm_problem* P, int64_t tile) {
+    if (!P->trE_valid) return;   // a full refresh is pending anyway
+    for (int i = 0; i < P->trE_ndirty; ++i)
+        if (P->trE_dirty[i] == tile) return;
+    if (P->trE_ndirty < dgm_problem::kMaxDirtyTiles)
+        P->trE_dirty[P->trE_ndirty++] = (int)tile;
+    else
+        P->trE_valid = false;
+}
+
 int tc_ensure_traces_E(dgm_problem* P, bool energy, cudaStream_t s) {
-    if (!P->trE_valid || (P->trE_dirty_tile >= 0 && energy)) return tc_traces(P, 0, s);
-    if (P->trE_dirty_tile >= 0) {
-        if (tc_launch_traces_tile(P->tca, 0, P->trE_dirty_tile, s)) return cuda_err(cudaGetLastError(), "traces launch");
-        P->trE_dirty_tile = -1;
-    }
+    if (!P->trE_valid || (P->trE_ndirty > 0 && energy)) return tc_traces(P, 0, s);
+    for (int i = 0; i < P->trE_ndirty; ++i)
+        if (tc_launch_traces_tile(P->tca, 0, P->trE_dirty[i], s)) return cuda_err(cudaGetLastError(), "traces launch");
+    P->trE_ndirty = 0;
     return DGM_OK;
 }
 
@@ -283,7 +292,7 @@ int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s) {
     if (tc_launch_phase_E(P->tca, P->tc_grid, dt, energy ? 1 : 0, s))
         return cuda_err(cudaGetLastError(), "E-phase launch");
     P->trE_valid = true;
-    P->trE_dirty_tile = -1;
+    P->trE_ndirty = 0;
     return DGM_OK;
 }
 
