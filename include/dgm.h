@@ -309,6 +309,18 @@ int dgm_project_device(dgm_problem* prob, int q1d, const double* E_pts, const do
                        void* stream);
 int dgm_eval_device(dgm_problem* prob, int q1d, double* E_pts, double* H_pts, void* stream);
 
+/* Host-array forms of the same, blocking:
+ * dgm_quad_points: *count = nt * nq * 3; with xyz != NULL also the physical
+ * points x = X0 + F xh_q of every element, [nt][nq][3] (computed on the device;
+ * NULL xyz is a size query).
+ * dgm_project: as dgm_project_device from host arrays [nt][nq][3] (one may be
+ * NULL, not both).
+ * dgm_eval: as dgm_eval_device into host arrays (one may be NULL, not both).
+ * Each allocates and frees a device buffer of the arrays' size. */
+int dgm_quad_points(dgm_problem* prob, int q1d, int64_t* count, double* xyz);
+int dgm_project(dgm_problem* prob, int q1d, const double* E_pts, const double* H_pts);
+int dgm_eval(dgm_problem* prob, int q1d, double* E_pts, double* H_pts);
+
 /* Reference tables of the library (host, FP64, orthonormalised basis
  * phi_a / ||phi_a||), for inspection and tests:
  *   which = 0,1,2: D_x, D_y, D_z  [N3(p-1)][N3(p)], entry (b,a) = (d phi_a, phi_b)

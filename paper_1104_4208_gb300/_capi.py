@@ -89,6 +89,9 @@ _SIGS = {
     "dgm_element_maps": ([_vp, _pd], C.c_int),
     "dgm_project_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
     "dgm_eval_device": ([_vp, C.c_int, _vp, _vp, _vp], C.c_int),
+    "dgm_quad_points": ([_vp, C.c_int, _pi64, _pd], C.c_int),
+    "dgm_project": ([_vp, C.c_int, _pd, _pd], C.c_int),
+    "dgm_eval": ([_vp, C.c_int, _pd, _pd], C.c_int),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -337,3 +340,27 @@ def dgm_batch_destroy(batch):
 def dgm_batch_run(batch, dts, nsteps, stream=None, energy_out=None):
     dts = np.ascontiguousarray(dts, dtype=np.float64)
     _check(_lib.dgm_batch_run(batch, _dptr(dts), int(nsteps), stream, _dptr(energy_out)))
+
+
+def dgm_quad_points(prob, q1d, nt):
+    """-> physical quadrature points [nt][nq][3] of the rule with q1d points per direction."""
+    count = _i64()
+    _check(_lib.dgm_quad_points(prob, int(q1d), C.byref(count), None))
+    out = np.empty(count.value)
+    _check(_lib.dgm_quad_points(prob, int(q1d), C.byref(count), _dptr(out)))
+    return out.reshape(nt, -1, 3)
+
+
+def dgm_project(prob, q1d, E_pts, H_pts=None):
+    E = np.ascontiguousarray(E_pts, dtype=np.float64) if E_pts is not None else None
+    H = np.ascontiguousarray(H_pts, dtype=np.float64) if H_pts is not None else None
+    _check(_lib.dgm_project(prob, int(q1d), _dptr(E), _dptr(H)))
+
+
+def dgm_eval(prob, q1d, nt, want_E=True, want_H=False):
+    """-> (E_pts, H_pts) [nt][nq][3] each (None where not wanted)."""
+    nq = int(q1d) ** 3
+    E = np.empty((nt, nq, 3)) if want_E else None
+    H = np.empty((nt, nq, 3)) if want_H else None
+    _check(_lib.dgm_eval(prob, int(q1d), _dptr(E), _dptr(H)))
+    return E, H

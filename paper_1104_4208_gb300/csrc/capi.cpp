@@ -15,6 +15,7 @@
 #include "problem.h"
 #include "adjoint.h"
 #include "eigen.h"
+#include "fieldio.h"
 
 namespace dgm {
 
@@ -1784,6 +1785,62 @@ int dgm_reference_table(int p, int which, double* out, int64_t count, int64_t* n
         }
         std::memcpy(out, v->data(), v->size() * sizeof(double));
     }
+    return DGM_OK;
+}
+
+int dgm_quad_points(dgm_problem* P, int q1d, int64_t* count, double* xyz) {
+    if (!P || !count || q1d < 1 || q1d > 32) {
+        set_error("dgm_quad_points: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const int nq = q1d * q1d * q1d;
+    *count = P->nt * nq * 3;
+    if (!xyz) return DGM_OK;
+    std::vector<double> x, w, col;
+    dgm::collapsed_rule(q1d, x, w, col);
+    DevBuf buf;
+    DGM_CUDA(cudaMalloc(&buf.p, (x.size() + (size_t)*count) * sizeof(double)));
+    double* dxh = (double*)buf.p;
+    double* dout = dxh + x.size();
+    DGM_CUDA(cudaMemcpy(dxh, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (dgm::launch_quad_points(P->nt, nq, P->dMaps, dxh, dout, 0))
+        return cuda_fail(cudaGetLastError(), "quad points launch");
+    DGM_CUDA(cudaMemcpy(xyz, dout, (size_t)*count * sizeof(double), cudaMemcpyDeviceToHost));
+    return DGM_OK;
+}
+
+int dgm_project(dgm_problem* P, int q1d, const double* E_pts, const double* H_pts) {
+    if (!P || (!E_pts && !H_pts) || q1d < 1 || q1d > 32) {
+        set_error("dgm_project: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)P->nt * q1d * q1d * q1d * 3;
+    DevBuf buf;
+    DGM_CUDA(cudaMalloc(&buf.p, ((E_pts ? n : 0) + (H_pts ? n : 0)) * sizeof(double)));
+    double* dE = E_pts ? (double*)buf.p : nullptr;
+    double* dH = H_pts ? (double*)buf.p + (E_pts ? n : 0) : nullptr;
+    if (dE) DGM_CUDA(cudaMemcpy(dE, E_pts, n * sizeof(double), cudaMemcpyHostToDevice));
+    if (dH) DGM_CUDA(cudaMemcpy(dH, H_pts, n * sizeof(double), cudaMemcpyHostToDevice));
+    int rc = dgm_project_device(P, q1d, dE, dH, nullptr);
+    if (rc) return rc;
+    DGM_CUDA(cudaDeviceSynchronize());
+    return DGM_OK;
+}
+
+int dgm_eval(dgm_problem* P, int q1d, double* E_pts, double* H_pts) {
+    if (!P || (!E_pts && !H_pts) || q1d < 1 || q1d > 32) {
+        set_error("dgm_eval: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)P->nt * q1d * q1d * q1d * 3;
+    DevBuf buf;
+    DGM_CUDA(cudaMalloc(&buf.p, ((E_pts ? n : 0) + (H_pts ? n : 0)) * sizeof(double)));
+    double* dE = E_pts ? (double*)buf.p : nullptr;
+    double* dH = H_pts ? (double*)buf.p + (E_pts ? n : 0) : nullptr;
+    int rc = dgm_eval_device(P, q1d, dE, dH, nullptr);
+    if (rc) return rc;
+    if (dE) DGM_CUDA(cudaMemcpy(E_pts, dE, n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (dH) DGM_CUDA(cudaMemcpy(H_pts, dH, n * sizeof(double), cudaMemcpyDeviceToHost));
     return DGM_OK;
 }
 

@@ -52,6 +52,14 @@ class Solver:
         unchanged) and keep the fastest; -> (configs, ms_per_step, chosen)."""
         return capi.dgm_autotune(self.prob, steps)
 
+    def project(self, fn, q1d=None):
+        """Set E, H to the covariant L2 projections of fn(x) -> (E(x), H(x)) (arrays
+        [..., 3] for points x [..., 3]) sampled at this problem's quadrature points."""
+        q1d = q1d or self.p + 2
+        x = capi.dgm_quad_points(self.prob, q1d, self.nt)
+        E, H = fn(x)
+        capi.dgm_project(self.prob, q1d, E, H)
+
     def resonances(self, m=300, nev=8, zero_rel=1e-8):
         """Smallest nonzero cavity resonance frequencies by Lanczos on the GPU
         operator (FP64); -> (omega, relative residuals)."""
