@@ -156,6 +156,19 @@ int dgm_kick(dgm_problem* prob, int which, double dt, void* stream);
  * Blocks until the energies are on the host when energy_out != NULL. */
 int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* energy_out);
 
+/* Higher-order symplectic time stepping (Sec. 3 leaves the explicit integrator
+ * open; the spatial operator conserves energy, so symplectic compositions keep
+ * the energy bounded).  order = 2: the leapfrog of dgm_run.  order = 4: every
+ * step of size dt is the symmetric composition of three leapfrog steps of
+ * sizes w1 dt, w0 dt, w1 dt with w1 = 1/(2 - 2^{1/3}), w0 = 1 - 2 w1 (the
+ * triple-jump construction of Yoshida, 1990), with adjacent half kicks merged:
+ * 3 E-kicks and 3 H-kicks per step.  The fields start and end synchronized, as
+ * in dgm_run.  The substep |w0| dt = 1.70 dt must itself be stable, so dt is
+ * bounded by about 0.59 of the leapfrog bound.  Point sources are not
+ * supported (DGM_ERR_UNSUPPORTED): they are sampled at leapfrog midpoints.
+ * Blocks until the steps are done; no energies are recorded (use dgm_energy). */
+int dgm_run_composed(dgm_problem* prob, double dt, int64_t nsteps, int order, void* stream);
+
 /* Stability bound of the explicit scheme (Sec. 3): dt <= 2 / sqrt(rho) with rho
  * the spectral radius of M_mu^{-1} C_h M_eps^{-1} C_h^T (face unknowns included
  * for the stabilized flux), estimated by `iters` power iterations (Sec. 3

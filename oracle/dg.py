@@ -540,3 +540,24 @@ def resonances(dg, zero_rel=1e-8):
     lam = np.sort(sl.eigh(Kc, sl.block_diag(*A_["ME"]), eigvals_only=True))
     zero = lam <= zero_rel * lam.max()
     return np.sqrt(lam[~zero]), int(zero.sum())
+
+
+def run_composed(dg, E0, H0, dt, nsteps, order, K0=None):
+    """Symmetric composition of leapfrog steps (Sec. 3 admits any explicit
+    integrator; compositions of the symplectic leapfrog stay symplectic).
+    order 2: one leapfrog step of size dt per step.  order 4: three leapfrog
+    steps of sizes w1 dt, w0 dt, w1 dt with w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1
+    (Yoshida's triple jump).  Each substep is a complete OracleDG.run step with
+    its own opening and closing half kicks (no merging).  Returns E, H, K."""
+    if order == 2:
+        ws = [1.0]
+    elif order == 4:
+        w1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+        ws = [w1, 1.0 - 2.0 * w1, w1]
+    else:
+        raise ValueError(order)
+    E, H, K = np.array(E0, dtype=float), np.array(H0, dtype=float), K0
+    for _ in range(nsteps):
+        for w in ws:
+            E, H, K, _ = dg.run(E, H, w * dt, 1, K0=K)
+    return E, H, K

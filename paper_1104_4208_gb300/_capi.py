@@ -69,6 +69,7 @@ _SIGS = {
     "dgm_get_fields_device": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "dgm_kick": ([_vp, C.c_int, C.c_double, _vp], C.c_int),
     "dgm_run": ([_vp, C.c_double, _i64, _vp, _pd], C.c_int),
+    "dgm_run_composed": ([_vp, C.c_double, _i64, C.c_int, _vp], C.c_int),
     "dgm_run_timed": ([_vp, C.c_double, _i64, _vp, _pd, C.POINTER(dgm_run_stats)], C.c_int),
     "dgm_energy": ([_vp, _pd], C.c_int),
     "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
@@ -364,3 +365,7 @@ def dgm_eval(prob, q1d, nt, want_E=True, want_H=False):
     H = np.empty((nt, nq, 3)) if want_H else None
     _check(_lib.dgm_eval(prob, int(q1d), _dptr(E), _dptr(H)))
     return E, H
+
+
+def dgm_run_composed(prob, dt, nsteps, order=4, stream=None):
+    _check(_lib.dgm_run_composed(prob, float(dt), int(nsteps), int(order), stream))

@@ -741,6 +741,46 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
     return DGM_OK;
 }
 
+int dgm_run_composed(dgm_problem* P, double dt, int64_t nsteps, int order, void* stream) {
+    if (!P || nsteps < 0 || !std::isfinite(dt) || (order != 2 && order != 4)) {
+        set_error("dgm_run_composed: bad argument (order must be 2 or 4)");
+        return DGM_ERR_INVALID_ARG;
+    }
+    if (P->src_on) {
+        set_error("dgm_run_composed: point sources are evaluated at leapfrog midpoints; use dgm_run");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    if (nsteps == 0) return DGM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // substep weights: one leapfrog step (order 2), or the symmetric triple jump
+    // w1, w0, w1 with w1 = 1 / (2 - 2^{1/3}), w0 = 1 - 2 w1 (order 4)
+    double w[3] = {1.0, 0.0, 0.0};
+    int nw = 1;
+    if (order == 4) {
+        const double c = std::cbrt(2.0);
+        w[0] = w[2] = 1.0 / (2.0 - c);
+        w[1] = 1.0 - 2.0 * w[0];
+        nw = 3;
+    }
+    // each substep is kick-drift-kick; adjacent H half kicks are merged
+    int rc = phase_H(P, 0.5 * w[0] * dt, 0.0, 1.0, nullptr, s);
+    for (int64_t n = 0; n < nsteps && !rc; ++n) {
+        for (int k = 0; k < nw && !rc; ++k) {
+            rc = phase_E(P, w[k] * dt, s);
+            if (rc) break;
+            const bool last = n == nsteps - 1 && k == nw - 1;
+            const double h = last ? 0.5 * w[k] * dt : 0.5 * (w[k] + w[(k + 1) % nw]) * dt;
+            rc = phase_H(P, h, 0.0, 1.0, nullptr, s);
+        }
+    }
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dgm_run_composed");
+    if (P->tc && (rc = dgm::tc_check_error(P))) return rc;
+    P->time += nsteps * dt;
+    return DGM_OK;
+}
+
 int dgm_energy(dgm_problem* P, double* W) {
     if (!P || !W) {
         set_error("dgm_energy: null argument");

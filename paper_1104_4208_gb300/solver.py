@@ -42,6 +42,10 @@ class Solver:
     def kick(self, which, dt, stream=None):
         capi.dgm_kick(self.prob, which, dt, stream)
 
+    def run_composed(self, dt, nsteps, order=4, stream=None):
+        """Symplectic composition of leapfrog steps (order 2 or 4); no energies."""
+        capi.dgm_run_composed(self.prob, dt, nsteps, order, stream)
+
     def run(self, dt, nsteps, stream=None, energies=False):
         out = np.empty(nsteps + 1) if energies else None
         capi.dgm_run(self.prob, dt, nsteps, stream, out)

@@ -406,6 +406,45 @@ def test_cavity_resonances_converge_under_p_refinement():
     assert np.max(np.abs(om[:8] - exact) / exact) < 2e-3
 
 
+@pytest.mark.parametrize("flux", ["central", "stabilized"])
+def test_composed_integrators_have_their_order(flux):
+    """Sec. 3 (any explicit integrator): the leapfrog and its symmetric triple-jump
+    composition against the exact solution of the semi-discrete system,
+    y(T) = expm(L T) y(0) with L the block operator of the kicks (one Kuhn cube,
+    p = 2).  Halving dt divides the error by 4 (order 2) and by 16 (order 4); a
+    step forward then backward returns the start (symmetric methods)."""
+    import scipy.linalg as sl
+    from oracle.dg import run_composed
+    m = kuhn_cube_mesh(1)
+    dg = OracleDG(m.xyz, m.tets, 2, 1.0, 1.0, flux=flux)
+    A = dg.assemble()
+    nE, nH = dg.sizeE, dg.sizeH
+    nK = dg.sizeK if flux == "stabilized" else 0
+    MEinv, MHinv = sl.block_diag(*A["MEinv"]), sl.block_diag(*A["MHinv"])
+    L = np.zeros((nE + nH + nK, nE + nH + nK))
+    L[:nE, nE:nE + nH] = MEinv @ A["CE"].toarray()
+    L[nE:nE + nH, :nE] = MHinv @ A["CH"].toarray()
+    if nK:
+        L[:nE, nE + nH:] = MEinv @ A["CEK"].toarray()
+        L[nE + nH:, :nE] = sl.block_diag(*A["MFinv"]) @ A["S"].toarray()
+    rng = np.random.default_rng(0)
+    E0, H0 = rng.standard_normal(nE), rng.standard_normal(nH)
+    K0 = np.zeros(nK) if nK else None
+    y0 = np.concatenate([E0, H0, np.zeros(nK)])
+    T = 0.05
+    yT = sl.expm(L * T) @ y0
+    for order, lo, hi in ((2, 3.8, 4.2), (4, 14.0, 18.0)):
+        errs = []
+        for ns in (10, 20):
+            E, H, K = run_composed(dg, E0, H0, T / ns, ns, order, K0=K0)
+            y = np.concatenate([E, H, K if nK else np.zeros(0)])
+            errs.append(np.linalg.norm(y - yT) / np.linalg.norm(yT))
+        assert lo < errs[0] / errs[1] < hi, (order, errs)
+    E, H, K = run_composed(dg, E0, H0, T / 10, 1, 4, K0=K0)
+    E2, H2, _ = run_composed(dg, E, H, -T / 10, 1, 4, K0=K)
+    assert np.abs(E2 - E0).max() < 1e-13 and np.abs(H2 - H0).max() < 1e-13
+
+
 def test_adjoint_gradient_matches_finite_differences():
     """Discrete adjoint of the leapfrog (objective J = sum_n sum_o |E^n(x_o)|^2,
     derivative with respect to per-element eps) vs central finite differences with
