@@ -339,6 +339,31 @@ def test_te110_cavity_convergence():
     assert errs[0] / errs[1] > 4.0
 
 
+@pytest.mark.parametrize("flux,e_lo,e_hi", [("central", 0.8, 1.3), ("stabilized", 2.0, 9.0)])
+def test_h_refinement_rates(flux, e_lo, e_hi):
+    """TE110 cavity mode, p = 2 (E of degree 2, H of degree 1), n = 4 -> 8, to
+    t = 0.25 with dt = 0.1 h / p^2.  H converges at rate p (about 2) with either
+    flux.  E converges at rate p - 1 with the central flux, one order below H,
+    as the flux is known to cost, and at rate >= p with the stabilized flux of
+    Sec. 2.1.  Observed E rates: 1.0 and 2.3; H rates: 2.1 and 2.0."""
+    rates_E, errs = [], []
+    for n in (4, 8):
+        m = kuhn_cube_mesh(n)
+        dg = OracleDG(m.xyz, m.tets, 2, 1.0, 1.0, flux=flux)
+        E0 = project(dg, lambda x: te110_fields(x, 0.0)[0], 2)
+        H0 = project(dg, lambda x: te110_fields(x, 0.0)[1], 1)
+        dt = 0.1 / n / 4
+        N = int(round(0.25 / dt))
+        E, H, _, _ = dg.run(E0, H0, dt, N)
+        eE, rE = l2_error(dg, E, lambda x: te110_fields(x, N * dt)[0], 2)
+        eH, rH = l2_error(dg, H, lambda x: te110_fields(x, N * dt)[1], 1)
+        errs.append((eE / rE, eH / rH))
+    rE = math.log2(errs[0][0] / errs[1][0])
+    rH = math.log2(errs[0][1] / errs[1][1])
+    assert e_lo < rE < e_hi, (rE, errs)
+    assert rH > 1.7, (rH, errs)
+
+
 def test_spurious_modes_removed_by_stabilization():
     """Sec. 2.1: the central flux leaves many non-physical zero modes; the stabilized
     central flux removes them.  On the PEC unit cube (n=2, p=2) the null space of the
