@@ -57,6 +57,40 @@ def test_phi3_matches_printed_formula_sympy():
                 assert grad[r, q, d] == pytest.approx(float(dphi[d].subs(sub)), abs=1e-12)
 
 
+# the 16 monomials of the printed support of the 3D d/dx relation (Sec. 4.2.2):
+# shifts (i, j, k) of the terms with D_x, then of the terms without
+_SUPPORT_DX_D = [(1, 1, 2), (1, 0, 3), (0, 2, 2), (0, 1, 3), (1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2),
+                 (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1)]
+_SUPPORT_DX_0 = [(1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2)]
+
+
+def _support_nullspace(i, j, k, drop=None):
+    """Rational nullspace of sum_m c_m D_x phi_{(i,j,k)+s_m} + sum_m c_m phi_{(i,j,k)+s_m} = 0
+    as a polynomial identity (coefficient comparison in x, y, z)."""
+    cols = []
+    for s, deriv in [(s, True) for s in _SUPPORT_DX_D] + [(s, False) for s in _SUPPORT_DX_0]:
+        (X, Y, Z), phi = _sympy_phi3(i + s[0], j + s[1], k + s[2])
+        poly = sp.Poly(sp.expand(sp.cancel(sp.together(phi))), X, Y, Z)
+        cols.append(poly.diff(X) if deriv else poly)
+    if drop is not None:
+        cols = [c for n, c in enumerate(cols) if n != drop]
+    monos = sorted({m for c in cols for m in c.as_dict()})
+    return sp.Matrix([[c.as_dict().get(m, 0) for c in cols] for m in monos]).nullspace()
+
+
+def test_printed_3d_dx_support_carries_one_relation():
+    """Sec. 4.2.2 names the 16 monomials of the d/dx relation for the 3D shape
+    functions (coefficients not printed).  At generic indices the ansatz on that
+    support has exactly one solution (up to scale), with all 16 coefficients
+    nonzero, so the support is minimal; without the leading term S_j S_k^3 D_x
+    no relation is left.  Exact rational arithmetic."""
+    for ijk in [(1, 0, 1), (1, 1, 1), (2, 1, 0)]:
+        ns = _support_nullspace(*ijk)
+        assert len(ns) == 1, ijk
+        assert all(v != 0 for v in ns[0]), ijk
+    assert len(_support_nullspace(1, 1, 1, drop=3)) == 0
+
+
 def test_psi2_matches_eq4_sympy():
     X, Y = sp.symbols("x y")
     pts = [(sp.Rational(1, 7), sp.Rational(2, 5)), (sp.Rational(3, 8), sp.Rational(1, 9))]
