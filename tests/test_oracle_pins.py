@@ -306,6 +306,58 @@ def test_exact_curl_of_polynomial_fields():
     assert np.abs(dE - ce).max() < 1e-11 * np.abs(ce).max()
 
 
+def test_local_kicks_exact_and_equal_to_assembly():
+    """The element-local kick path (used for sampled parity at full size) gives the
+    exact curl of the polynomial fields of the test above on every element, and on
+    random fields the same kicks as the assembled operator."""
+    p = 4
+    m = kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    dg = OracleDG(m.xyz, m.tets, p, 1.0, 1.0)
+    E, curlE, H, curlH = _poly_fields()
+    ts = np.arange(dg.nt)
+    c = project(dg, curlE, p - 1)
+    dH = dg.local_kick_H(project(dg, E, p), ts, 1.0).ravel()
+    assert np.abs(dH + c).max() < 1e-12 * np.abs(c).max()
+    ce = project(dg, curlH, p)
+    dE = dg.local_kick_E(project(dg, H, p - 1), ts, 1.0).ravel()
+    assert np.abs(dE - ce).max() < 1e-11 * np.abs(ce).max()
+    A = dg.assemble()
+    rng = np.random.default_rng(8)
+    Er, Hr = rng.standard_normal(dg.sizeE), rng.standard_normal(dg.sizeH)
+    ref_H = 0.3 * dg._blockmul(A["MHinv"], A["CH"] @ Er)
+    ref_E = 0.3 * dg._blockmul(A["MEinv"], A["CE"] @ Hr)
+    assert np.abs(dg.local_kick_H(Er, ts, 0.3).ravel() - ref_H).max() < 1e-12 * np.abs(ref_H).max()
+    assert np.abs(dg.local_kick_E(Hr, ts, 0.3).ravel() - ref_E).max() < 1e-12 * np.abs(ref_E).max()
+
+
+def test_point_observation_and_source_closed_forms():
+    """Point evaluation and the point source on a linear field, which the degree-2
+    space reproduces exactly: the observation rows give the field at the points,
+    point_values gives it at mapped reference points, located reference points map
+    back to the physical points, and the dipole source vector contracted with the
+    field's coefficients is -f dir . E(x_s) (its entries are -f dir . N_{a,m}(x_s))."""
+    from oracle.dg import observation_matrix, locate_points, dipole_source_vector
+    from oracle.project import point_values
+    m = kuhn_cube_mesh(2, jitter=0.15, seed=5, shuffle_local=True)
+    dg = OracleDG(m.xyz, m.tets, 2, 1.0, 1.0)
+    A = np.array([[0.3, -1.0, 0.2], [0.5, 0.1, -0.7], [1.1, 0.4, 0.0]])
+    b = np.array([0.2, -0.1, 0.4])
+    lin = lambda x: x @ A.T + b
+    Ec = project(dg, lin, 2)
+    rng = np.random.default_rng(21)
+    pts = rng.uniform(0.05, 0.95, (6, 3))
+    P = observation_matrix(dg, pts)
+    assert np.abs((P @ Ec).reshape(-1, 3) - lin(pts)).max() < 1e-12
+    ts, xhs = locate_points(dg, pts)
+    for t, xh, x in zip(ts, xhs, pts):
+        assert np.abs(dg.geo.to_phys(t, xh) - x).max() < 1e-14
+        assert xh.min() > -1e-12 and xh.sum() < 1 + 1e-12
+        assert np.abs(point_values(dg, Ec, 2, t, xh[None, :])[0] - lin(x)).max() < 1e-12
+    xs, d, f = np.array([0.43, 0.52, 0.47]), np.array([0.3, -0.2, 0.9]), 1.7
+    src = dipole_source_vector(dg, xs, d, f)
+    assert src @ Ec == pytest.approx(-f * d @ lin(xs), rel=1e-12)
+
+
 def test_flat_mass_closed_form():
     """Sec. 3.3.1: flat elements, constant eps: M = |det F| eps (F^{-1} F^{-T}) (x) diag(||phi||^2)."""
     p = 3
