@@ -617,25 +617,31 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     from workloads.configs import make_workload
-    w = make_workload(args.workload)
+    batched = args.workload == "batched_64"
+    # the batched workload has no single configuration: step i samples run i mod 64
+    pick = (lambda i: make_workload(f"batched_64:{i % 64}")) if batched else (lambda i: make_workload(args.workload))
+    w = pick(0)
     per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
     total_el = 0
+    total_dof = 0
     t_total = 0.0
-    D = dof_per_elem(w.p)
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(w, per_step)
+        wi = pick(i) if batched else w
+        r = cpu_oracle_rate(wi, per_step)
         if r is None:
             return {"impl": "reference", "unavailable": "CPU oracle failed to run"}
         if i >= args.warmup:
             total_el += r["elements"]
+            total_dof += r["elements"] * dof_per_elem(wi.p)
             t_total += r["seconds"]
-    value = total_el * D / t_total
+    value = total_dof / t_total
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "tets": w.nt, "p": w.p, "precision": "fp64"},
+            "config": ({"workload": "batched_64", "runs_sampled": min(64, args.steps), "precision": "fp64"}
+                       if batched else {"workload": w.name, "tets": w.nt, "p": w.p, "precision": "fp64"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": f"{total_el} random elements of {w.name} over {args.steps} steps, "
+                             "sample": f"{total_el} random elements of {args.workload} over {args.steps} steps, "
                                        "H- and E-kick, 1 thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -8,6 +8,7 @@ planewave_n32_p6  periodic [0,1]^3, n=32 (196,608 tets), p=6, eps=mu=1,
 pulse_n32_p4      the pulse_n16_p4 recipe on n=32 (196,608 tets, p=4): its state
                   (130 MB in fp32) no longer fits in the 129 MB L2
 batched_64        64 runs, n in {8,12,16}, jitter 0.1h, p in {2..6}, eps~U[1,4], dipole source, 500 steps
+                  (make_workload("batched_64:r") builds run r alone)
 adjoint_n16_p4    mesh/p of pulse_n16_p4, 8 observation points, 500 steps, checkpoint every 50
 
 The time step is dt = 0.2 h / p^2 with h = 1/n, the polynomial order p is the
@@ -75,9 +76,15 @@ def make_workload(name, n=None, p=None, steps=None, shuffle_local=False):
         "adjoint_n16_p4": dict(n=16, p=4, steps=500, periodic=False, jitter=0.15, seed=1002,
                                init="pulse", eps_range=(1.0, 4.0)),
     }
-    if name not in table:
+    if name.startswith("batched_64:"):
+        # run r of the batched workload: its own n, p, seed; jitter 0.1h, eps ~ U[1,4]
+        n_r, p_r, seed_r = batched_runs(64)[int(name.split(":")[1])]
+        kw = dict(n=n_r, p=p_r, steps=500, periodic=False, jitter=0.1, seed=seed_r, init="pulse",
+                  eps_range=(1.0, 4.0))
+    elif name not in table:
         raise KeyError(name)
-    kw = dict(table[name])
+    else:
+        kw = dict(table[name])
     if n is not None:
         kw["n"] = n
     if p is not None:
