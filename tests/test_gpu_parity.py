@@ -714,7 +714,7 @@ def test_resonances_reject_reduced_precision(capi):
 
 def test_resonances_ignore_stale_device_memory(capi):
     """Workspace that dgm_resonances allocates is only written before it is read:
-    after device memory full of NaN bit patterns is freed back to the driver (so
+    after device memory full of NaN bit patterns is released by the caching allocator (so
     later allocations may reuse it), the frequencies and residuals are the same as
     on clean memory and every one converges."""
     import torch
