@@ -82,10 +82,13 @@ enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2, DG
 
 typedef struct dgm_options {
     int flux;           /* dgm_flux */
-    double alpha0;      /* alpha = alpha0 * p^2 (Sec. 2.1, "alpha scales with p^2") */
+    double alpha0;      /* alpha = alpha0 * p^2 (Sec. 2.1: alpha grows like p^2) */
     int precision;      /* dgm_precision */
     int variant;        /* 0 = automatic kernel choice */
-    int checks;         /* nonzero: validate inputs (CFL bound, NaN scan) */
+    int checks;         /* reserved: accepted, no effect.  Inputs are always validated at
+                           creation; an unstable dt shows as DGM_ERR_UNSTABLE from the energy
+                           watchdog of dgm_run (energies requested), and dgm_estimate_dt
+                           gives the bound */
 } dgm_options;
 
 typedef struct dgm_ctx dgm_ctx;
