@@ -11,7 +11,8 @@ reading stated in the package header:
 [[E]] = E_T - E_nbr on dT (relative to nu_T), {{H}} = (H_T + H_nbr)/2; on a
 PEC face the ghost state is E_nbr = -E_T, H_nbr = H_T.  The central flux is
 the same system without H^F.  Spaces: E, e of degree p, H, h of degree p-1
-(Sec. 2, V^{k+1} x V^k); H^F tangential of degree p on each face.
+(Sec. 2, V^{k+1} x V^k) or, for the equal-order variant, of degree p; H^F
+tangential of degree p on each face.
 
 Every integral is a Gauss sum in physical space over covariant basis functions
 N_{a,m}(x) = F^{-T} e_m phi_a(Phi^{-1}(x)) (Sec. 3.2.1), curl by the chain rule:
@@ -59,14 +60,19 @@ def _curl_values(Finv, pgrad):
 
 class OracleDG:
     def __init__(self, xyz, tets, p, eps, mu, vertex_key=None, flux="central",
-                 alpha0=1.0, chunk=64):
+                 alpha0=1.0, chunk=64, h_degree=None):
+        """h_degree: degree of H; p - 1 (default, the spaces V^{k+1} x V^k of
+        Sec. 2) or p (the equal-order variant: E and H of the same degree)."""
         if p < 1:
             raise ValueError("p >= 1 required")
+        self.pH = p - 1 if h_degree is None else int(h_degree)
+        if self.pH not in (p - 1, p):
+            raise ValueError("h_degree must be p - 1 or p")
         self.geo = Geometry(xyz, tets, vertex_key)
         self.p = p
         self.nt = self.geo.nt
         self.NE = n3(p)
-        self.NH = n3(p - 1)
+        self.NH = n3(self.pH)
         self.N2 = n2(p)
         self.eps = np.broadcast_to(np.asarray(eps, dtype=float), (self.nt,)).copy()
         self.mu = np.broadcast_to(np.asarray(mu, dtype=float), (self.nt,)).copy()
@@ -79,7 +85,7 @@ class OracleDG:
         self.vq, self.vw = tet_rule(q)
         self.fq, self.fw = tri_rule(q)
         self.phiE, self.gE = phi3(p, self.vq)
-        self.phiH, self.gH = phi3(p - 1, self.vq)
+        self.phiH, self.gH = phi3(self.pH, self.vq)
         self.nfaces = len(self.geo.faces)
         self._assembled = None
 
@@ -157,14 +163,14 @@ class OracleDG:
         nb = g.nbr[ts, f]
         interior = nb >= 0
         NEo = self._eval_at(ts, x, self.p)
-        NHo = self._eval_at(ts, x, self.p - 1)
+        NHo = self._eval_at(ts, x, self.pH)
         NEn = np.zeros_like(NEo)
         NHn = np.zeros_like(NHo)
         if np.any(interior):
             ti = ts[interior]
             xn = x[interior] + g.shift[ti, f][:, None, :]
             NEn[interior] = self._eval_at(nb[interior], xn, self.p)
-            NHn[interior] = self._eval_at(nb[interior], xn, self.p - 1)
+            NHn[interior] = self._eval_at(nb[interior], xn, self.pH)
         cown = np.where(interior, 0.5, 1.0)     # PEC ghost: [[E]] = 2E, {{H}} = H
         nuB = nu[:, None, None, None, :]
         ExnuO = np.cross(NEo, np.broadcast_to(nuB, NEo.shape))
