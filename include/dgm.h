@@ -77,7 +77,11 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
  * TC16: as TC32, but the tensor-core operands are fp16 (also 10-bit mantissa,
  * range 6e-8 .. 65504): fp16 copies of E and H written next to the float
  * state, fp16 tables and face-trace buffers, fp16 MMAs with K = 16 and FP32
- * accumulation; the update and the energy use the float state. */
+ * accumulation; the update and the energy use the float state.  The
+ * orthonormalised coefficients and face traces must stay inside the fp16 range
+ * (magnitudes well below 65504, and far above 6e-8 to keep their precision):
+ * the equations are linear, so scale the fields into that range.  An overflow
+ * shows as DGM_ERR_UNSTABLE from dgm_run when energies are requested. */
 enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2, DGM_PREC_TC16 = 3 };
 
 typedef struct dgm_options {
