@@ -12,6 +12,12 @@ Tolerances (relative to the max-abs of the reference):
         FP64 oracle's: the tensor cores multiply TF32 operands (10-bit mantissa:
         state truncated, tables rounded to nearest) and accumulate in FP32.
         First measurements: 4e-4..1.2e-3 per application, 1.3e-2 trajectory.
+  TC16: the same bounds as TC32 (fp16 operands also carry 10 mantissa bits; the
+        state, update and energy stay fp32).  Observed 3e-4..1.1e-3 per
+        application, 2.4e-2 on the cavity trajectory.
+  Resonances (FP64): every frequency with relative residual r < 1e-6 lies within
+        r of an oracle frequency; the three smallest distinct ones to 1e-8.
+  Order-4 composition: the trajectory bounds above, per precision.
 """
 
 import numpy as np
