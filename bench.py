@@ -70,6 +70,14 @@ def flops_per_elem_step(p):
     return 24 * n3(p - 1) * n3(p) + 32 * (n2(p) * n3(p) + n2(p - 1) * n3(p - 1))
 
 
+def phase_bytes(nt, p, b):
+    """Algorithmic bytes of one H-phase and one E-phase launch over nt elements with
+    b bytes per state value (g = 64 B geometry, c = 20 B topology per element): the
+    H-phase reads E and H and writes H, the E-phase reads H and E and writes E."""
+    NE, NH = n3(p), n3(p - 1)
+    return nt * (b * (3 * NE + 6 * NH) + 64 + 20), nt * (b * (6 * NE + 3 * NH) + 64 + 20)
+
+
 def alu_roofline(w, ms_per_step):
     achieved = w.nt * flops_per_elem_step(w.p) / (ms_per_step * 1e-3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -361,11 +369,7 @@ def run_gpu(args, rank, world, local):
 
     # roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
     b = 8 if args.precision == "fp64" else 4
-    NE, NH = n3(w.p), n3(w.p - 1)
-    # algorithmic bytes per element and phase (g = 64 B geometry, c = 20 B topology):
-    # H-phase reads E, H and writes H; E-phase reads H, E and writes E
-    bytes_H = w.nt * (b * (3 * NE + 6 * NH) + 64 + 20)
-    bytes_E = w.nt * (b * (6 * NE + 3 * NH) + 64 + 20)
+    bytes_H, bytes_E = phase_bytes(w.nt, w.p, b)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
     tcp = args.precision in ("tc32", "tc16")
