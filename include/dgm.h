@@ -341,6 +341,25 @@ int dgm_quad_points(dgm_problem* prob, int q1d, int64_t* count, double* xyz);
 int dgm_project(dgm_problem* prob, int q1d, const double* E_pts, const double* H_pts);
 int dgm_eval(dgm_problem* prob, int q1d, double* E_pts, double* H_pts);
 
+/* The d/dx recurrence of the 3D shape functions (Sec. 3.2.2, Sec. 4.2.2), host
+ * only, no GPU.  Sec. 4.2.2 prints the 16-monomial support of a relation
+ *   sum_{s in SD} c_s d/dx phi_{(i,j,k)+s} + sum_{s in S0} c_s phi_{(i,j,k)+s} = 0,
+ * SD = {(1,1,2),(1,0,3),(0,2,2),(0,1,3),(1,1,1),(1,0,2),(0,2,1),(0,1,2),(1,1,0),
+ *       (1,0,1),(0,2,0),(0,1,1)} (terms with d/dx), S0 = {(1,1,1),(1,0,2),(0,2,1),
+ * (0,1,2)} (terms without), but not its coefficients.
+ * dgm_dx_recurrence: the coefficients at every (i, j, k) with i + j + k <= p - 4
+ * where the support carries exactly one relation, found numerically (lead term
+ * (0,1,3) scaled to 1), in the printed (unnormalised) basis.  *count relations;
+ * ijk [*count][3] and coef [*count][16] (SD order, then S0) may be NULL for a
+ * size query.  p in [1, 8].
+ * dgm_dx_sweep: b [N3(p-1)] = coefficients of d/dx of u = sum a_ijk phi_ijk
+ * (a [N3(p)], both lexicographic in (i, j, k), unnormalised basis) by the
+ * backward sweep over those relations, visiting indices by descending (degree,
+ * k, j, i).  Indices that no relation leads with get the dense column (exact
+ * quadrature).  *swept (nullable) counts the coefficients a relation handled. */
+int dgm_dx_recurrence(int p, int* count, int32_t* ijk, double* coef);
+int dgm_dx_sweep(int p, const double* a, double* b, int* swept);
+
 /* Reference tables of the library (host, FP64, orthonormalised basis
  * phi_a / ||phi_a||), for inspection and tests:
  *   which = 0,1,2: D_x, D_y, D_z  [N3(p-1)][N3(p)], entry (b,a) = (d phi_a, phi_b)

@@ -74,6 +74,8 @@ _SIGS = {
     "dgm_energy": ([_vp, _pd], C.c_int),
     "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
     "dgm_resonances": ([_vp, C.c_int, C.c_int, C.c_double, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
+    "dgm_dx_recurrence": ([C.c_int, C.POINTER(C.c_int), _pi32, _pd], C.c_int),
+    "dgm_dx_sweep": ([C.c_int, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_tridiag_eig": ([C.c_int, _pd, _pd, C.c_int, C.c_int, _pd, _pd], C.c_int),
     "dgm_autotune": ([_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_set_materials": ([_vp, _pd, _pd], C.c_int),
@@ -369,3 +371,23 @@ def dgm_eval(prob, q1d, nt, want_E=True, want_H=False):
 
 def dgm_run_composed(prob, dt, nsteps, order=4, stream=None):
     _check(_lib.dgm_run_composed(prob, float(dt), int(nsteps), int(order), stream))
+
+
+def dgm_dx_recurrence(p):
+    """-> (ijk [n][3], coef [n][16]) of the d/dx relations at degree p (host only)."""
+    n = C.c_int()
+    _check(_lib.dgm_dx_recurrence(int(p), C.byref(n), None, None))
+    ijk = np.empty((n.value, 3), dtype=np.int32)
+    coef = np.empty((n.value, 16))
+    _check(_lib.dgm_dx_recurrence(int(p), C.byref(n), ijk.ctypes.data_as(_pi32), _dptr(coef)))
+    return ijk, coef
+
+
+def dgm_dx_sweep(p, a):
+    """-> (b, swept): d/dx of sum a_ijk phi_ijk by the recurrence sweep (host only)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    nh = p * (p + 1) * (p + 2) // 6
+    b = np.empty(nh)
+    sw = C.c_int()
+    _check(_lib.dgm_dx_sweep(int(p), _dptr(a), _dptr(b), C.byref(sw)))
+    return b, sw.value

@@ -360,4 +360,13 @@ int build_ref_tables(int p, RefTables& t) {
     return DGM_OK;
 }
 
+void phi3_values(int p, const std::vector<int>& idx, double xi, double eta, double zeta, double* val, double* dx) {
+    if (!dx) {
+        phi3_at(p, idx, xi, eta, zeta, val, nullptr, nullptr, nullptr);
+        return;
+    }
+    std::vector<double> dy(idx.size() / 3), dz(idx.size() / 3);
+    phi3_at(p, idx, xi, eta, zeta, val, dx, dy.data(), dz.data());
+}
+
 }  // namespace dgm

@@ -161,3 +161,74 @@ def test_tridiagonal_eigen_helper(capi):
     with pytest.raises(capi.DgmError) as ex:
         capi.dgm_tridiag_eig(np.ones(3), np.ones(2), 2, 2)
     assert ex.value.code == capi.DGM_ERR_INVALID_ARG
+
+
+def _n3(q):
+    return (q + 1) * (q + 2) * (q + 3) // 6
+
+
+def test_dx_recurrence_equals_exact_relation(capi):
+    """The library's numerically found d/dx relation at (i,j,k) = (1,1,1), p = 7,
+    against the exact rational nullspace of the printed support (sympy, direct
+    symbolic differentiation of the printed 3D shape functions)."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols("x y z")
+
+    def phi(i, j, k):
+        e = ((1 - X - Y) ** i * (1 - X) ** j * sp.legendre(i, 2 * Z / (1 - X - Y) - 1)
+             * sp.jacobi(j, 2 * i + 1, 0, 2 * Y / (1 - X) - 1) * sp.jacobi(k, 2 * i + 2 * j + 2, 0, 2 * X - 1))
+        return sp.Poly(sp.expand(sp.cancel(sp.together(e))), X, Y, Z)
+    SD = [(1, 1, 2), (1, 0, 3), (0, 2, 2), (0, 1, 3), (1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2),
+          (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1)]
+    S0 = [(1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2)]
+    cols = [phi(1 + a, 1 + b, 1 + c).diff(X) for a, b, c in SD] + [phi(1 + a, 1 + b, 1 + c) for a, b, c in S0]
+    monos = sorted({m for c in cols for m in c.as_dict()})
+    ns = sp.Matrix([[c.as_dict().get(m, 0) for c in cols] for m in monos]).nullspace()
+    assert len(ns) == 1
+    exact = np.array([float(v / ns[0][3]) for v in ns[0]])
+    ijk, coef = capi.dgm_dx_recurrence(7)
+    r = [n for n, t in enumerate(ijk) if tuple(t) == (1, 1, 1)]
+    assert len(r) == 1
+    assert np.abs(coef[r[0]] - exact).max() < 1e-9 * np.abs(exact).max()
+
+
+def test_dx_relations_hold_with_the_oracle_basis(capi):
+    """Every relation at p = 8 annihilates the oracle's phi and d/dx phi (textbook
+    Jacobi recurrence with forward-mode derivatives) at points the library never
+    sampled; and the relations exist exactly at the generic indices i >= 1."""
+    from oracle.basis import phi3, index3
+    p = 8
+    ijk, coef = capi.dgm_dx_recurrence(p)
+    assert sorted(map(tuple, ijk)) == sorted((i, j, k) for (i, j, k) in index3(p - 4) if i >= 1)
+    rng = np.random.default_rng(2)
+    b = rng.dirichlet([1, 1, 1, 1], 40)[:, :3]
+    val, grad = phi3(p, b)
+    pos = {t: r for r, t in enumerate(index3(p))}
+    SD = [(1, 1, 2), (1, 0, 3), (0, 2, 2), (0, 1, 3), (1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2),
+          (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1)]
+    S0 = [(1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2)]
+    for (i, j, k), c in zip(ijk, coef):
+        terms = [c[s] * grad[pos[(i + a, j + bb, k + cc)], :, 0] for s, (a, bb, cc) in enumerate(SD)]
+        terms += [c[12 + s] * val[pos[(i + a, j + bb, k + cc)]] for s, (a, bb, cc) in enumerate(S0)]
+        scale = max(np.abs(t).max() for t in terms)
+        assert np.abs(sum(terms)).max() < 1e-10 * scale, (i, j, k)
+
+
+@pytest.mark.parametrize("p", [1, 3, 5, 6, 8])
+def test_dx_sweep_equals_direct_differentiation(capi, p):
+    """The backward sweep (relations where they lead, dense columns elsewhere)
+    against d/dx of the series projected by exact quadrature with the oracle's
+    basis and the closed-form norms."""
+    from oracle.basis import phi3, index3
+    from oracle.quadrature import tet_rule
+    rng = np.random.default_rng(p)
+    a = rng.standard_normal(_n3(p))
+    b, swept = capi.dgm_dx_sweep(p, a)
+    xq, wq = tet_rule(p + 2)
+    _, grad = phi3(p, xq)
+    valH, _ = phi3(p - 1, xq)
+    du = a @ grad[:, :, 0]
+    norms = np.array([1.0 / (2 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3)) for (i, j, k) in index3(p - 1)])
+    ref = (valH * (wq * du)[None, :]).sum(1) / norms
+    assert np.abs(b - ref).max() < 1e-12 * np.abs(ref).max()
+    assert swept == len(capi.dgm_dx_recurrence(p)[0])
