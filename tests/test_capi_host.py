@@ -232,3 +232,32 @@ def test_dx_sweep_equals_direct_differentiation(capi, p):
     ref = (valH * (wq * du)[None, :]).sum(1) / norms
     assert np.abs(b - ref).max() < 1e-12 * np.abs(ref).max()
     assert swept == len(capi.dgm_dx_recurrence(p)[0])
+
+
+def test_header_is_plain_c_and_links(capi, tmp_path):
+    """The boundary is a C ABI: include/dgm.h compiles as pedantic C99, and a C
+    program links against the library and calls a host-only entry point."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text('#include "dgm.h"\n#include <stdio.h>\n'
+                   'int main(void) {\n'
+                   '    dgm_options o; double vals[2]; const double d[3] = {2.0, 2.0, 2.0}, e[2] = {1.0, 1.0};\n'
+                   '    dgm_default_options(&o);\n'
+                   '    if (dgm_tridiag_eig(3, d, e, 0, 2, vals, 0) != DGM_OK) return 1;\n'
+                   '    printf("%d %.12f %.12f\\n", o.precision, vals[0], vals[1]);\n'
+                   '    return 0;\n}\n')
+    lib = os.path.dirname(capi.LIB_PATH)
+    exe = tmp_path / "t.out"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", lib, "-ldgm", f"-Wl,-rpath,{lib}", "-o", str(exe)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    prec, l0, l1 = out.stdout.split()
+    # eigenvalues of tridiag(1, 2, 1) of size 3: 2 - sqrt 2, 2, 2 + sqrt 2
+    assert int(prec) == 0 and abs(float(l0) - (2 - 2 ** 0.5)) < 1e-12 and abs(float(l1) - 2.0) < 1e-12
