@@ -341,24 +341,30 @@ int dgm_quad_points(dgm_problem* prob, int q1d, int64_t* count, double* xyz);
 int dgm_project(dgm_problem* prob, int q1d, const double* E_pts, const double* H_pts);
 int dgm_eval(dgm_problem* prob, int q1d, double* E_pts, double* H_pts);
 
-/* The d/dx recurrence of the 3D shape functions (Sec. 3.2.2, Sec. 4.2.2), host
- * only, no GPU.  Sec. 4.2.2 prints the 16-monomial support of a relation
- *   sum_{s in SD} c_s d/dx phi_{(i,j,k)+s} + sum_{s in S0} c_s phi_{(i,j,k)+s} = 0,
- * SD = {(1,1,2),(1,0,3),(0,2,2),(0,1,3),(1,1,1),(1,0,2),(0,2,1),(0,1,2),(1,1,0),
- *       (1,0,1),(0,2,0),(0,1,1)} (terms with d/dx), S0 = {(1,1,1),(1,0,2),(0,2,1),
- * (0,1,2)} (terms without), but not its coefficients.
- * dgm_dx_recurrence: the coefficients at every (i, j, k) with i + j + k <= p - 4
- * where the support carries exactly one relation, found numerically (lead term
- * (0,1,3) scaled to 1), in the printed (unnormalised) basis.  *count relations;
- * ijk [*count][3] and coef [*count][16] (SD order, then S0) may be NULL for a
+/* Recurrences for the derivatives of the 3D shape functions (Sec. 3.2.2,
+ * Sec. 4.2.2), host only, no GPU.  A relation in direction dir (0 x, 1 y, 2 z)
+ *   sum_{s in SD} c_s d/d(dir) phi_{(i,j,k)+s} + sum_{s in S0} c_s phi_{(i,j,k)+s} = 0
+ * ties shifts of the derivative to shifts of the functions.  For x the support
+ * is the one printed in Sec. 4.2.2 (16 terms).  For y (20 terms) and z (19
+ * terms) the paper states that relations exist but prints no support: these
+ * were found by a numerical search.
+ * dgm_grad_support: *nterms, the shifts [nterms][4] = (di, dj, dk, 1 if the term
+ * carries the derivative else 0) (nullable), and *lead (nullable), the position
+ * of the term that is highest in the order (degree, k, j, i).
+ * dgm_grad_recurrence: the coefficients at every (i, j, k) where the support
+ * carries exactly one relation (all i >= 1 with the shifted indices <= p), found
+ * numerically with the lead coefficient 1, in the printed (unnormalised) basis;
+ * *count relations, ijk [*count][3] and coef [*count][nterms] nullable for a
  * size query.  p in [1, 8].
- * dgm_dx_sweep: b [N3(p-1)] = coefficients of d/dx of u = sum a_ijk phi_ijk
- * (a [N3(p)], both lexicographic in (i, j, k), unnormalised basis) by the
- * backward sweep over those relations, visiting indices by descending (degree,
- * k, j, i).  Indices that no relation leads with get the dense column (exact
- * quadrature).  *swept (nullable) counts the coefficients a relation handled. */
-int dgm_dx_recurrence(int p, int* count, int32_t* ijk, double* coef);
-int dgm_dx_sweep(int p, const double* a, double* b, int* swept);
+ * dgm_grad_sweep: b [N3(p-1)] = coefficients of the derivative of
+ * u = sum a_ijk phi_ijk (a [N3(p)], both lexicographic in (i, j, k),
+ * unnormalised basis) by the backward sweep over those relations, visiting
+ * indices by descending (degree, k, j, i).  Indices that lead no relation get
+ * the dense column (exact quadrature).  *swept (nullable) counts the
+ * coefficients a relation handled. */
+int dgm_grad_support(int dir, int* nterms, int32_t* shifts, int* lead);
+int dgm_grad_recurrence(int p, int dir, int* count, int32_t* ijk, double* coef);
+int dgm_grad_sweep(int p, int dir, const double* a, double* b, int* swept);
 
 /* Reference tables of the library (host, FP64, orthonormalised basis
  * phi_a / ||phi_a||), for inspection and tests:

@@ -74,8 +74,9 @@ _SIGS = {
     "dgm_energy": ([_vp, _pd], C.c_int),
     "dgm_estimate_dt": ([_vp, C.c_int, _pd, _pd], C.c_int),
     "dgm_resonances": ([_vp, C.c_int, C.c_int, C.c_double, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
-    "dgm_dx_recurrence": ([C.c_int, C.POINTER(C.c_int), _pi32, _pd], C.c_int),
-    "dgm_dx_sweep": ([C.c_int, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
+    "dgm_grad_support": ([C.c_int, C.POINTER(C.c_int), _pi32, C.POINTER(C.c_int)], C.c_int),
+    "dgm_grad_recurrence": ([C.c_int, C.c_int, C.POINTER(C.c_int), _pi32, _pd], C.c_int),
+    "dgm_grad_sweep": ([C.c_int, C.c_int, _pd, _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_tridiag_eig": ([C.c_int, _pd, _pd, C.c_int, C.c_int, _pd, _pd], C.c_int),
     "dgm_autotune": ([_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _pd, C.POINTER(C.c_int)], C.c_int),
     "dgm_set_materials": ([_vp, _pd, _pd], C.c_int),
@@ -373,21 +374,30 @@ def dgm_run_composed(prob, dt, nsteps, order=4, stream=None):
     _check(_lib.dgm_run_composed(prob, float(dt), int(nsteps), int(order), stream))
 
 
-def dgm_dx_recurrence(p):
-    """-> (ijk [n][3], coef [n][16]) of the d/dx relations at degree p (host only)."""
+def dgm_grad_support(direction):
+    """-> (shifts [n][4] = (di, dj, dk, carries derivative), lead position) (host only)."""
+    n, lead = C.c_int(), C.c_int()
+    sh = np.empty((20, 4), dtype=np.int32)
+    _check(_lib.dgm_grad_support(int(direction), C.byref(n), sh.ctypes.data_as(_pi32), C.byref(lead)))
+    return sh[:n.value].copy(), lead.value
+
+
+def dgm_grad_recurrence(p, direction):
+    """-> (ijk [n][3], coef [n][nterms]) of the derivative relations at degree p (host only)."""
     n = C.c_int()
-    _check(_lib.dgm_dx_recurrence(int(p), C.byref(n), None, None))
+    _check(_lib.dgm_grad_recurrence(int(p), int(direction), C.byref(n), None, None))
+    nterms = len(dgm_grad_support(direction)[0])
     ijk = np.empty((n.value, 3), dtype=np.int32)
-    coef = np.empty((n.value, 16))
-    _check(_lib.dgm_dx_recurrence(int(p), C.byref(n), ijk.ctypes.data_as(_pi32), _dptr(coef)))
+    coef = np.empty((n.value, nterms))
+    _check(_lib.dgm_grad_recurrence(int(p), int(direction), C.byref(n), ijk.ctypes.data_as(_pi32), _dptr(coef)))
     return ijk, coef
 
 
-def dgm_dx_sweep(p, a):
-    """-> (b, swept): d/dx of sum a_ijk phi_ijk by the recurrence sweep (host only)."""
+def dgm_grad_sweep(p, direction, a):
+    """-> (b, swept): derivative of sum a_ijk phi_ijk by the recurrence sweep (host only)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     nh = p * (p + 1) * (p + 2) // 6
     b = np.empty(nh)
     sw = C.c_int()
-    _check(_lib.dgm_dx_sweep(int(p), _dptr(a), _dptr(b), C.byref(sw)))
+    _check(_lib.dgm_grad_sweep(int(p), int(direction), _dptr(a), _dptr(b), C.byref(sw)))
     return b, sw.value

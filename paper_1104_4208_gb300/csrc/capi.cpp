@@ -1884,25 +1884,36 @@ int dgm_eval(dgm_problem* P, int q1d, double* E_pts, double* H_pts) {
     return DGM_OK;
 }
 
-int dgm_dx_recurrence(int p, int* count, int32_t* ijk, double* coef) {
-    if (p < 1 || p > DGM_PMAX || !count) {
-        set_error("dgm_dx_recurrence: bad argument");
+int dgm_grad_support(int dir, int* nterms, int32_t* shifts, int* lead) {
+    if (dir < 0 || dir > 2 || !nterms) {
+        set_error("dgm_grad_support: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    int sh[80];
+    dgm::grad_support(dir, nterms, sh, lead);
+    if (shifts) std::copy(sh, sh + 4 * (*nterms), shifts);
+    return DGM_OK;
+}
+
+int dgm_grad_recurrence(int p, int dir, int* count, int32_t* ijk, double* coef) {
+    if (p < 1 || p > DGM_PMAX || dir < 0 || dir > 2 || !count) {
+        set_error("dgm_grad_recurrence: bad argument");
         return DGM_ERR_INVALID_ARG;
     }
     std::vector<int> r_ijk;
     std::vector<double> r_c;
-    *count = dgm::dx_relations(p, r_ijk, r_c);
+    *count = dgm::grad_relations(p, dir, r_ijk, r_c);
     if (ijk) std::copy(r_ijk.begin(), r_ijk.end(), ijk);
     if (coef) std::copy(r_c.begin(), r_c.end(), coef);
     return DGM_OK;
 }
 
-int dgm_dx_sweep(int p, const double* a, double* b, int* swept) {
-    if (p < 1 || p > DGM_PMAX || !a || !b) {
-        set_error("dgm_dx_sweep: bad argument");
+int dgm_grad_sweep(int p, int dir, const double* a, double* b, int* swept) {
+    if (p < 1 || p > DGM_PMAX || dir < 0 || dir > 2 || !a || !b) {
+        set_error("dgm_grad_sweep: bad argument");
         return DGM_ERR_INVALID_ARG;
     }
-    const int n = dgm::dx_sweep(p, a, b);
+    const int n = dgm::grad_sweep(p, dir, a, b);
     if (swept) *swept = n;
     return DGM_OK;
 }

@@ -43,16 +43,18 @@ void collapsed_rule(int q1d, std::vector<double>& xh, std::vector<double>& w, st
 // Orthonormalised phi'_a at the collapsed rule's points, [nq][N3(p)].
 void phi_table(int p, int q1d, std::vector<double>& phi);
 // Unnormalised phi_ijk (Sec. 4.2.2) of the index list idx (lexicographic, |ijk| <= p)
-// and, with dx non-NULL, their x-derivatives at the collapsed point (xi, eta, zeta).
-void phi3_values(int p, const std::vector<int>& idx, double xi, double eta, double zeta, double* val, double* dx);
-// d/dx relations on the printed 3D support at every generic (i, j, k) with
-// i + j + k <= p - 4 (3 ints and 16 coefficients each, lead S_j S_k^3 D_x = 1,
-// unnormalised basis); returns their number.
-int dx_relations(int p, std::vector<int>& ijk_out, std::vector<double>& coef_out);
-// b [N3(p-1)] = modal d/dx of u = sum a_ijk phi_ijk (unnormalised basis, lexicographic
-// order) by the backward sweep over those relations, dense columns elsewhere;
-// returns how many nonzero coefficients a relation handled.
-int dx_sweep(int p, const double* a, double* b);
+// and their Cartesian gradients grad [n][3] at the collapsed point (xi, eta, zeta).
+void phi3_grad(int p, const std::vector<int>& idx, double xi, double eta, double zeta, double* val, double* grad);
+// Support of the derivative relation in direction dir (0 x, 1 y, 2 z): shifts
+// [n][4] = (di, dj, dk, carries the derivative), the lead term's position; returns n.
+int grad_support(int dir, int* nterms, int* shifts, int* lead);
+// The relations at every (i, j, k) where the support carries exactly one
+// (3 ints and n coefficients each, lead coefficient 1, unnormalised basis).
+int grad_relations(int p, int dir, std::vector<int>& ijk_out, std::vector<double>& coef_out);
+// b [N3(p-1)] = modal derivative in direction dir of u = sum a_ijk phi_ijk
+// (unnormalised basis, lexicographic order) by the backward sweep over those
+// relations, dense columns elsewhere; returns how many coefficients a relation handled.
+int grad_sweep(int p, int dir, const double* a, double* b);
 // Orthonormalised phi'_a at n Cartesian reference points xh [n][3], [n][N3(p)].
 void phi_at_points(int p, const double* xh, int n, std::vector<double>& out);
 void index2(int p, std::vector<int>& ij);

@@ -1,24 +1,34 @@
-// The d/dx relation of the 3D shape functions (Sec. 3.2.2, Sec. 4.2.2) and the
-// backward sweep it gives (host side).
+// Recurrences for the derivatives of the 3D shape functions (Sec. 3.2.2,
+// Sec. 4.2.2) and the backward sweep they give (host side).
 //
-// Sec. 4.2.2 prints the support of a relation between shifts of d/dx phi_ijk
-// and of phi_ijk: 16 monomials, with coefficients rational in (i, j, k) that the
-// paper does not print.
-//   sum_{s in SD} c_s d/dx phi_{(i,j,k)+s} + sum_{s in S0} c_s phi_{(i,j,k)+s} = 0
-// At a concrete (i, j, k) the coefficients span the nullspace of this ansatz,
-// read as an identity in x, y, z.  They are found here numerically:
-// - the 16 functions are sampled at fixed interior points;
-// - the lead coefficient (term S_j S_k^3 D_x) is set to 1;
-// - the other 15 follow by least squares (Householder QR on scaled columns).
-// Where those 15 columns are rank deficient, the index carries more than one
-// relation (low indices); it is left to the dense operator.
+// A relation in direction d (x, y or z) ties shifts of d/dd phi_ijk to shifts
+// of phi_ijk:
+//   sum_{s in SD} c_s d/dd phi_{(i,j,k)+s} + sum_{s in S0} c_s phi_{(i,j,k)+s} = 0
+// with coefficients rational in (i, j, k).
+// - For d/dx, Sec. 4.2.2 prints the support: 12 derivative terms and 4 value
+//   terms.  It prints no coefficients.
+// - For d/dy and d/dz the paper states that such relations exist but prints
+//   neither supports nor coefficients.  The supports below were found by a
+//   numerical search: greedy elimination of monomials from a window of shifts,
+//   keeping a one-dimensional nullspace, at a generic index.  The same search
+//   gives back the printed d/dx support exactly.
+//   - d/dy: 18 derivative terms and 2 value terms, shifts up to (1, 3, 4);
+//   - d/dz: 18 derivative terms and 1 value term, shifts up to (2, 4, 4).
+//
+// At a concrete (i, j, k) the coefficients span the nullspace of the ansatz,
+// read as an identity in x, y, z.  They are found numerically:
+// - the functions are sampled at fixed interior points;
+// - the lead coefficient is set to 1, the lead being the derivative term that is
+//   highest in the order (degree, k, j, i);
+// - the rest follow by least squares (Householder QR on scaled columns).
+// Where the other columns are rank deficient, the index carries more than one
+// relation (it happens exactly at i = 0); it is left to the dense operator.
 //
 // Sweep, the 3D analogue of the Legendre example of Sec. 3.2.2.  For
-// u = sum a_ijk phi_ijk the indices are visited from the highest down, in the
-// order (degree, k, j, i).  Where an index is the lead of a relation, its
-// derivative is replaced by the relation's other terms: derivatives of
-// indices lower in that order, and values of degree one less.  Everywhere
-// else its dense column is added.
+// u = sum a_ijk phi_ijk the indices are visited from the highest down, in that
+// order.  Where an index is the lead of a relation, its derivative is replaced
+// by the relation's other terms: derivatives of indices lower in the order, and
+// values of degree one less.  Everywhere else its dense column is added.
 
 #include <algorithm>
 #include <cmath>
@@ -31,11 +41,31 @@ namespace dgm {
 
 namespace {
 
-// printed support of the d/dx relation: shifts of the terms with D_x, then of those without
-constexpr int kSD[12][3] = {{1, 1, 2}, {1, 0, 3}, {0, 2, 2}, {0, 1, 3}, {1, 1, 1}, {1, 0, 2},
-                            {0, 2, 1}, {0, 1, 2}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}};
-constexpr int kS0[4][3] = {{1, 1, 1}, {1, 0, 2}, {0, 2, 1}, {0, 1, 2}};
-constexpr int kLead = 3;   // S_j S_k^3 D_x
+// supports: shift (di, dj, dk) and whether the term carries the derivative
+struct Support {
+    int n;
+    int lead;
+    int sh[20][4];
+};
+// d/dx: printed in Sec. 4.2.2 (derivative terms, then value terms)
+constexpr Support kSupX = {16, 3, {{1, 1, 2, 1}, {1, 0, 3, 1}, {0, 2, 2, 1}, {0, 1, 3, 1}, {1, 1, 1, 1}, {1, 0, 2, 1},
+                                   {0, 2, 1, 1}, {0, 1, 2, 1}, {1, 1, 0, 1}, {1, 0, 1, 1}, {0, 2, 0, 1}, {0, 1, 1, 1},
+                                   {1, 1, 1, 0}, {1, 0, 2, 0}, {0, 2, 1, 0}, {0, 1, 2, 0}}};
+// d/dy and d/dz: found by the search described above (derivative terms by
+// descending (degree, k, j, i), then value terms)
+constexpr Support kSupY = {20, 0, {{0, 1, 4, 1}, {1, 0, 4, 1}, {0, 2, 3, 1}, {1, 1, 3, 1}, {0, 3, 2, 1}, {1, 2, 2, 1},
+                                   {0, 1, 3, 1}, {1, 0, 3, 1}, {0, 2, 2, 1}, {1, 1, 2, 1}, {0, 3, 1, 1}, {1, 2, 1, 1},
+                                   {0, 1, 2, 1}, {1, 0, 2, 1}, {0, 2, 1, 1}, {1, 1, 1, 1}, {0, 3, 0, 1}, {1, 2, 0, 1},
+                                   {0, 2, 2, 0}, {1, 1, 2, 0}}};
+constexpr Support kSupZ = {19, 0, {{0, 2, 4, 1}, {2, 0, 4, 1}, {0, 3, 3, 1}, {2, 1, 3, 1}, {0, 4, 2, 1}, {2, 2, 2, 1},
+                                   {0, 2, 3, 1}, {2, 0, 3, 1}, {0, 3, 2, 1}, {2, 1, 2, 1}, {0, 4, 1, 1}, {2, 2, 1, 1},
+                                   {0, 2, 2, 1}, {2, 0, 2, 1}, {0, 3, 1, 1}, {2, 1, 1, 1}, {0, 4, 0, 1}, {2, 2, 0, 1},
+                                   {1, 2, 2, 0}}};
+const Support& support(int dir) { return dir == 0 ? kSupX : (dir == 1 ? kSupY : kSupZ); }
+int support_degree(const Support& S) {
+    const int* l = S.sh[S.lead];
+    return l[0] + l[1] + l[2];
+}
 constexpr int kPoints = 64;
 
 struct Index3 {
@@ -98,58 +128,70 @@ bool least_squares(int m, int n, std::vector<double> A, std::vector<double> y, s
 
 }  // namespace
 
-int dx_relations(int p, std::vector<int>& ijk_out, std::vector<double>& coef_out) {
+int grad_support(int dir, int* nterms, int* shifts, int* lead) {
+    const Support& S = support(dir);
+    if (nterms) *nterms = S.n;
+    if (lead) *lead = S.lead;
+    if (shifts)
+        for (int t = 0; t < S.n; ++t)
+            for (int c = 0; c < 4; ++c) shifts[4 * t + c] = S.sh[t][c];
+    return S.n;
+}
+
+int grad_relations(int p, int dir, std::vector<int>& ijk_out, std::vector<double>& coef_out) {
     ijk_out.clear();
     coef_out.clear();
-    if (p < 4) return 0;
+    const Support& S = support(dir);
+    const int top = support_degree(S);
+    if (p < top) return 0;
     const Index3 I(p);
     const int N = I.size();
-    // samples of every phi and d/dx phi up to degree p at fixed interior collapsed points
-    std::vector<double> val((size_t)kPoints * N), dx((size_t)kPoints * N);
+    // samples of every phi and its derivative in direction dir at fixed interior collapsed points
+    std::vector<double> val((size_t)kPoints * N), der((size_t)kPoints * N), g3(3 * (size_t)N);
     for (int q = 0; q < kPoints; ++q) {
         const double xi = 0.05 + 0.9 * std::fmod(0.6180339887498949 * (q + 1), 1.0);
         const double eta = 0.05 + 0.9 * std::fmod(0.7548776662466927 * (q + 1), 1.0);
         const double zeta = 0.05 + 0.9 * std::fmod(0.5698402909980532 * (q + 1), 1.0);
-        phi3_values(p, I.ijk, xi, eta, zeta, &val[(size_t)q * N], &dx[(size_t)q * N]);
+        phi3_grad(p, I.ijk, xi, eta, zeta, &val[(size_t)q * N], g3.data());
+        for (int r = 0; r < N; ++r) der[(size_t)q * N + r] = g3[3 * (size_t)r + dir];
     }
+    const int m = S.n - 1;   // unknowns besides the lead
     for (int r = 0; r < N; ++r) {
         const int i = I.ijk[3 * r], j = I.ijk[3 * r + 1], k = I.ijk[3 * r + 2];
-        if (i + j + k + 4 > p) continue;
-        // the 16 columns; column c of the lead is the right-hand side
-        int cols[16];
-        for (int s = 0; s < 12; ++s) cols[s] = I.find(i + kSD[s][0], j + kSD[s][1], k + kSD[s][2]);
-        for (int s = 0; s < 4; ++s) cols[12 + s] = I.find(i + kS0[s][0], j + kS0[s][1], k + kS0[s][2]);
-        std::vector<double> A((size_t)kPoints * 15), y(kPoints), scale(15);
+        if (i + j + k + top > p) continue;
+        int cols[20];
+        for (int t = 0; t < S.n; ++t) cols[t] = I.find(i + S.sh[t][0], j + S.sh[t][1], k + S.sh[t][2]);
+        std::vector<double> A((size_t)kPoints * m), y(kPoints), scale(m);
         int c = 0;
-        for (int s = 0; s < 16; ++s) {
-            if (s == kLead) continue;
-            const std::vector<double>& src = s < 12 ? dx : val;
+        for (int t = 0; t < S.n; ++t) {
+            if (t == S.lead) continue;
+            const std::vector<double>& src = S.sh[t][3] ? der : val;
             double nrm = 0.0;
-            for (int q = 0; q < kPoints; ++q) nrm += src[(size_t)q * N + cols[s]] * src[(size_t)q * N + cols[s]];
+            for (int q = 0; q < kPoints; ++q) nrm += src[(size_t)q * N + cols[t]] * src[(size_t)q * N + cols[t]];
             nrm = std::sqrt(nrm);
             scale[c] = nrm > 0.0 ? 1.0 / nrm : 1.0;
-            for (int q = 0; q < kPoints; ++q) A[(size_t)c * kPoints + q] = src[(size_t)q * N + cols[s]] * scale[c];
+            for (int q = 0; q < kPoints; ++q) A[(size_t)c * kPoints + q] = src[(size_t)q * N + cols[t]] * scale[c];
             ++c;
         }
         double ynrm = 0.0;
         for (int q = 0; q < kPoints; ++q) {
-            y[q] = -dx[(size_t)q * N + cols[kLead]];
+            y[q] = -der[(size_t)q * N + cols[S.lead]];
             ynrm += y[q] * y[q];
         }
         std::vector<double> sol;
-        if (!least_squares(kPoints, 15, A, y, sol)) continue;
+        if (!least_squares(kPoints, m, A, y, sol)) continue;
         // the relation must hold at every sample, not only in the least-squares sense
         double res = 0.0;
         for (int q = 0; q < kPoints; ++q) {
-            double s = -y[q];
-            for (int t = 0; t < 15; ++t) s += A[(size_t)t * kPoints + q] * sol[t];
-            res += s * s;
+            double v = -y[q];
+            for (int t = 0; t < m; ++t) v += A[(size_t)t * kPoints + q] * sol[t];
+            res += v * v;
         }
         if (!(res <= 1e-18 * ynrm)) continue;
         ijk_out.insert(ijk_out.end(), {i, j, k});
         c = 0;
-        for (int s = 0; s < 16; ++s) {
-            if (s == kLead) {
+        for (int t = 0; t < S.n; ++t) {
+            if (t == S.lead) {
                 coef_out.push_back(1.0);
             } else {
                 coef_out.push_back(sol[c] * scale[c]);
@@ -160,38 +202,40 @@ int dx_relations(int p, std::vector<int>& ijk_out, std::vector<double>& coef_out
     return (int)ijk_out.size() / 3;
 }
 
-int dx_sweep(int p, const double* a, double* b) {
+int grad_sweep(int p, int dir, const double* a, double* b) {
+    const Support& S = support(dir);
     const Index3 IE(p);
     const Index3 IH(std::max(p - 1, 0));
     const int NE = IE.size(), NH = p >= 1 ? IH.size() : 0;
     for (int r = 0; r < NH; ++r) b[r] = 0.0;
     if (p < 1) return 0;
-    // dense d/dx in the unnormalised basis by exact quadrature:
-    // Dx[beta][alpha] = (d/dx phi_alpha, phi_beta) / ||phi_beta||^2
+    // dense derivative in the unnormalised basis by exact quadrature:
+    // D[beta][alpha] = (d/dd phi_alpha, phi_beta) / ||phi_beta||^2
     std::vector<double> xh, w, col;
     collapsed_rule(p + 2, xh, w, col);
     const int nq = (int)w.size();
-    std::vector<double> Dx((size_t)NH * NE, 0.0), v(NE), d(NE);
+    std::vector<double> D((size_t)NH * NE, 0.0), v(NE), g3(3 * (size_t)NE);
     for (int q = 0; q < nq; ++q) {
-        phi3_values(p, IE.ijk, col[3 * q], col[3 * q + 1], col[3 * q + 2], v.data(), d.data());
+        phi3_grad(p, IE.ijk, col[3 * q], col[3 * q + 1], col[3 * q + 2], v.data(), g3.data());
         for (int bh = 0; bh < NH; ++bh) {
             const int be = IE.find(IH.ijk[3 * bh], IH.ijk[3 * bh + 1], IH.ijk[3 * bh + 2]);
             const double wb = w[q] * v[be];
-            for (int al = 0; al < NE; ++al) Dx[(size_t)bh * NE + al] += wb * d[al];
+            for (int al = 0; al < NE; ++al) D[(size_t)bh * NE + al] += wb * g3[3 * (size_t)al + dir];
         }
     }
     for (int bh = 0; bh < NH; ++bh) {
         const double n2 = dubiner3_norm2(IH.ijk[3 * bh], IH.ijk[3 * bh + 1], IH.ijk[3 * bh + 2]);
-        for (int al = 0; al < NE; ++al) Dx[(size_t)bh * NE + al] /= n2;
+        for (int al = 0; al < NE; ++al) D[(size_t)bh * NE + al] /= n2;
     }
     // relations, indexed by their lead
     std::vector<int> rel_ijk;
     std::vector<double> rel_c;
-    const int nrel = dx_relations(p, rel_ijk, rel_c);
+    const int nrel = grad_relations(p, dir, rel_ijk, rel_c);
     std::vector<int> lead_of(NE, -1);
     for (int r = 0; r < nrel; ++r) {
         const int i = rel_ijk[3 * r], j = rel_ijk[3 * r + 1], k = rel_ijk[3 * r + 2];
-        lead_of[IE.find(i + kSD[kLead][0], j + kSD[kLead][1], k + kSD[kLead][2])] = r;
+        const int* l = S.sh[S.lead];
+        lead_of[IE.find(i + l[0], j + l[1], k + l[2])] = r;
     }
     // visiting order: degree, then k, then j, then i, all descending
     std::vector<int> order(NE);
@@ -210,12 +254,17 @@ int dx_sweep(int p, const double* a, double* b) {
         if (rel >= 0) {
             ++swept;
             const int i = rel_ijk[3 * rel], j = rel_ijk[3 * rel + 1], k = rel_ijk[3 * rel + 2];
-            const double* c = &rel_c[(size_t)16 * rel];
-            for (int s = 0; s < 12; ++s)
-                if (s != kLead) at[IE.find(i + kSD[s][0], j + kSD[s][1], k + kSD[s][2])] -= coef * c[s];
-            for (int s = 0; s < 4; ++s) b[IH.find(i + kS0[s][0], j + kS0[s][1], k + kS0[s][2])] -= coef * c[12 + s];
+            const double* c = &rel_c[(size_t)S.n * rel];
+            for (int t = 0; t < S.n; ++t) {
+                if (t == S.lead) continue;
+                const int si = i + S.sh[t][0], sj = j + S.sh[t][1], sk = k + S.sh[t][2];
+                if (S.sh[t][3])
+                    at[IE.find(si, sj, sk)] -= coef * c[t];
+                else
+                    b[IH.find(si, sj, sk)] -= coef * c[t];
+            }
         } else {
-            for (int bh = 0; bh < NH; ++bh) b[bh] += coef * Dx[(size_t)bh * NE + r];
+            for (int bh = 0; bh < NH; ++bh) b[bh] += coef * D[(size_t)bh * NE + r];
         }
     }
     return swept;

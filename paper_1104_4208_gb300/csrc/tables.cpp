@@ -360,13 +360,15 @@ int build_ref_tables(int p, RefTables& t) {
     return DGM_OK;
 }
 
-void phi3_values(int p, const std::vector<int>& idx, double xi, double eta, double zeta, double* val, double* dx) {
-    if (!dx) {
-        phi3_at(p, idx, xi, eta, zeta, val, nullptr, nullptr, nullptr);
-        return;
+void phi3_grad(int p, const std::vector<int>& idx, double xi, double eta, double zeta, double* val, double* grad) {
+    const size_t n = idx.size() / 3;
+    std::vector<double> dx(n), dy(n), dz(n);
+    phi3_at(p, idx, xi, eta, zeta, val, dx.data(), dy.data(), dz.data());
+    for (size_t r = 0; r < n; ++r) {
+        grad[3 * r] = dx[r];
+        grad[3 * r + 1] = dy[r];
+        grad[3 * r + 2] = dz[r];
     }
-    std::vector<double> dy(idx.size() / 3), dz(idx.size() / 3);
-    phi3_at(p, idx, xi, eta, zeta, val, dx, dy.data(), dz.data());
 }
 
 }  // namespace dgm

@@ -167,71 +167,93 @@ def _n3(q):
     return (q + 1) * (q + 2) * (q + 3) // 6
 
 
-def test_dx_recurrence_equals_exact_relation(capi):
-    """The library's numerically found d/dx relation at (i,j,k) = (1,1,1), p = 7,
-    against the exact rational nullspace of the printed support (sympy, direct
-    symbolic differentiation of the printed 3D shape functions)."""
+_PRINTED_DX = {(1, 1, 2, 1), (1, 0, 3, 1), (0, 2, 2, 1), (0, 1, 3, 1), (1, 1, 1, 1), (1, 0, 2, 1), (0, 2, 1, 1),
+               (0, 1, 2, 1), (1, 1, 0, 1), (1, 0, 1, 1), (0, 2, 0, 1), (0, 1, 1, 1),
+               (1, 1, 1, 0), (1, 0, 2, 0), (0, 2, 1, 0), (0, 1, 2, 0)}
+
+
+def test_grad_supports(capi):
+    """The d/dx support is the one printed in Sec. 4.2.2; each support's lead is
+    its unique highest derivative term in the order (degree, k, j, i)."""
+    sh, lead = capi.dgm_grad_support(0)
+    assert set(map(tuple, sh)) == _PRINTED_DX and tuple(sh[lead]) == (0, 1, 3, 1)
+    for d in (0, 1, 2):
+        sh, lead = capi.dgm_grad_support(d)
+        key = lambda s: (s[0] + s[1] + s[2], s[2], s[1], s[0])
+        ders = [tuple(s) for s in sh if s[3] == 1]
+        assert max(ders, key=key) == tuple(sh[lead])
+        assert sum(1 for t in ders if key(t) == key(tuple(sh[lead]))) == 1
+        # value terms are of degree one less than the lead
+        assert all(s[0] + s[1] + s[2] == key(tuple(sh[lead]))[0] - 1 for s in sh if s[3] == 0)
+
+
+@pytest.mark.parametrize("direction,ijk,p", [(0, (1, 1, 1), 7), (1, (1, 1, 1), 8), (2, (1, 0, 0), 8)])
+def test_grad_recurrence_equals_exact_relation(capi, direction, ijk, p):
+    """The library's numerically found relation against the exact rational
+    nullspace of its support (sympy, direct symbolic differentiation of the
+    printed 3D shape functions): one relation, equal coefficients."""
     sp = pytest.importorskip("sympy")
     X, Y, Z = sp.symbols("x y z")
+    V = (X, Y, Z)[direction]
 
     def phi(i, j, k):
         e = ((1 - X - Y) ** i * (1 - X) ** j * sp.legendre(i, 2 * Z / (1 - X - Y) - 1)
              * sp.jacobi(j, 2 * i + 1, 0, 2 * Y / (1 - X) - 1) * sp.jacobi(k, 2 * i + 2 * j + 2, 0, 2 * X - 1))
         return sp.Poly(sp.expand(sp.cancel(sp.together(e))), X, Y, Z)
-    SD = [(1, 1, 2), (1, 0, 3), (0, 2, 2), (0, 1, 3), (1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2),
-          (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1)]
-    S0 = [(1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2)]
-    cols = [phi(1 + a, 1 + b, 1 + c).diff(X) for a, b, c in SD] + [phi(1 + a, 1 + b, 1 + c) for a, b, c in S0]
+    sh, lead = capi.dgm_grad_support(direction)
+    i, j, k = ijk
+    cols = [phi(i + a, j + b, k + c).diff(V) if der else phi(i + a, j + b, k + c) for a, b, c, der in sh]
     monos = sorted({m for c in cols for m in c.as_dict()})
     ns = sp.Matrix([[c.as_dict().get(m, 0) for c in cols] for m in monos]).nullspace()
     assert len(ns) == 1
-    exact = np.array([float(v / ns[0][3]) for v in ns[0]])
-    ijk, coef = capi.dgm_dx_recurrence(7)
-    r = [n for n, t in enumerate(ijk) if tuple(t) == (1, 1, 1)]
+    exact = np.array([float(v / ns[0][lead]) for v in ns[0]])
+    got_ijk, coef = capi.dgm_grad_recurrence(p, direction)
+    r = [n for n, t in enumerate(got_ijk) if tuple(t) == ijk]
     assert len(r) == 1
     assert np.abs(coef[r[0]] - exact).max() < 1e-9 * np.abs(exact).max()
 
 
-def test_dx_relations_hold_with_the_oracle_basis(capi):
-    """Every relation at p = 8 annihilates the oracle's phi and d/dx phi (textbook
-    Jacobi recurrence with forward-mode derivatives) at points the library never
-    sampled; and the relations exist exactly at the generic indices i >= 1."""
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_grad_relations_hold_with_the_oracle_basis(capi, direction):
+    """Every relation at p = 8 annihilates the oracle's phi and its derivative
+    (textbook Jacobi recurrence, forward-mode derivatives) at points the library
+    never sampled; relations exist exactly at the indices with i >= 1."""
     from oracle.basis import phi3, index3
     p = 8
-    ijk, coef = capi.dgm_dx_recurrence(p)
-    assert sorted(map(tuple, ijk)) == sorted((i, j, k) for (i, j, k) in index3(p - 4) if i >= 1)
+    sh, lead = capi.dgm_grad_support(direction)
+    top = int(sh[lead][0] + sh[lead][1] + sh[lead][2])
+    ijk, coef = capi.dgm_grad_recurrence(p, direction)
+    assert sorted(map(tuple, ijk)) == sorted(t for t in index3(p - top) if t[0] >= 1)
     rng = np.random.default_rng(2)
-    b = rng.dirichlet([1, 1, 1, 1], 40)[:, :3]
-    val, grad = phi3(p, b)
+    pts = rng.dirichlet([1, 1, 1, 1], 40)[:, :3]
+    val, grad = phi3(p, pts)
     pos = {t: r for r, t in enumerate(index3(p))}
-    SD = [(1, 1, 2), (1, 0, 3), (0, 2, 2), (0, 1, 3), (1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2),
-          (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1)]
-    S0 = [(1, 1, 1), (1, 0, 2), (0, 2, 1), (0, 1, 2)]
     for (i, j, k), c in zip(ijk, coef):
-        terms = [c[s] * grad[pos[(i + a, j + bb, k + cc)], :, 0] for s, (a, bb, cc) in enumerate(SD)]
-        terms += [c[12 + s] * val[pos[(i + a, j + bb, k + cc)]] for s, (a, bb, cc) in enumerate(S0)]
+        terms = [c[n] * (grad[pos[(i + a, j + b, k + cc)], :, direction] if der else val[pos[(i + a, j + b, k + cc)]])
+                 for n, (a, b, cc, der) in enumerate(sh)]
         scale = max(np.abs(t).max() for t in terms)
         assert np.abs(sum(terms)).max() < 1e-10 * scale, (i, j, k)
 
 
-@pytest.mark.parametrize("p", [1, 3, 5, 6, 8])
-def test_dx_sweep_equals_direct_differentiation(capi, p):
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("p", [1, 3, 6, 8])
+def test_grad_sweep_equals_direct_differentiation(capi, direction, p):
     """The backward sweep (relations where they lead, dense columns elsewhere)
-    against d/dx of the series projected by exact quadrature with the oracle's
-    basis and the closed-form norms."""
+    against the derivative of the series projected by exact quadrature with the
+    oracle's basis and the closed-form norms."""
     from oracle.basis import phi3, index3
     from oracle.quadrature import tet_rule
-    rng = np.random.default_rng(p)
+    rng = np.random.default_rng(10 * p + direction)
     a = rng.standard_normal(_n3(p))
-    b, swept = capi.dgm_dx_sweep(p, a)
+    b, swept = capi.dgm_grad_sweep(p, direction, a)
     xq, wq = tet_rule(p + 2)
     _, grad = phi3(p, xq)
     valH, _ = phi3(p - 1, xq)
-    du = a @ grad[:, :, 0]
+    du = a @ grad[:, :, direction]
     norms = np.array([1.0 / (2 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3)) for (i, j, k) in index3(p - 1)])
     ref = (valH * (wq * du)[None, :]).sum(1) / norms
     assert np.abs(b - ref).max() < 1e-12 * np.abs(ref).max()
-    assert swept == len(capi.dgm_dx_recurrence(p)[0])
+    assert swept == len(capi.dgm_grad_recurrence(p, direction)[0])
 
 
 def test_header_is_plain_c_and_links(capi, tmp_path):
