@@ -351,9 +351,12 @@ int dgm_eval(dgm_problem* prob, int q1d, double* E_pts, double* H_pts);
  * dgm_grad_support: *nterms, the shifts [nterms][4] = (di, dj, dk, 1 if the term
  * carries the derivative else 0) (nullable), and *lead (nullable), the position
  * of the term that is highest in the order (degree, k, j, i).
- * dgm_grad_recurrence: the coefficients at every (i, j, k) where the support
- * carries exactly one relation (all i >= 1 with the shifted indices <= p), found
- * numerically with the lead coefficient 1, in the printed (unnormalised) basis;
+ * dgm_grad_recurrence: the coefficients at every (i, j, k) with the shifted
+ * indices <= p where the support carries a relation with a nonzero lead term:
+ * all such indices for x and y, i >= 1 for z (d/dz of phi_0jk vanishes).  At
+ * i >= 1 the relation is unique; at i = 0 there are several and a basic one is
+ * returned.  Found numerically with the lead coefficient 1, in the printed
+ * (unnormalised) basis;
  * *count relations, ijk [*count][3] and coef [*count][nterms] nullable for a
  * size query.  p in [1, 8].
  * dgm_grad_sweep: b [N3(p-1)] = coefficients of the derivative of

@@ -22,7 +22,10 @@
 //   highest in the order (degree, k, j, i);
 // - the rest follow by least squares (Householder QR on scaled columns).
 // Where the other columns are rank deficient, the index carries more than one
-// relation (it happens exactly at i = 0); it is left to the dense operator.
+// relation (it happens exactly at i = 0); a basic one is taken (dependent
+// columns dropped), as long as it reproduces the lead.  For d/dz at i = 0 the
+// lead derivative itself vanishes (phi_0jk does not depend on z), and the
+// index needs no relation.
 //
 // Sweep, the 3D analogue of the Legendre example of Sec. 3.2.2.  For
 // u = sum a_ijk phi_ijk the indices are visited from the highest down, in that
@@ -85,45 +88,49 @@ struct Index3 {
     int size() const { return (int)ijk.size() / 3; }
 };
 
-// least squares min |A c - y| for A [m][n] (column-major, n <= m) by Householder QR;
-// returns false when the columns are rank deficient (relative to the largest pivot)
-bool least_squares(int m, int n, std::vector<double> A, std::vector<double> y, std::vector<double>& c) {
-    std::vector<double> diag(n);
+// least squares min |A c - y| for A [m][n] (column-major, n <= m) by Householder
+// QR that skips numerically dependent columns (their coefficient is 0): a basic
+// solution when the columns are rank deficient.  The caller checks the residual.
+void least_squares(int m, int n, std::vector<double> A, std::vector<double> y, std::vector<double>& c) {
+    std::vector<double> colnorm(n), diag;
+    std::vector<int> kept;
     for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += A[(size_t)k * m + i] * A[(size_t)k * m + i];
+        colnorm[k] = std::sqrt(s);
+    }
+    int rank = 0;
+    for (int k = 0; k < n && rank < m; ++k) {
         double* a = &A[(size_t)k * m];
         double nrm = 0.0;
-        for (int i = k; i < m; ++i) nrm += a[i] * a[i];
+        for (int i = rank; i < m; ++i) nrm += a[i] * a[i];
         nrm = std::sqrt(nrm);
-        const double alpha = a[k] > 0 ? -nrm : nrm;
-        diag[k] = alpha;
-        if (nrm == 0.0) continue;
-        a[k] -= alpha;
+        if (!(nrm > 1e-9 * colnorm[k])) continue;   // in the span of the kept columns
+        const double alpha = a[rank] > 0 ? -nrm : nrm;
+        a[rank] -= alpha;
         double vv = 0.0;
-        for (int i = k; i < m; ++i) vv += a[i] * a[i];
-        if (vv == 0.0) continue;
+        for (int i = rank; i < m; ++i) vv += a[i] * a[i];
         for (int j = k + 1; j < n; ++j) {
             double* b = &A[(size_t)j * m];
             double s = 0.0;
-            for (int i = k; i < m; ++i) s += a[i] * b[i];
+            for (int i = rank; i < m; ++i) s += a[i] * b[i];
             s = 2.0 * s / vv;
-            for (int i = k; i < m; ++i) b[i] -= s * a[i];
+            for (int i = rank; i < m; ++i) b[i] -= s * a[i];
         }
         double s = 0.0;
-        for (int i = k; i < m; ++i) s += a[i] * y[i];
+        for (int i = rank; i < m; ++i) s += a[i] * y[i];
         s = 2.0 * s / vv;
-        for (int i = k; i < m; ++i) y[i] -= s * a[i];
+        for (int i = rank; i < m; ++i) y[i] -= s * a[i];
+        diag.push_back(alpha);
+        kept.push_back(k);
+        ++rank;
     }
-    double dmax = 0.0;
-    for (double d : diag) dmax = std::max(dmax, std::fabs(d));
-    for (double d : diag)
-        if (!(std::fabs(d) > 1e-9 * dmax)) return false;
     c.assign(n, 0.0);
-    for (int k = n - 1; k >= 0; --k) {
-        double s = y[k];
-        for (int j = k + 1; j < n; ++j) s -= A[(size_t)j * m + k] * c[j];
-        c[k] = s / diag[k];
+    for (int r = rank - 1; r >= 0; --r) {
+        double s = y[r];
+        for (int t = r + 1; t < rank; ++t) s -= A[(size_t)kept[t] * m + r] * c[kept[t]];
+        c[kept[r]] = s / diag[r];
     }
-    return true;
 }
 
 }  // namespace
@@ -178,8 +185,9 @@ int grad_relations(int p, int dir, std::vector<int>& ijk_out, std::vector<double
             y[q] = -der[(size_t)q * N + cols[S.lead]];
             ynrm += y[q] * y[q];
         }
+        if (!(ynrm > 0.0)) continue;   // the lead derivative vanishes (d/dz of phi_0jk)
         std::vector<double> sol;
-        if (!least_squares(kPoints, m, A, y, sol)) continue;
+        least_squares(kPoints, m, A, y, sol);
         // the relation must hold at every sample, not only in the least-squares sense
         double res = 0.0;
         for (int q = 0; q < kPoints; ++q) {
