@@ -354,8 +354,8 @@ int dgm_eval(dgm_problem* prob, int q1d, double* E_pts, double* H_pts);
  * dgm_grad_recurrence: the coefficients at every (i, j, k) with the shifted
  * indices <= p where the support carries a relation with a nonzero lead term:
  * all such indices for x and y, i >= 1 for z (d/dz of phi_0jk vanishes).  At
- * i >= 1 the relation is unique; at i = 0 there are several and a basic one is
- * returned.  Found numerically with the lead coefficient 1, in the printed
+ * i >= 1 the relation is unique; at i = 0 there are several and the one with
+ * the smallest coefficients (minimum norm) is returned.  Found numerically with the lead coefficient 1, in the printed
  * (unnormalised) basis;
  * *count relations, ijk [*count][3] and coef [*count][nterms] nullable for a
  * size query.  p in [1, 8].

@@ -49,8 +49,8 @@ void phi3_grad(int p, const std::vector<int>& idx, double xi, double eta, double
 // [n][4] = (di, dj, dk, carries the derivative), the lead term's position; returns n.
 int grad_support(int dir, int* nterms, int* shifts, int* lead);
 // The relations at every (i, j, k) with the shifted indices <= p where the
-// support carries a relation with a nonzero lead (a basic one where there are
-// several; 3 ints and n coefficients each, lead coefficient 1, unnormalised basis).
+// support carries a relation with a nonzero lead (the minimum-norm one where
+// there are several; 3 ints and n coefficients each, lead coefficient 1, unnormalised basis).
 int grad_relations(int p, int dir, std::vector<int>& ijk_out, std::vector<double>& coef_out);
 // b [N3(p-1)] = modal derivative in direction dir of u = sum a_ijk phi_ijk
 // (unnormalised basis, lexicographic order) by the backward sweep over those

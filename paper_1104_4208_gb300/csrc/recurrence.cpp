@@ -22,8 +22,9 @@
 //   highest in the order (degree, k, j, i);
 // - the rest follow by least squares (Householder QR on scaled columns).
 // Where the other columns are rank deficient, the index carries more than one
-// relation (it happens exactly at i = 0); a basic one is taken (dependent
-// columns dropped), as long as it reproduces the lead.  For d/dz at i = 0 the
+// relation (it happens exactly at i = 0); the one with the smallest
+// coefficients is taken (minimum-norm least squares), as long as it reproduces
+// the lead.  For d/dz at i = 0 the
 // lead derivative itself vanishes (phi_0jk does not depend on z), and the
 // index needs no relation.
 //
@@ -89,11 +90,14 @@ struct Index3 {
 };
 
 // least squares min |A c - y| for A [m][n] (column-major, n <= m) by Householder
-// QR that skips numerically dependent columns (their coefficient is 0): a basic
-// solution when the columns are rank deficient.  The caller checks the residual.
+// QR that skips numerically dependent columns, then the minimum-norm solution
+// of the triangular system.  For full rank that is back substitution.  Where the
+// columns are dependent, with R = the first r rows of Q^T A (r the rank, all n
+// columns) and b = the first r entries of Q^T y, it is c = R^T w with
+// (R R^T) w = b, the smallest c.  The caller checks the residual.
 void least_squares(int m, int n, std::vector<double> A, std::vector<double> y, std::vector<double>& c) {
-    std::vector<double> colnorm(n), diag;
-    std::vector<int> kept;
+    std::vector<double> colnorm(n);
+    std::vector<char> kept(n, 0);
     for (int k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < m; ++i) s += A[(size_t)k * m + i] * A[(size_t)k * m + i];
@@ -107,29 +111,71 @@ void least_squares(int m, int n, std::vector<double> A, std::vector<double> y, s
         nrm = std::sqrt(nrm);
         if (!(nrm > 1e-9 * colnorm[k])) continue;   // in the span of the kept columns
         const double alpha = a[rank] > 0 ? -nrm : nrm;
-        a[rank] -= alpha;
+        std::vector<double> v(a + rank, a + m);
+        v[0] -= alpha;
         double vv = 0.0;
-        for (int i = rank; i < m; ++i) vv += a[i] * a[i];
-        for (int j = k + 1; j < n; ++j) {
+        for (double x : v) vv += x * x;
+        // apply the reflector to every other column (also those skipped before) and to y
+        for (int j = 0; j < n; ++j) {
+            if (j == k || kept[j]) continue;
             double* b = &A[(size_t)j * m];
             double s = 0.0;
-            for (int i = rank; i < m; ++i) s += a[i] * b[i];
+            for (int i = rank; i < m; ++i) s += v[i - rank] * b[i];
             s = 2.0 * s / vv;
-            for (int i = rank; i < m; ++i) b[i] -= s * a[i];
+            for (int i = rank; i < m; ++i) b[i] -= s * v[i - rank];
         }
         double s = 0.0;
-        for (int i = rank; i < m; ++i) s += a[i] * y[i];
+        for (int i = rank; i < m; ++i) s += v[i - rank] * y[i];
         s = 2.0 * s / vv;
-        for (int i = rank; i < m; ++i) y[i] -= s * a[i];
-        diag.push_back(alpha);
-        kept.push_back(k);
+        for (int i = rank; i < m; ++i) y[i] -= s * v[i - rank];
+        a[rank] = alpha;
+        for (int i = rank + 1; i < m; ++i) a[i] = 0.0;
+        kept[k] = 1;
         ++rank;
     }
     c.assign(n, 0.0);
-    for (int r = rank - 1; r >= 0; --r) {
-        double s = y[r];
-        for (int t = r + 1; t < rank; ++t) s -= A[(size_t)kept[t] * m + r] * c[kept[t]];
-        c[kept[r]] = s / diag[r];
+    if (rank == n) {
+        // full rank: back substitution on the triangle (no squared condition number)
+        for (int r1 = n - 1; r1 >= 0; --r1) {
+            double s = y[r1];
+            for (int t = r1 + 1; t < n; ++t) s -= A[(size_t)t * m + r1] * c[t];
+            c[r1] = s / A[(size_t)r1 * m + r1];
+        }
+        return;
+    }
+    // R [rank][n]: rows 0..rank-1 of the transformed columns; G = R R^T (SPD)
+    std::vector<double> G((size_t)rank * rank, 0.0), w(y.begin(), y.begin() + rank);
+    for (int r1 = 0; r1 < rank; ++r1)
+        for (int r2 = 0; r2 <= r1; ++r2) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += A[(size_t)j * m + r1] * A[(size_t)j * m + r2];
+            G[(size_t)r1 * rank + r2] = G[(size_t)r2 * rank + r1] = s;
+        }
+    // Cholesky G = L L^T, then w = G^{-1} b
+    for (int r1 = 0; r1 < rank; ++r1) {
+        for (int r2 = 0; r2 <= r1; ++r2) {
+            double s = G[(size_t)r1 * rank + r2];
+            for (int t = 0; t < r2; ++t) s -= G[(size_t)r1 * rank + t] * G[(size_t)r2 * rank + t];
+            if (r1 == r2)
+                G[(size_t)r1 * rank + r1] = std::sqrt(std::max(s, 1e-300));
+            else
+                G[(size_t)r1 * rank + r2] = s / G[(size_t)r2 * rank + r2];
+        }
+    }
+    for (int r1 = 0; r1 < rank; ++r1) {
+        double s = w[r1];
+        for (int t = 0; t < r1; ++t) s -= G[(size_t)r1 * rank + t] * w[t];
+        w[r1] = s / G[(size_t)r1 * rank + r1];
+    }
+    for (int r1 = rank - 1; r1 >= 0; --r1) {
+        double s = w[r1];
+        for (int t = r1 + 1; t < rank; ++t) s -= G[(size_t)t * rank + r1] * w[t];
+        w[r1] = s / G[(size_t)r1 * rank + r1];
+    }
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int r1 = 0; r1 < rank; ++r1) s += A[(size_t)j * m + r1] * w[r1];
+        c[j] = s;
     }
 }
 
