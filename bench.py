@@ -337,12 +337,13 @@ for it, name in enumerate(names):
 
 
 def cpu_procs():
-    """Worker processes for the oracle timing: one single-threaded process per host core."""
+    """Worker processes for the oracle timing: one single-threaded process per host core
+    (at most 32; each holds about 1.2 GB at planewave_n32_p6)."""
     try:
         n = len(os.sched_getaffinity(0))
     except AttributeError:
         n = os.cpu_count() or 1
-    return max(1, min(n, 64))
+    return max(1, min(n, 32))
 
 
 def cpu_oracle_samples(names, seconds, procs=None):
