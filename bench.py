@@ -476,7 +476,7 @@ def run_gpu(args, rank, world, local):
     out = None
     if rank == 0:
         cpu = None
-        if not args.no_cpu:
+        if not args.no_cpu and world == 1:   # the oracle baseline is timed at N = 1 only
             res = cpu_oracle_samples([w.name], args.cpu_seconds, args.cpu_procs)
             if res:
                 (r,), procs = res
