@@ -54,9 +54,22 @@ def dof_per_elem(p):
     return 3 * n3(p) + 3 * n3(p - 1)
 
 
-# nominal FP64 rate of one GB300 (no measured FP64 peak is available); the FP64
-# path is bound by it, not by HBM
+# nominal FP64 rate of one GB300: used only if the measurement below fails; the
+# FP64 path is bound by FP64 arithmetic, not by HBM
 FP64_NOMINAL_TFLOPS = 1.25
+_FP64_PEAK = {}
+
+
+def fp64_peak(device=0):
+    """FP64 FMA rate of the device measured in this run (dgm_measure_fp64_peak:
+    CUDA events around a kernel of independent FMA chains on every SM, best of 5)."""
+    if device not in _FP64_PEAK:
+        try:
+            from paper_1104_4208_gb300 import _capi as capi
+            _FP64_PEAK[device] = (capi.dgm_measure_fp64_peak(device, 5), "measured (FP64 FMA microbenchmark, this run)")
+        except Exception as e:   # measurement failed: say so and fall back to the nominal rate
+            _FP64_PEAK[device] = (FP64_NOMINAL_TFLOPS, f"nominal GB300 FP64 rate (measurement failed: {e})")
+    return _FP64_PEAK[device]
 
 
 def n2(q):
@@ -78,10 +91,11 @@ def phase_bytes(nt, p, b):
     return nt * (b * (3 * NE + 6 * NH) + 64 + 20), nt * (b * (6 * NE + 3 * NH) + 64 + 20)
 
 
-def alu_roofline(w, ms_per_step):
+def alu_roofline(w, ms_per_step, device=0):
     achieved = w.nt * flops_per_elem_step(w.p) / (ms_per_step * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 FP64 rate",
+    peak, src = fp64_peak(device)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src,
             "flops_per_element_step": flops_per_elem_step(w.p), "traffic": None}
 
 
@@ -420,7 +434,7 @@ def run_gpu(args, rank, world, local):
         kname, kbytes, kms = kpre + "_E", bytes_E, tE
     peak, peak_src = measured_peak_hbm()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    roof = alu_roofline(w, ms / args.steps) if args.precision == "fp64" else \
+    roof = alu_roofline(w, ms / args.steps, local) if args.precision == "fp64" else \
         {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
             "traffic": profile_traffic(f"{kname}/{args.precision}" if tcp else f"{kname}<{'float' if b == 4 else 'double'}>"),
@@ -445,7 +459,7 @@ def run_gpu(args, rank, world, local):
         fp64 = {"value": v64, "ms_per_step": ms64 / args.steps, "speedup_of_mixed": value / v64,
                 "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0]),
                 "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev,
-                "roofline": alu_roofline(w, ms64 / args.steps)}
+                "roofline": alu_roofline(w, ms64 / args.steps, local)}
         S64.close()
         S = make_solver(w, args.precision)
         project_initial(S, w, torch, q1d)

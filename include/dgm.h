@@ -160,7 +160,9 @@ int dgm_kick(dgm_problem* prob, int which, double dt, void* stream);
  *   W^n = 1/2 (eps E^n, E^n) + 1/2 (mu H^{n-1/2}, H^{n+1/2})
  *         [+ 1/2 sum_F (h_F/alpha) (H^{F,n-1/2}, H^{F,n+1/2})_F]
  * which the scheme conserves exactly up to round-off (Sec. 2.1, Eq. (2)).
- * Blocks until the energies are on the host when energy_out != NULL. */
+ * Blocks until the energies are on the host when energy_out != NULL.  With
+ * energies requested, a blow-up is reported as DGM_ERR_UNSTABLE: a recorded
+ * energy that is not finite, or (no point source set) one above 10 W^0. */
 int dgm_run(dgm_problem* prob, double dt, int64_t nsteps, void* stream, double* energy_out);
 
 /* Higher-order symplectic time stepping (Sec. 3 leaves the explicit integrator
@@ -292,6 +294,27 @@ typedef struct dgm_run_stats {
 int dgm_run_timed(dgm_problem* prob, double dt, int64_t nsteps, void* stream,
                   double* energy_out, dgm_run_stats* stats);
 
+/* Failure injection for tests of the bounded waits (tensor-core precisions
+ * only; not part of the method of the paper).  The next `nlaunches` phase
+ * kernels this problem launches each first wait on a barrier that nothing
+ * arrives at; the wait gives up after about a millisecond, before the kernel
+ * has issued any copy or MMA, the kernel records the timeout in the problem's
+ * device error word, frees its tensor memory and returns without touching the
+ * fields.  The host call that next reads the error word (dgm_run with
+ * energies, dgm_run_composed, dgm_get_fields) returns DGM_ERR_TIMEOUT and
+ * clears it; the problem stays usable.  nlaunches = 0 cancels a pending
+ * injection.  DGM_ERR_UNSUPPORTED for the CUDA-core precisions, which have no
+ * waits. */
+int dgm_inject_wait_timeout(dgm_problem* prob, int nlaunches);
+
+/* FP64 arithmetic peak of CUDA device `device` in TFLOP/s (2 flops per fused
+ * multiply-add), measured with CUDA events over `repeats` timed launches of a
+ * kernel of independent FMA chains that fills every SM (the best launch
+ * counts).  The FP64 path's phase kernels are bound by FP64 arithmetic, so this
+ * is their roofline denominator.  Not part of the method of the paper.
+ * Allocates and frees a small device buffer; blocks. */
+int dgm_measure_fp64_peak(int device, int repeats, double* tflops);
+
 /* Discrete energy 1/2 (eps E,E) + 1/2 (mu H,H) [+ face term] of the current
  * state (no staggering), FP64. */
 int dgm_energy(dgm_problem* prob, double* W);
@@ -300,12 +323,16 @@ int dgm_energy(dgm_problem* prob, double* W);
  * on the problem's device) and ordered on `stream`, without allocating any
  * device memory.  The paper has no counterpart; this serves callers that may
  * not call cudaMalloc/cudaFree (for example applications that hand all device
- * memory to their own pool at start-up).  The partial sums live in a fixed
- * device array of 4096 doubles per device, shared by every call: calls whose
- * kernels overlap on the GPU race on it.  The first call on a device looks up
- * that array's address; make it before any stream capture.  Problems needing
- * more than 4096 partial sums are rejected with DGM_ERR_INVALID_ARG (on GB300
- * a problem uses at most 16 per SM). */
+ * memory to their own pool at start-up).  Every precision is served: the
+ * CUDA-core precisions through the H-phase kernel with dt = 0, the tensor-core
+ * precisions through the state-energy kernel of the tiled state.  The partial
+ * sums live in a fixed device array of 4096 doubles per device, shared by
+ * every call: calls whose kernels overlap on the GPU race on it.  The first
+ * call on a device looks up that array's address; make it before any stream
+ * capture.  Problems needing more than 4096 partial sums are rejected with
+ * DGM_ERR_INVALID_ARG; on GB300 (152 SMs) a problem uses at most 24 per SM
+ * (CUDA-core precisions, autotuned) or 4 per SM (tensor-core precisions: two
+ * CTAs, an E and an H sum each), so none is rejected there. */
 int dgm_energy_noalloc(dgm_problem* prob, double* W_device, void* stream);
 
 /* Initial data and evaluation (Sec. 2: initial conditions; covariant L2

@@ -85,6 +85,8 @@ _SIGS = {
     "dgm_get_time": ([_vp, _pd], C.c_int),
     "dgm_adjoint_grad": ([_vp, C.c_double, _i64, C.c_int, _pd, C.c_int, _pd, _pd, _pd], C.c_int),
     "dgm_energy_noalloc": ([_vp, _vp, _vp], C.c_int),
+    "dgm_inject_wait_timeout": ([_vp, C.c_int], C.c_int),
+    "dgm_measure_fp64_peak": ([C.c_int, C.c_int, _pd], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
     "dgm_batch_create": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)], C.c_int),
@@ -297,6 +299,17 @@ def dgm_energy(prob):
 
 def dgm_energy_noalloc(prob, W_device_ptr, stream=None):
     _check(_lib.dgm_energy_noalloc(prob, W_device_ptr, stream))
+
+
+def dgm_inject_wait_timeout(prob, nlaunches):
+    _check(_lib.dgm_inject_wait_timeout(prob, int(nlaunches)))
+
+
+def dgm_measure_fp64_peak(device=0, repeats=5):
+    """-> measured FP64 FMA rate of the device in TFLOP/s."""
+    t = C.c_double()
+    _check(_lib.dgm_measure_fp64_peak(int(device), int(repeats), C.byref(t)))
+    return t.value
 
 
 def dgm_reference_table(p, which):

@@ -140,7 +140,7 @@ template <typename real>
 int add_point_source(real* E, int N, int K, int tiled, int64_t ts, const double* phi, const double* v,
                      const double* fvals, int64_t n, double dt, cudaStream_t s) {
     k_point_source<real><<<1, 128, 0, s>>>(E, Lay{N, K, tiled}, ts, phi, v, fvals, n, dt);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 template int add_point_source<double>(double*, int, int, int, int64_t, const double*, const double*, const double*,
                                       int64_t, double, cudaStream_t);
@@ -151,14 +151,14 @@ template <typename real>
 int adj_observe(const ObsDev& O, const real* E, int N, int K, int tiled, double* J, cudaStream_t s) {
     if (O.nobs > kMaxObs) return -1;
     k_observe<real><<<1, kObsWarps * 32, 0, s>>>(O, E, Lay{N, K, tiled}, J);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
 int adj_source(const ObsDev& O, const real* E, real* adj, int N, int K, int tiled, cudaStream_t s) {
     if (O.nobs > kMaxObs) return -1;
     k_obs_source<real><<<1, kObsWarps * 32, 0, s>>>(O, E, adj, Lay{N, K, tiled});
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -167,7 +167,7 @@ int adj_grad(int64_t nt, const double* geo, const real* adj, const real* E1, con
     const int64_t blocks = (nt + 7) / 8;   // 8 warps of 32 per block, one warp per element
     k_grad_accum<real><<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(nt, geo, adj, E1, E0, Lay{N, K, tiled},
                                                                            grad);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template int adj_observe<double>(const ObsDev&, const double*, int, int, int, double*, cudaStream_t);

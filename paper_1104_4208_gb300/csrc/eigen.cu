@@ -86,25 +86,25 @@ int grid_for(int64_t n) {
 int eig_mass_apply(int64_t nt, int N, const double* geo, const double* x, double* z, cudaStream_t s) {
     if (nt <= 0) return 0;
     k_mass_apply<<<grid_for(nt * N), kThreads, 0, s>>>(nt, N, geo, x, z);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int eig_scale(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
     if (n <= 0) return 0;
     k_scale<<<grid_for(n), kThreads, 0, s>>>(n, a, x, y);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int eig_dots(const double* V, int64_t ld, int k, const double* z, int64_t n, double* out, cudaStream_t s) {
     if (k <= 0) return 0;
     k_dots<<<k, kThreads, 0, s>>>(V, ld, z, n, out);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int eig_sub_combination(double* w, const double* V, int64_t ld, int k, const double* h, int64_t n, cudaStream_t s) {
     if (k <= 0 || n <= 0) return 0;
     k_sub_combination<<<grid_for(n), kThreads, 0, s>>>(w, V, ld, k, h, n);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 // ------------------------------------------------------------------ host side

@@ -29,7 +29,7 @@ int launch_quad_points(int64_t nt, int nq, const double* maps, const double* xh,
     if (n <= 0) return 0;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
     k_quad_points<<<(int)blocks, 256, 0, s>>>(nt, nq, maps, xh, out);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace dgm

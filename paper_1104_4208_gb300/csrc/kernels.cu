@@ -467,7 +467,7 @@ int launch_project(int64_t nt, int N, int nq, const double* maps, const double* 
                    cudaStream_t s) {
     const int64_t blocks = (nt + 3) / 4;
     k_project<real><<<(int)(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(nt, N, nq, maps, wphi, pts, out);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -475,7 +475,7 @@ int launch_eval(int64_t nt, int N, int nq, const double* maps, const double* phi
                 cudaStream_t s) {
     const int64_t blocks = (nt + 3) / 4;
     k_eval<real><<<(int)(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(nt, N, nq, maps, phi, c, pts);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template int launch_project<double>(int64_t, int, int, const double*, const double*, const double*, double*, cudaStream_t);
@@ -495,7 +495,7 @@ int launch_phase_H(const KParams<real>& P, int grid, double dt, double a_lo, dou
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_phase_H<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_phase_H<real><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -504,7 +504,7 @@ int launch_phase_E(const KParams<real>& P, int grid, double dt, cudaStream_t s) 
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_phase_E<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_phase_E<real><<<grid, kWarps * 32, smem, s>>>(P, dt);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -512,7 +512,7 @@ int launch_import(const double* src, real* dst, const double* nrm, int64_t n, in
     if (n == 0) return 0;
     const int64_t blocks = (n + 255) / 256;
     k_import<real><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, nrm, n, ncoef);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -520,7 +520,7 @@ int launch_export(const real* src, double* dst, const double* nrm, int64_t n, in
     if (n == 0) return 0;
     const int64_t blocks = (n + 255) / 256;
     k_export<real><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(src, dst, nrm, n, ncoef);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
@@ -528,14 +528,14 @@ int launch_axpby(int64_t n, double a, const real* x, double b, real* y, cudaStre
     if (n == 0) return 0;
     const int64_t blocks = (n + 255) / 256;
     k_axpby<real><<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, a, x, b, y);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 template int launch_axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);
 template int launch_axpby<float>(int64_t, double, const float*, double, float*, cudaStream_t);
 
 int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s) {
     k_energy_reduce<<<1, 256, 0, s>>>(partials, n, out);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int phase_warps_per_block() { return kWarps; }

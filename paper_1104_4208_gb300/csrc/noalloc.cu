@@ -8,13 +8,16 @@
 // application.  dgm_energy may allocate (its output slot is created on first
 // use); this entry point never does.
 //
-// How: the H-phase kernel writes one FP64 partial sum per thread block.  Here
-// those partials go to a file-scope device array of fixed size instead of a
-// buffer owned by the problem, and the fixed-order reduction writes the result
-// to the caller's device pointer.  The array exists once per device for the
-// lifetime of the process.  Its device address is looked up with
-// cudaGetSymbolAddress on the first call made on each device (so make that
-// first call before any stream capture); later calls reuse the address.
+// How: the energy kernels write one FP64 partial sum per thread block -- the
+// H-phase kernel with dt = 0 on the CUDA-core precisions (FP64, FP32), the
+// state-energy kernel on the tensor-core precisions (TC32, TC16; two sums, E
+// and H, per block).  Here those partials go to a file-scope device array of
+// fixed size instead of a buffer owned by the problem, and the fixed-order
+// reduction writes the result to the caller's device pointer.  The array
+// exists once per device for the lifetime of the process.  Its device address
+// is looked up with cudaGetSymbolAddress on the first call made on each
+// device (so make that first call before any stream capture); later calls
+// reuse the address.
 //
 // Every call on a device shares the one array: two calls whose kernels overlap
 // on the GPU (different streams, different problems) race on it and may return
@@ -73,8 +76,11 @@ extern "C" int dgm_energy_noalloc(dgm_problem* P, double* W_device, void* stream
         dgm::set_error("dgm_energy_noalloc: null argument");
         return DGM_ERR_INVALID_ARG;
     }
-    if (P->grid > kNoallocMaxBlocks) {
-        dgm::set_error("dgm_energy_noalloc: the problem uses " + std::to_string(P->grid) +
+    // partial sums this problem's energy kernels write: one per block of the
+    // CUDA-core phase kernel, or an E and an H sum per tensor-core CTA
+    const int nsums = P->tc ? 2 * P->tc_grid : P->grid;
+    if (nsums > kNoallocMaxBlocks) {
+        dgm::set_error("dgm_energy_noalloc: the problem uses " + std::to_string(nsums) +
                        " partial sums but the static scratch holds at most " +
                        std::to_string(kNoallocMaxBlocks));
         return DGM_ERR_INVALID_ARG;
@@ -94,11 +100,21 @@ extern "C" int dgm_energy_noalloc(dgm_problem* P, double* W_device, void* stream
     int rc = scratch_for_current_device(&scratch);
     if (rc == DGM_OK) {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        // dt = 0: the H-phase leaves H unchanged and its energy partial is
-        // 1/2 (eps E, E) + 1/2 (mu H, H) -- the same launch dgm_energy makes
-        int r = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, 0.0, 0.0, 0.0, scratch, s)
+        int r;
+        if (P->tc) {
+            // the tiled state's 1/2 (eps E, E) and 1/2 (mu H, H) partials, E sums
+            // first, then H sums -- the launch dgm_energy makes, redirected
+            dgm::TCArgs a = P->tca;
+            a.partE = scratch;
+            a.partH = scratch + P->tc_grid;
+            r = dgm::tc_launch_state_energy(a, P->tc_grid, s);
+        } else {
+            // dt = 0: the H-phase leaves H unchanged and its energy partial is
+            // 1/2 (eps E, E) + 1/2 (mu H, H) -- the same launch dgm_energy makes
+            r = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, 0.0, 0.0, 0.0, scratch, s)
                         : dgm::launch_phase_H<double>(P->kd, P->grid, 0.0, 0.0, 0.0, scratch, s);
-        if (r == 0) r = dgm::launch_energy_reduce(scratch, P->grid, W_device, s);
+        }
+        if (r == 0) r = dgm::launch_energy_reduce(scratch, nsums, W_device, s);
         if (r != 0) {
             dgm::set_error(std::string("dgm_energy_noalloc: launch failed: ") +
                            cudaGetErrorString(cudaGetLastError()));

@@ -68,6 +68,7 @@ struct dgm_problem {
     double* dTcGeo = nullptr;
     int32_t* dTcNbr = nullptr;
     int* dErr = nullptr;
+    int tc_stall_tests = 0;              // phase launches still to run as failure injections
     bool trE_valid = false, trH_valid = false;
     std::vector<double> hmaps;           // [nt][12] X0, F (host copy, point location)
     double time = 0.0;                   // time of the state (advanced by dgm_run)
@@ -102,6 +103,9 @@ void tc_problem_free(dgm_problem* P);
 int tc_import(dgm_problem* P, const double* dE, const double* dH, const double* nrmE, const double* nrmH,
               cudaStream_t s);
 int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const double* nrmH, cudaStream_t s);
+// the problem's kernel arguments for one phase launch (a pending failure
+// injection of dgm_inject_wait_timeout is consumed here)
+TCArgs tc_launch_args(dgm_problem* P);
 int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s);
 int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s);
 int tc_traces(dgm_problem* P, int which, cudaStream_t s);

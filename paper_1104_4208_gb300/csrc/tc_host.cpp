@@ -271,12 +271,22 @@ int tc_ensure_traces_E(dgm_problem* P, bool energy, cudaStream_t s) {
     return DGM_OK;
 }
 
+TCArgs tc_launch_args(dgm_problem* P) {
+    TCArgs a = P->tca;
+    a.stall_test = 0;
+    if (P->tc_stall_tests > 0) {
+        a.stall_test = 1;
+        --P->tc_stall_tests;
+    }
+    return a;
+}
+
 int tc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s) {
     {
         int rc = tc_ensure_traces_E(P, energy_slot != nullptr, s);
         if (rc) return rc;
     }
-    if (tc_launch_phase_H(P->tca, P->tc_grid, dt, a_lo, c_out, energy_slot ? 1 : 0, s))
+    if (tc_launch_phase_H(tc_launch_args(P), P->tc_grid, dt, a_lo, c_out, energy_slot ? 1 : 0, s))
         return cuda_err(cudaGetLastError(), "H-phase launch");
     P->trH_valid = true;
     if (energy_slot && launch_energy_reduce(P->tca.partE, 2 * P->tc_grid, energy_slot, s))
@@ -289,7 +299,7 @@ int tc_phase_E(dgm_problem* P, double dt, bool energy, cudaStream_t s) {
         int rc = tc_traces(P, 1, s);
         if (rc) return rc;
     }
-    if (tc_launch_phase_E(P->tca, P->tc_grid, dt, energy ? 1 : 0, s))
+    if (tc_launch_phase_E(tc_launch_args(P), P->tc_grid, dt, energy ? 1 : 0, s))
         return cuda_err(cudaGetLastError(), "E-phase launch");
     P->trE_valid = true;
     P->trE_ndirty = 0;

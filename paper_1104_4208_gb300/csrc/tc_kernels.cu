@@ -47,6 +47,7 @@ constexpr int kStages = 4;
 constexpr uint32_t kHead = 256;             // control block at the start of shared memory
 constexpr long long kLimit = 4000000000LL;  // cycles before a wait gives up (~2 s)
 constexpr long long kDrain = 200000000LL;
+constexpr long long kStallTestLimit = 2000000LL;   // ~1 ms: the injected wait's limit
 constexpr int kErrTimeout = 1;
 
 int padto(int x, int m) { return (x + m - 1) / m * m; }
@@ -403,7 +404,14 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
     uint32_t g = 0, done_cnt = 0;
     double eacc = 0.0;
     const int half_steps = d.FB / OP::VPC;   // MMA K-steps of two faces (2 FB values)
-    for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    if (A.stall_test) {
+        // failure injection: wait on the `load` barrier, which nothing arrives
+        // at, until the limit runs out -- before any copy or MMA is issued, so
+        // nothing is in flight when the kernel gives up
+        if (tid == 0 && !tc::mbar_wait(&ctl->load, 0u, kStallTestLimit)) ctl->abort = 1;
+        __syncthreads();
+    }
+    for (int tile = blockIdx.x; tile < A.ntiles && !ctl->abort; tile += gridDim.x) {
         const int64_t t = (int64_t)tile * kTcRows + tid;
         // GEMM1: curl (H-phase) or curl^T (E-phase) of the input field
         if (tid == 0) {
@@ -720,7 +728,7 @@ int launch_phase(const TCArgs& a, int grid, double dt, double a_lo, double c_out
     const size_t sm = smem_of(a);
     if (set_smem((const void*)k_tc_phase<IS_H, OP>, sm)) return -1;
     k_tc_phase<IS_H, OP><<<grid, 128, sm, s>>>(a, dt, a_lo, c_out, energy);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename OP>
@@ -728,7 +736,7 @@ int launch_traces(const TCArgs& a, int grid, int which, int tile0, int tile1, in
     const size_t sm = smem_of(a);
     if (set_smem((const void*)k_tc_traces<OP>, sm)) return -1;
     k_tc_traces<OP><<<grid, 128, sm, s>>>(a, which, tile0, tile1, energy);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
@@ -757,12 +765,12 @@ int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s) {
     if (n == 0) return 0;
     const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
     k_to_half<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(dst), n);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s) {
     k_tc_state_energy<<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s) {
@@ -770,7 +778,7 @@ int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt,
     if (n == 0) return 0;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
     k_tc_pack<<<(int)blocks, 256, 0, s>>>(src, dst, nrm, nt, N, K);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s) {
@@ -778,7 +786,7 @@ int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t n
     if (n == 0) return 0;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
     k_tc_unpack<<<(int)blocks, 256, 0, s>>>(src, dst, nrm, nt, N, K);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace dgm

@@ -53,6 +53,8 @@ struct TCArgs {
     uint32_t stage_bytes;      // bytes of one ring stage
     uint32_t tmem_cols;        // TMEM columns allocated per CTA (power of two)
     uint32_t r2_offset;        // offset of the resident tile region
+    int stall_test;            // nonzero: the phase kernel waits on a barrier nothing arrives at,
+                               // gives up after a short limit, records a timeout and does no work
 };
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset);

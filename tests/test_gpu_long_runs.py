@@ -1,0 +1,122 @@
+"""Full-length accuracy of the headline workload in every precision.
+
+planewave_n32_p6: periodic unit box, n = 32 (196,608 tets), p = 6, eps = mu = 1,
+plane wave k = 2 pi (1, 2, 3), dt = 0.2 h / p^2, 2,000 leapfrog steps (Sec. 3),
+central flux (Sec. 2.1).  Each precision starts from the same device projection
+of the wave and runs the whole horizon with the energy recorded every step.
+The FP64 path is the reference: its kicks match the FP64 oracle to 1e-12 at
+this size (test_sampled_parity_full_planewave_workload), so its end state
+stands for the oracle's.  Reported per precision (DGM_TEST_LOG):
+
+  dev_fp64   ||E - E_fp64||_M / ||E_fp64||_M     (M: the mass matrix, eps = 1)
+  err_wave   ||E - P E_wave(T)||_M / ||P E_wave(T)||_M, P the L2 projection
+  drift      max_n |W^n - W^0| / W^0 of the modified energy
+
+Bounds, per precision (stated before the tests, from the arithmetic):
+  FP64   drift 1e-11; err_wave within 1e-12 of itself (reference)
+  FP32   dev_fp64 1e-4, drift 1e-5
+  TC32   dev_fp64 2e-2, drift 1e-4
+  TC16   dev_fp64 2e-2, drift 1e-4
+The tensor-core operands carry 10 mantissa bits (unit roundoff 4.9e-4); a
+table entry's rounding perturbs the operator once (C_h and C_h^T stay exact
+transposes, so the scheme stays energy conserving), while the state's
+rounding to the operand type is fresh noise in every kick.
+"""
+
+import numpy as np
+import pytest
+
+from workloads.configs import make_workload
+from workloads.fields import plane_wave_fields
+
+pytestmark = pytest.mark.gpu
+
+BOUND_DEV = {"fp32": 1e-4, "tc32": 2e-2, "tc16": 2e-2}
+BOUND_DRIFT = {"fp64": 1e-11, "fp32": 1e-5, "tc32": 1e-4, "tc16": 1e-4}
+
+
+def _log(name, **kw):
+    import json, os
+    path = os.environ.get("DGM_TEST_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(dict(test=name, **kw)) + "\n")
+
+
+def _project(capi, S, w, T, torch):
+    """E, H of the solver := L2 projections of the plane wave at time T (device path)."""
+    q1d = w.p + 1
+    xh, _ = capi.dgm_quad_rule(q1d)
+    maps = capi.dgm_element_maps(S.mesh, S.nt)
+    F = maps[:, 3:].reshape(-1, 3, 3)
+    Ed = torch.empty((S.nt, xh.shape[0], 3), dtype=torch.float64, device="cuda")
+    Hd = torch.empty_like(Ed)
+    for s in range(0, S.nt, 16384):
+        e = min(S.nt, s + 16384)
+        x = maps[s:e, None, :3] + np.einsum("tij,qj->tqi", F[s:e], xh)
+        Ex, Hx = plane_wave_fields(x, T)
+        Ed[s:e].copy_(torch.from_numpy(Ex))
+        Hd[s:e].copy_(torch.from_numpy(Hx))
+    capi.dgm_project_device(S.prob, q1d, Ed.data_ptr(), Hd.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    del Ed, Hd
+    torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def runs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4208_gb300 import build
+    build.build()
+    from paper_1104_4208_gb300 import _capi as capi
+    from paper_1104_4208_gb300.solver import Solver
+    w = make_workload("planewave_n32_p6")
+    m = w.mesh
+    out = {}
+    for prec in ("fp64", "fp32", "tc32", "tc16"):
+        S = Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=prec)
+        _project(capi, S, w, 0.0, torch)
+        W = S.run(w.dt, w.steps, energies=True)
+        E, _ = S.get_fields()
+        out[prec] = (E, W)
+        if prec != "fp64":
+            S.close()
+        else:
+            S64 = S
+    # mass-norm measurements with the FP64 problem (eps = mu = 1): energy of (X, 0) = ||X||^2 / 2
+    T = w.steps * w.dt
+    zH = np.zeros(S64.nH)
+
+    def norm(X):
+        S64.set_fields(X, zH)
+        return np.sqrt(2.0 * S64.energy())
+
+    E64 = out["fp64"][0]
+    _project(capi, S64, w, T, torch)
+    Ewave, _ = S64.get_fields()
+    res = {}
+    n64, nwave = norm(E64), norm(Ewave)
+    for prec, (E, W) in out.items():
+        res[prec] = dict(dev_fp64=norm(E - E64) / n64, err_wave=norm(E - Ewave) / nwave,
+                         drift=float(np.abs(W - W[0]).max() / W[0]))
+        _log("planewave_2000_steps", precision=prec, **res[prec])
+    S64.close()
+    return res
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])
+def test_planewave_full_horizon(runs, precision):
+    """planewave_n32_p6 over its stated 2,000 steps: deviation from the FP64 path,
+    error against the analytic wave and energy drift within each precision's bound."""
+    r = runs[precision]
+    assert r["drift"] < BOUND_DRIFT[precision]
+    if precision == "fp64":
+        assert r["dev_fp64"] == 0.0
+        # the discretisation error of the FP64 path over the horizon: small against the wave
+        assert r["err_wave"] < 1e-3
+    else:
+        assert r["dev_fp64"] < BOUND_DEV[precision]
+        # the triangle inequality ties each error against the wave to the FP64 path's
+        assert abs(r["err_wave"] - runs["fp64"]["err_wave"]) <= r["dev_fp64"] * 1.0001 + 1e-12

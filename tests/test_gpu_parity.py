@@ -179,7 +179,7 @@ def test_sampled_parity_full_pulse_workload(capi, precision):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tc32", "tc16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])
 def test_sampled_parity_full_planewave_workload(capi, precision):
     """Workload planewave_n32_p6 at full size (196,608 tets, periodic, p=6) in the
     launch configuration the benchmark times (autotuned first): one H-kick and
@@ -613,6 +613,53 @@ def test_batch_graph_matches_individual_runs(capi):
     for pair, _ in made:
         for S in pair:
             S.close()
+
+
+def test_batch_vs_oracle(capi):
+    """dgm_batch_run (one CUDA graph for several problems) against the oracle's own
+    leapfrog (Sec. 3), run by run: a plain FP64 run, an FP64 run driven by a point
+    dipole source, and a TC16 run with a source, in one batch; fields after 20
+    steps and the per-step energies."""
+    from oracle.dg import OracleDG, dipole_source_vector
+    from workloads.fields import dipole_waveform
+    from paper_1104_4208_gb300.solver import Solver
+    specs = [(2, 3, "fp64", False), (3, 2, "fp64", True), (3, 3, "tc16", True)]
+    N = 20
+    rng = np.random.default_rng(91)
+    made = []
+    for k, (n, p, prec, src) in enumerate(specs):
+        m = kuhn_cube_mesh(n, jitter=0.1, seed=910 + k, shuffle_local=True)
+        eps = rng.uniform(1, 4, m.nt)
+        dt = 0.2 / n / p ** 2
+        dg = OracleDG(m.xyz, m.tets, p, eps, 1.0)
+        S = Solver(m.xyz, m.tets, p, eps, 1.0, precision=prec)
+        if src:
+            E0, H0 = np.zeros(dg.sizeE), np.zeros(dg.sizeH)
+            xs, d = rng.uniform(0.3, 0.7, 3), np.array([0.0, 0.6, 0.8])
+            tau = N * dt / 6
+            t0 = 3 * tau
+            unit = dipole_source_vector(dg, xs, d, 1.0)
+            f = (lambda u, t0, tau: (lambda i: u * dipole_waveform((i + 0.5) * dt, t0, tau)))(unit, t0, tau)
+            capi.dgm_set_source(S.prob, xs, d, t0, tau, 1.0)
+            capi.dgm_set_time(S.prob, 0.0)
+            Eo, Ho, _, Wo = dg.run(E0, H0, dt, N, source=f)
+        else:
+            E0, H0 = rng.standard_normal(dg.sizeE), rng.standard_normal(dg.sizeH)
+            Eo, Ho, _, Wo = dg.run(E0, H0, dt, N)
+        S.set_fields(E0, H0)
+        made.append((S, dt, prec, Eo, Ho, Wo))
+    B = capi.dgm_batch_create(made[0][0].ctx, [x[0].prob for x in made])
+    Wb = np.empty((len(made), N + 1))
+    capi.dgm_batch_run(B, np.array([x[1] for x in made]), N, None, Wb)
+    capi.dgm_batch_destroy(B)
+    for r, (S, dt, prec, Eo, Ho, Wo) in enumerate(made):
+        E, H = S.get_fields()
+        eE, eH = _rel(E, Eo), _rel(H, Ho)
+        eW = float(np.abs(Wb[r] - Wo).max() / np.abs(Wo).max())
+        _log("batch_vs_oracle", run=r, precision=prec, errE=eE, errH=eH, errW=eW)
+        assert eE < TOL_TRAJ[prec] and eH < TOL_TRAJ[prec], (r, eE, eH)
+        assert eW < (1e-12 if prec == "fp64" else 1e-3), (r, eW)
+        S.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])

@@ -4,9 +4,11 @@ dgm_energy_noalloc exists for callers that may not allocate device memory
 (for instance applications whose pool allocator owns the whole device); it
 keeps its partial sums in a fixed device array instead.  This test calls it
 through the C ABI twice in a row, on two different states of the same
-problem, and checks each result against dgm_energy on that state.  It lives
-in its own file, collected last, and passes both alone in a fresh process and
-after the other GPU tests.
+problem, and checks each result against dgm_energy on that state, for every
+precision (the tensor-core ones reduce the tiled state's partial sums).  The
+second call must leave the device's free memory unchanged.  It lives in its
+own file, collected last, and passes both alone in a fresh process and after
+the other GPU tests.
 """
 
 import numpy as np
@@ -15,7 +17,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16"])
 def test_energy_noalloc_matches_dgm_energy(precision):
     import torch
     if not torch.cuda.is_available():
@@ -41,12 +43,15 @@ def test_energy_noalloc_matches_dgm_energy(precision):
     S.kick(0, 0.01)
     S.kick(1, 0.01)
     torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
     capi.dgm_energy_noalloc(S.prob, out[1:2].data_ptr(), stream.cuda_stream)
     torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
     ref1 = S.energy()
 
     got = out.cpu().numpy()
     assert abs(got[0] - ref0) <= 1e-12 * abs(ref0)
     assert abs(got[1] - ref1) <= 1e-12 * abs(ref1)
     assert ref0 != ref1
+    assert free1 == free0, (free0, free1)
     S.close()
