@@ -37,10 +37,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DoF-steps/s at p=4/6 (mixed vs FP64 plain, same GB300); % HBM roofline; err"
-DTYPE = {"tc32": "tf32", "tc16": "f16", "fp32": "f32", "fp64": "f64"}
+DTYPE = {"tc32": "tf32", "tc16": "f16", "tcbf16": "bf16", "fp32": "f32", "fp64": "f64"}
 ARITH = {"tc32": "fp32 state, TF32 tensor-core operators (tcgen05), fp32 accumulate, fp64 geometry and energy",
          "tc16": "fp32 state with fp16 operand copies, fp16 tables and trace buffers, fp16 tensor-core operators "
                  "(tcgen05 kind::f16), fp32 accumulate, fp64 geometry and energy",
+         "tcbf16": "fp32 state with bf16 operand copies, bf16 tables and trace buffers, bf16 tensor-core "
+                   "operators (tcgen05 kind::f16, bf16 encoding), fp32 accumulate, fp64 energy sums",
          "fp32": "fp32 state and CUDA-core arithmetic, fp64 geometry and energy",
          "fp64": "fp64 throughout"}
 UNIT = "DoF-steps/s"
@@ -106,7 +108,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="planewave_n32_p6")
-    ap.add_argument("--precision", default="tc16", choices=["tc16", "tc32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tc16", choices=["tc16", "tcbf16", "tc32", "fp32", "fp64"])
+    ap.add_argument("--variant", type=int, default=0,
+                    help="TC16 only: 0 resident-table kernels (default), 1 dense-operator kernels")
+    ap.add_argument("--no-p4", action="store_true", help="skip the p = 4 sub-block of the default workload")
     ap.add_argument("--fp64-steps", type=int, default=1, help="nonzero: also run the FP64 path over the same steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     ap.add_argument("--cpu-procs", type=int, default=None,
@@ -197,6 +202,7 @@ def profile_traffic(kernel):
     recorded beside the numbers)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = os.path.join(ROOT, "paper_1104_4208_gb300", "csrc",
+                       "tc2_kernels.cu" if kernel.startswith("k_tc2") else
                        "tc_kernels.cu" if kernel.startswith("k_tc") else "kernels.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -210,10 +216,11 @@ def profile_traffic(kernel):
 
 
 # ---------------------------------------------------------------- GPU arm
-def make_solver(w, precision):
+def make_solver(w, precision, variant=0):
     from paper_1104_4208_gb300.solver import Solver
     m = w.mesh
-    return Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=precision)
+    return Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=precision,
+                  variant=variant if precision == "tc16" else 0)
 
 
 def project_initial(S, w, torch, q1d):
@@ -402,7 +409,7 @@ def run_gpu(args, rank, world, local):
     D = dof_per_elem(w.p)
     dofs = w.nt * D
     q1d = w.p + 1
-    S = make_solver(w, args.precision)
+    S = make_solver(w, args.precision, args.variant)
     maps, xh = project_initial(S, w, torch, q1d)
     err0 = l2_rel_error(S, w, torch, q1d, maps, xh, 0.0)
     dt = w.dt
@@ -426,8 +433,9 @@ def run_gpu(args, rank, world, local):
     bytes_H, bytes_E = phase_bytes(w.nt, w.p, b)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
-    tcp = args.precision in ("tc32", "tc16")
-    kpre = "k_tc_phase" if tcp else "k_phase"
+    tcp = args.precision in ("tc32", "tc16", "tcbf16")
+    resident = args.precision in ("tc16", "tcbf16") and args.variant == 0
+    kpre = "k_tc2_phase" if resident else ("k_tc_phase" if tcp else "k_phase")
     if stats.h_phase_ms >= stats.e_phase_ms:
         kname, kbytes, kms = kpre + "_H", bytes_H, tH
     else:
@@ -461,7 +469,7 @@ def run_gpu(args, rank, world, local):
                 "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev,
                 "roofline": alu_roofline(w, ms64 / args.steps, local)}
         S64.close()
-        S = make_solver(w, args.precision)
+        S = make_solver(w, args.precision, args.variant)
         project_initial(S, w, torch, q1d)
 
     # end to end through the C ABI with pinned host buffers
@@ -487,6 +495,10 @@ def run_gpu(args, rank, world, local):
                "note": "one upload, K steps, one download per timed call"}
     S.close()
 
+    p4 = None
+    if args.workload == "planewave_n32_p6" and not args.no_p4:
+        p4 = p4_block(args, torch, world)
+
     out = None
     if rank == 0:
         cpu = None
@@ -507,13 +519,80 @@ def run_gpu(args, rank, world, local):
                           "l2": l2_note(dofs * (8 if args.precision == "fp64" else 4)),
                           "state_mb": dofs * (8 if args.precision == 'fp64' else 4) / 1e6,
                           "arithmetic": ARITH[args.precision],
-                          "launch": ({"autotuned": tune, "unit": "CTAs per SM" if tcp else "blocks per SM"}
+                          "kernels": ("resident-table tensor-core kernels (k_tc2)" if resident else
+                                      "dense-operator tensor-core kernels (k_tc_phase)" if tcp else
+                                      "CUDA-core kernels (k_phase)"),
+                          "launch": ({"autotuned": tune,
+                                      "unit": ("update/trace threads per element, one CTA per SM" if resident
+                                               else "CTAs per SM" if tcp else "blocks per SM")}
                                      if tune else "default")},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks,
                "err": {"l2_rel_E_vs_analytic": err, "l2_rel_E_initial_projection": err0,
                        "energy_drift": drift},
-               "fp64_plain": fp64}
+               "fp64_plain": fp64, "p4": p4}
+    return out
+
+
+P4_WORKLOADS = ("pulse_n16_p4", "pulse_n32_p4")
+P4_PRECISIONS = ("fp64", "fp32", "tc16")
+
+
+def p4_block(args, torch, world):
+    """The metric's p = 4 half, beside the p = 6 headline: pulse_n16_p4 (24,576 tets,
+    state in L2) and pulse_n32_p4 (196,608 tets, state larger than L2), each in FP64,
+    FP32 and TC16 (autotuned unless --no-autotune), timed like the headline (CUDA
+    events around dgm_run_timed after the warm-up steps).  Per precision: DoF-steps/s,
+    the dominant kernel's roofline fraction, the energy drift and the deviation of E
+    from the FP64 run after the same steps in the energy norm (eps-weighted L2)."""
+    from workloads.configs import make_workload
+    steps = max(5, min(args.steps, 20))
+    warm = max(3, args.warmup)
+    out = {}
+    for name in P4_WORKLOADS:
+        w = make_workload(name)
+        dofs = w.nt * dof_per_elem(w.p)
+        rows, fields, S64 = {}, {}, None
+        for prec in P4_PRECISIONS:
+            S = make_solver(w, prec)
+            project_initial(S, w, torch, w.p + 1)
+            if not args.no_autotune:
+                S.autotune(2)
+            ms, st, W = timed_run(S, torch, w.dt, steps, warm)
+            ms = dist_max(ms)
+            tH = st.h_phase_ms / max(st.h_launches, 1)
+            tE = st.e_phase_ms / max(st.e_launches, 1)
+            if prec == "fp64":
+                roof = alu_roofline(w, ms / steps, torch.cuda.current_device())
+                frac = {"bound": "alu", "frac": roof["frac"], "achieved": roof["achieved"], "unit": "TFLOP/s"}
+            else:
+                bH, bE = phase_bytes(w.nt, w.p, 4)
+                kb, kt = (bH, tH) if st.h_phase_ms >= st.e_phase_ms else (bE, tE)
+                peak, _ = measured_peak_hbm()
+                ach = kb / (kt * 1e-3) / 1e9
+                frac = {"bound": "hbm", "frac": ach / peak, "achieved": ach, "unit": "GB/s",
+                        "kernel": "H-phase" if st.h_phase_ms >= st.e_phase_ms else "E-phase"}
+            rows[prec] = {"value": world * dofs * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                          "roofline": frac, "energy_drift": float(np.abs(W - W[0]).max() / W[0])}
+            fields[prec] = S.get_fields()[0]
+            if prec == "fp64":
+                S64 = S
+            else:
+                S.close()
+        zH = np.zeros(S64.nH)
+
+        def enorm(X):
+            S64.set_fields(X, zH)
+            return np.sqrt(2.0 * S64.energy())
+
+        n64 = enorm(fields["fp64"])
+        for prec in P4_PRECISIONS:
+            if prec != "fp64":
+                rows[prec]["e_minus_fp64_energy_norm_rel"] = enorm(fields[prec] - fields["fp64"]) / n64
+                rows[prec]["speedup_vs_fp64"] = rows[prec]["value"] / rows["fp64"]["value"]
+        S64.close()
+        out[name] = {"tets": w.nt, "p": w.p, "dof": dofs, "steps": steps, "warmup": warm,
+                     "l2": l2_note(dofs * 4), **rows}
     return out
 
 

@@ -81,14 +81,29 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
  * orthonormalised coefficients and face traces must stay inside the fp16 range
  * (magnitudes well below 65504, and far above 6e-8 to keep their precision):
  * the equations are linear, so scale the fields into that range.  An overflow
- * shows as DGM_ERR_UNSTABLE from dgm_run when energies are requested. */
-enum dgm_precision { DGM_PREC_FP64 = 0, DGM_PREC_FP32 = 1, DGM_PREC_TC32 = 2, DGM_PREC_TC16 = 3 };
+ * shows as DGM_ERR_UNSTABLE from dgm_run when energies are requested.
+ * By default (variant 0) TC16 runs the resident-table kernels: the operators
+ * are split by field component -- the three reference derivatives of the
+ * curl (Sec. 3.2.2) and one trace matrix per face (Sec. 3.2.3), signed by the
+ * reference face tangents -- and the whole set stays in shared memory, one
+ * CTA per SM.  Variant 1 selects the dense-operator kernels of TC32 with fp16
+ * operands (the operators streamed through a copy ring per tile).
+ * TCBF16: the resident-table kernels with bf16 operands (8-bit mantissa,
+ * fp32's range: no scaling needed; operand rounding 8x coarser than fp16).
+ * Central flux, p <= 6 for every tensor-core precision. */
+enum dgm_precision {
+    DGM_PREC_FP64 = 0,
+    DGM_PREC_FP32 = 1,
+    DGM_PREC_TC32 = 2,
+    DGM_PREC_TC16 = 3,
+    DGM_PREC_TCBF16 = 4
+};
 
 typedef struct dgm_options {
     int flux;           /* dgm_flux */
     double alpha0;      /* alpha = alpha0 * p^2 (Sec. 2.1: alpha grows like p^2) */
     int precision;      /* dgm_precision */
-    int variant;        /* 0 = automatic kernel choice */
+    int variant;        /* 0 = automatic kernel choice; TC16 only: 1 = dense-operator kernels */
     int checks;         /* reserved: accepted, no effect.  Inputs are always validated at
                            creation; an unstable dt shows as DGM_ERR_UNSTABLE from the energy
                            watchdog of dgm_run (energies requested), and dgm_estimate_dt
@@ -227,8 +242,10 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * after one warm-up step) on this problem's own fields with dt = 0, which
  * leaves the fields unchanged; the fastest is kept for all later calls.
  * Candidates: CUDA-core kernels (FP64, FP32) -- 4, 8, 16 or 24 blocks per SM;
- * tensor-core kernels (TC32, TC16) -- 1 or 2 CTAs per SM (2 only where the
- * TMEM columns and shared memory of a CTA allow it).  Every candidate computes
+ * dense-operator tensor-core kernels (TC32, TC16 variant 1) -- 1 or 2 CTAs per
+ * SM (2 only where the TMEM columns and shared memory of a CTA allow it);
+ * resident-table tensor-core kernels (TC16, TCBF16) -- 1 or 2 threads per
+ * element in the update and trace epilogues (one CTA per SM either way).  Every candidate computes
  * each element with the same operations, so the fields of later runs do not
  * depend on the choice; the energy's last bits can (block partial sums).
  * Outputs (nullable): *ncand (<= DGM_AUTOTUNE_MAX), per candidate its

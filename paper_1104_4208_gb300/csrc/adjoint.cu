@@ -6,8 +6,8 @@
 // a negative step (see adjoint_grad in capi.cpp); these kernels add the point
 // sources M_eps^{-1} 2 P^T P E^m, accumulate -e^_T . (G (x) I)(E^m - E^{m-1})_T
 // (= dJ/d eps_T, since d M_eps^{-1} / d eps_T = -M_eps^{-1}|_T / eps_T), and
-// evaluate E at the observation points.  Both state layouts are supported:
-// element-major [t][m][a] and the tensor-core tiles.
+// evaluate E at the observation points.  Every state layout is supported:
+// element-major [t][m][a] and both tensor-core tile layouts.
 
 #include <cuda_runtime.h>
 
@@ -24,7 +24,8 @@ struct Lay {
     int N, K, tiled;
     __device__ __forceinline__ int64_t at(int64_t t, int m, int a) const {
         if (!tiled) return (t * 3 + m) * N + a;
-        const int k = 3 * a + m;
+        // tensor-core tiles, row length K: interleaved (k = 3 a + m) or component-major (k = m K/3 + a)
+        const int k = tiled == 2 ? m * (K / 3) + a : 3 * a + m;
         return (((t >> 7) * (K >> 2) + (k >> 2)) * 128 + (t & 127)) * 4 + (k & 3);
     }
 };

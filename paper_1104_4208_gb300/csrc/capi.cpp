@@ -305,8 +305,12 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         return DGM_ERR_INVALID_ARG;
     }
     if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32 && o.precision != DGM_PREC_TC32 &&
-        o.precision != DGM_PREC_TC16) {
+        o.precision != DGM_PREC_TC16 && o.precision != DGM_PREC_TCBF16) {
         set_error("dgm_problem_create: unknown precision");
+        return DGM_ERR_INVALID_ARG;
+    }
+    if (o.variant != 0 && !(o.variant == 1 && o.precision == DGM_PREC_TC16)) {
+        set_error("dgm_problem_create: variant 1 (dense-operator kernels) exists for TC16 only; else use 0");
         return DGM_ERR_INVALID_ARG;
     }
     const dgm::MeshData& m = mesh->m;
@@ -348,7 +352,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaSetDevice"));
     const size_t rs = P->fp32 ? sizeof(float) : sizeof(double);
     const int64_t nE = m.nt * 3 * P->NE, nH = m.nt * 3 * P->NH;
-    const bool tc = o.precision == DGM_PREC_TC32 || o.precision == DGM_PREC_TC16;
+    const bool tc = o.precision == DGM_PREC_TC32 || o.precision == DGM_PREC_TC16 || o.precision == DGM_PREC_TCBF16;
     cudaError_t e;
     if (!tc) {
         if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc E"));
@@ -871,7 +875,7 @@ int prepare_source(dgm_problem* P, double t0, double dt, int64_t nsteps) {
 // E += -dt f(t_{n+1/2}) M_eps^{-1} (dir . e(x_s)) on the source element
 int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s) {
     if (!P->src_on) return DGM_OK;
-    const int K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? 1 : 0;
+    const int K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? P->tca.d.layout : 0;
     const bool f32 = P->tc || P->fp32;
     const int r = f32 ? dgm::add_point_source<float>((float*)E, P->NE, K, tiled, P->src_elem, P->dSrc + 3, P->dSrc,
                                                      P->dSrcF, n, dt, s)
@@ -994,14 +998,22 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
     }
     const int sms = P->ctx->num_sms;
     std::vector<int> cand;
-    if (P->tc) {
+    const bool resident = P->tc && P->tca.d.layout == 2;
+    if (resident) {
+        // resident-table kernels: one CTA per SM; update/trace threads per element
+        cand.push_back(1);
+        cand.push_back(2);
+    } else if (P->tc) {
         cand.push_back(1);
         if (P->tc_grid_cap > sms) cand.push_back(2);   // two CTAs per SM allowed
     } else {
         for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b);
     }
+    const int keep_upe = P->tca.upe;
     auto apply = [&](int c) {
-        if (P->tc) {
+        if (resident) {
+            P->tca.upe = c;
+        } else if (P->tc) {
             P->tc_grid = std::min(P->tc_grid_cap, sms * c);
             P->tca.partH = P->tca.partE + P->tc_grid;   // the reduction sums 2 tc_grid contiguous partials
         } else {
@@ -1037,6 +1049,7 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
     if (rc) {
         P->grid = keep_grid;
         P->tc_grid = keep_tc;
+        P->tca.upe = keep_upe;
         if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
         return rc;
     }
@@ -1218,7 +1231,7 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
     const StateView v = state_view(P);
     const size_t es = v.f32 ? sizeof(float) : sizeof(double);
     const int64_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
-    const int N = P->NE, K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? 1 : 0;
+    const int N = P->NE, K = P->tc ? P->tca.d.KE : 0, tiled = P->tc ? P->tca.d.layout : 0;
     const size_t sE = v.nE * es, sH = v.nH * es;
     // one allocation: obs data, J, grad, saved state, checkpoints, segment, adjoint state
     const size_t obs_bytes = ((nobs * sizeof(int32_t) + 255) / 256) * 256 + (ophi.size() + oFi.size() + ogi.size()) * 8;

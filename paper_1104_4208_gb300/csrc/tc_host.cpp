@@ -66,8 +66,15 @@ int cuda_err(cudaError_t e, const char* what) {
 
 }  // namespace
 
+namespace {
+int tc2_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
+                     const std::vector<int32_t>& nbr);
+}
+
 int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
                     const std::vector<int32_t>& nbr) {
+    if ((P->opt.precision == DGM_PREC_TC16 && P->opt.variant != 1) || P->opt.precision == DGM_PREC_TCBF16)
+        return tc2_problem_init(P, m, geo, nbr);
     const RefTables& T = P->tab;
     const bool f16 = P->opt.precision == DGM_PREC_TC16;
     const char* name = f16 ? "TC16" : "TC32";
@@ -221,6 +228,178 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     return DGM_OK;
 }
 
+namespace {
+
+int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// Layout 2 (resident-table kernels, 2-byte operands): component-separated
+// tables, component-major state, trace blocks per (face, tangent).
+int tc2_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>& geo,
+                     const std::vector<int32_t>& nbr) {
+    const RefTables& T = P->tab;
+    const bool bf = P->opt.precision == DGM_PREC_TCBF16;
+    const char* name = bf ? "TCBF16" : "TC16";
+    TCDims d{};
+    d.NE = T.NE;
+    d.NH = T.NH;
+    d.N2H = T.N2H;
+    d.layout = 2;
+    d.f16 = 1;
+    d.bf16 = bf ? 1 : 0;
+    d.VPC = 8;
+    d.NEp = pad_to(T.NE, 16);
+    d.NHp = pad_to(T.NH, 16);
+    d.G8 = pad_to(T.N2H, 8);
+    d.G = pad_to(T.N2H, 16);
+    d.KE = d.KEo = 3 * d.NEp;
+    d.KH = d.KHo = 3 * d.NHp;
+    d.FB = 2 * d.G8;
+    d.NT = 8 * d.G8;
+    const TC2Smem LH = tc2_smem(d, true), LE = tc2_smem(d, false);
+    if (P->p > 6 || LH.total > 227 * 1024 || LE.total > 227 * 1024 || 8 * d.G > 512 || 3 * d.NEp > 512) {
+        set_error(std::string("precision ") + name + " supports p <= 6");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    if (P->opt.flux != DGM_FLUX_CENTRAL) {
+        set_error(std::string("precision ") + name + " supports the central flux only");
+        return DGM_ERR_UNSUPPORTED;
+    }
+    TCArgs& A = P->tca;
+    for (int f = 0; f < 4; ++f)
+        for (int i = 0; i < 2; ++i)
+            for (int c = 0; c < 3; ++c) {
+                const double v = T.that[f][i][c];
+                if (v != 0.0 && v != 1.0 && v != -1.0) {
+                    set_error("reference face tangent with an entry other than -1, 0, 1");
+                    return DGM_ERR_UNSUPPORTED;
+                }
+                A.tsgn[f][i][c] = (int8_t)v;
+            }
+    const int64_t ntiles = (m.nt + kTcRows - 1) / kTcRows;
+    const int64_t nrow = ntiles * kTcRows;
+    // one allocation: fp32 state E, H; 2-byte operand copies; trace buffers; tables; float geometry
+    const size_t bE = round_up((size_t)nrow * d.KE * 4, 1024), bH = round_up((size_t)nrow * d.KH * 4, 1024);
+    const size_t bEo = round_up((size_t)nrow * d.KE * 2, 1024), bHo = round_up((size_t)nrow * d.KH * 2, 1024);
+    const size_t bTr = round_up((size_t)nrow * d.NT * 2, 1024);
+    const size_t nTabH = LH.tab / 2, nTabE = LE.tab / 2;   // values
+    const size_t bTab = round_up((nTabH + nTabE) * 2, 1024);
+    const size_t bGeo = (size_t)nrow * 16 * sizeof(float);
+    const size_t o_E = 0, o_H = bE, o_Eo = o_H + bH, o_Ho = o_Eo + bEo, o_trE = o_Ho + bHo, o_trH = o_trE + bTr,
+                 o_tab = o_trH + bTr, o_geo = o_tab + bTab;
+    const size_t total = o_geo + bGeo;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P->dTc, total)) != cudaSuccess) return cuda_err(e, "alloc");
+    if ((e = cudaMemset(P->dTc, 0, o_tab)) != cudaSuccess) return cuda_err(e, "memset");
+    uint8_t* base8 = static_cast<uint8_t*>(P->dTc);
+
+    // tables (fp32 staging, rounded to the operand type on the device)
+    std::vector<float> tab(nTabH + nTabE, 0.0f);
+    const int NE = T.NE, NH = T.NH, N2H = T.N2H, G = d.G;
+    for (int ph = 0; ph < 2; ++ph) {
+        const bool is_h = ph == 0;
+        const TC2Smem& L = is_h ? LH : LE;
+        float* base = tab.data() + (is_h ? 0 : nTabH);
+        const int npin = is_h ? d.NEp : d.NHp, npout = is_h ? d.NHp : d.NEp;
+        const int nout = is_h ? NH : NE;
+        // curl tables d = x, y, z: [npin/8][npout][8], row = output coefficient, k = input coefficient
+        for (int dd = 0; dd < 3; ++dd) {
+            float* tb = base + (size_t)dd * npin * npout;
+            for (int b = 0; b < NH; ++b)
+                for (int a = 0; a < NE; ++a) {
+                    const float v = (float)T.D[dd][(size_t)b * NE + a];
+                    const int row = is_h ? b : a, k = is_h ? a : b;
+                    tb[((size_t)(k / 8) * npout + row) * 8 + (k % 8)] = v;
+                }
+        }
+        // per face: lift [G/8][npout][8] (row = output coefficient, k = face mode) and
+        // trace [npout/8][G][8] (row = face mode, k = coefficient), the same numbers
+        float* lift = base + L.curl / 2;
+        float* trace = base + (L.curl + L.lift) / 2;
+        for (int f = 0; f < 4; ++f)
+            for (int g = 0; g < N2H; ++g)
+                for (int a = 0; a < nout; ++a) {
+                    const double v = is_h ? T.TrH[f][(size_t)g * NH + a] : T.TrE[f][(size_t)T.pos2H[g] * NE + a];
+                    float* lf = lift + (size_t)f * npout * G;
+                    float* tf = trace + (size_t)f * G * npout;
+                    lf[((size_t)(g / 8) * npout + a) * 8 + (g % 8)] = (float)v;
+                    tf[((size_t)(a / 8) * G + g) * 8 + (a % 8)] = (float)v;
+                }
+    }
+    uint8_t* dtab = base8 + o_tab;
+    {
+        float* stage32 = nullptr;
+        if ((e = cudaMalloc(&stage32, tab.size() * sizeof(float))) != cudaSuccess) return cuda_err(e, "alloc tables");
+        e = cudaMemcpy(stage32, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            const int r = bf ? tc_launch_to_bf16(stage32, dtab, tab.size(), 0)
+                             : tc_launch_to_half(stage32, dtab, tab.size(), 0);
+            if (r) e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(stage32);
+        if (e != cudaSuccess) return cuda_err(e, "tables");
+    }
+    // geometry: double records (energy of the state) and the kernels' float records
+    std::vector<double> g2((size_t)nrow * kGeoStride, 0.0);
+    std::copy(geo.begin(), geo.end(), g2.begin());
+    std::vector<float> gf((size_t)nrow * 16, 0.0f);
+    for (int64_t t = 0; t < nrow; ++t) {
+        double* r = &g2[(size_t)t * kGeoStride];
+        if (t >= m.nt) {   // padding elements: identity metric, unit materials, PEC faces, zero fields
+            r[0] = r[3] = r[5] = r[6] = r[9] = r[11] = 1.0;
+            r[kGeoEps] = r[kGeoInvEps] = r[kGeoMu] = r[kGeoInvMu] = r[kGeoSign] = 1.0;
+        }
+        float* o = &gf[(size_t)t * 16];
+        for (int q = 0; q < 12; ++q) o[q] = (float)r[q];
+        o[12] = (float)r[kGeoEps];
+        o[13] = (float)r[kGeoMu];
+        o[14] = (float)r[kGeoSign];
+    }
+    std::vector<int32_t> n2((size_t)nrow * 4, -1);
+    std::copy(nbr.begin(), nbr.end(), n2.begin());
+    if ((e = cudaMalloc(&P->dTcGeo, g2.size() * sizeof(double))) != cudaSuccess) return cuda_err(e, "alloc geo");
+    if ((e = cudaMalloc(&P->dTcNbr, n2.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(e, "alloc nbr");
+    cudaMemcpy(P->dTcGeo, g2.data(), g2.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(P->dTcNbr, n2.data(), n2.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(base8 + o_geo, gf.data(), bGeo, cudaMemcpyHostToDevice);
+    if ((e = cudaMalloc(&P->dErr, sizeof(int))) != cudaSuccess) return cuda_err(e, "alloc err");
+    cudaMemset(P->dErr, 0, sizeof(int));
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->ctx->device);
+    P->tc_grid = (int)std::min<int64_t>(ntiles, (int64_t)sms);   // one CTA per SM
+    P->tc_grid_cap = P->tc_grid;
+    double* part = nullptr;
+    if ((e = cudaMalloc(&part, 2 * (size_t)P->tc_grid_cap * sizeof(double))) != cudaSuccess)
+        return cuda_err(e, "alloc partials");
+    cudaMemset(part, 0, 2 * (size_t)P->tc_grid_cap * sizeof(double));
+
+    A.nt = m.nt;
+    A.ntiles = (int)ntiles;
+    A.d = d;
+    A.E = reinterpret_cast<float*>(base8 + o_E);
+    A.H = reinterpret_cast<float*>(base8 + o_H);
+    A.Eop = base8 + o_Eo;
+    A.Hop = base8 + o_Ho;
+    A.trE = base8 + o_trE;
+    A.trH = base8 + o_trH;
+    A.geo = P->dTcGeo;
+    A.geoF = reinterpret_cast<const float*>(base8 + o_geo);
+    A.nbr = P->dTcNbr;
+    A.T2H = dtab;
+    A.T2E = dtab + nTabH * 2;
+    A.partE = part;
+    A.partH = part + P->tc_grid;
+    A.err = P->dErr;
+    for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
+    A.upe = 2;
+    P->tc = true;
+    P->trE_valid = P->trH_valid = false;
+    return DGM_OK;
+}
+
+}  // namespace
+
 void tc_problem_free(dgm_problem* P) {
     void* ptrs[] = {P->dTc, P->dTcGeo, P->dTcNbr, P->dErr, P->tca.partE};
     for (void* q : ptrs)
@@ -231,8 +410,13 @@ int tc_import(dgm_problem* P, const double* dE, const double* dH, const double* 
               cudaStream_t s) {
     const TCArgs& A = P->tca;
     int r = 0;
-    if (dE) r |= tc_launch_pack(dE, A.E, nrmE, A.nt, A.d.NE, A.d.KE, s);
-    if (dH) r |= tc_launch_pack(dH, A.H, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    if (A.d.layout == 2) {
+        if (dE) r |= tc2_launch_pack(dE, A.E, nrmE, A.nt, A.d.NE, A.d.NEp, s);
+        if (dH) r |= tc2_launch_pack(dH, A.H, nrmH, A.nt, A.d.NH, A.d.NHp, s);
+    } else {
+        if (dE) r |= tc_launch_pack(dE, A.E, nrmE, A.nt, A.d.NE, A.d.KE, s);
+        if (dH) r |= tc_launch_pack(dH, A.H, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    }
     if (dE) P->trE_valid = false;
     if (dH) P->trH_valid = false;
     return r ? cuda_err(cudaGetLastError(), "pack") : DGM_OK;
@@ -241,8 +425,13 @@ int tc_import(dgm_problem* P, const double* dE, const double* dH, const double* 
 int tc_export(dgm_problem* P, double* dE, double* dH, const double* nrmE, const double* nrmH, cudaStream_t s) {
     const TCArgs& A = P->tca;
     int r = 0;
-    if (dE) r |= tc_launch_unpack(A.E, dE, nrmE, A.nt, A.d.NE, A.d.KE, s);
-    if (dH) r |= tc_launch_unpack(A.H, dH, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    if (A.d.layout == 2) {
+        if (dE) r |= tc2_launch_unpack(A.E, dE, nrmE, A.nt, A.d.NE, A.d.NEp, s);
+        if (dH) r |= tc2_launch_unpack(A.H, dH, nrmH, A.nt, A.d.NH, A.d.NHp, s);
+    } else {
+        if (dE) r |= tc_launch_unpack(A.E, dE, nrmE, A.nt, A.d.NE, A.d.KE, s);
+        if (dH) r |= tc_launch_unpack(A.H, dH, nrmH, A.nt, A.d.NH, A.d.KH, s);
+    }
     return r ? cuda_err(cudaGetLastError(), "unpack") : DGM_OK;
 }
 

@@ -677,7 +677,10 @@ TCDims tc_dims(int NE, int NH, int N2H, bool f16) {
     d.NE = NE;
     d.NH = NH;
     d.N2H = N2H;
+    d.layout = 1;
     d.f16 = f16 ? 1 : 0;
+    d.bf16 = 0;
+    d.NEp = d.NHp = d.G8 = d.G = 0;
     d.VPC = f16 ? 8 : 4;
     d.KE = padto(3 * NE, 24);
     d.KH = padto(3 * NH, 24);
@@ -742,21 +745,25 @@ int launch_traces(const TCArgs& a, int grid, int which, int tile0, int tile1, in
 }  // namespace
 
 int tc_launch_phase_H(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int energy, cudaStream_t s) {
+    if (a.d.layout == 2) return tc2_launch_phase(a, true, grid, dt, a_lo, c_out, energy, s);
     return a.d.f16 ? launch_phase<true, OpF16>(a, grid, dt, a_lo, c_out, energy, s)
                    : launch_phase<true, OpTf32>(a, grid, dt, a_lo, c_out, energy, s);
 }
 
 int tc_launch_phase_E(const TCArgs& a, int grid, double dt, int energy, cudaStream_t s) {
+    if (a.d.layout == 2) return tc2_launch_phase(a, false, grid, dt, 0.0, 1.0, energy, s);
     return a.d.f16 ? launch_phase<false, OpF16>(a, grid, dt, 0.0, 1.0, energy, s)
                    : launch_phase<false, OpTf32>(a, grid, dt, 0.0, 1.0, energy, s);
 }
 
 int tc_launch_traces(const TCArgs& a, int grid, int which, cudaStream_t s) {
+    if (a.d.layout == 2) return tc2_launch_traces(a, which, grid, 0, a.ntiles, which == 0, s);
     return a.d.f16 ? launch_traces<OpF16>(a, grid, which, 0, a.ntiles, which == 0, s)
                    : launch_traces<OpTf32>(a, grid, which, 0, a.ntiles, which == 0, s);
 }
 
 int tc_launch_traces_tile(const TCArgs& a, int which, int tile, cudaStream_t s) {
+    if (a.d.layout == 2) return tc2_launch_traces(a, which, 1, tile, tile + 1, 0, s);
     return a.d.f16 ? launch_traces<OpF16>(a, 1, which, tile, tile + 1, 0, s)
                    : launch_traces<OpTf32>(a, 1, which, tile, tile + 1, 0, s);
 }
@@ -769,6 +776,7 @@ int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s) {
 }
 
 int tc_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s) {
+    if (a.d.layout == 2) return tc2_launch_state_energy(a, grid, s);
     k_tc_state_energy<<<grid, 128, 0, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

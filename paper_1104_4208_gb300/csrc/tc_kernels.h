@@ -15,7 +15,12 @@ constexpr int kTcRows = 128;   // elements per tile = MMA M
 // fp16 (8 per chunk).
 struct TCDims {
     int NE, NH, N2H;
-    int f16;         // operands in fp16 (else TF32)
+    int layout;      // 1: interleaved element rows (k = 3 a + m; TC32 kernels)
+                     // 2: component-major element rows (k = m Np + a; the resident-table kernels)
+    int f16;         // operands are 2-byte (fp16, or bf16 when bf16 = 1); else TF32
+    int bf16;        // 2-byte operands are bf16 (8-bit mantissa, fp32 range)
+    int NEp, NHp;    // layout 2: per-component padded lengths (multiples of 16)
+    int G8, G;       // layout 2: face modes per tangent block, padded to 8 (trace buffer) and 16 (MMA)
     int VPC;         // operand values per 16-byte chunk: 4 (TF32) or 8 (fp16)
     int KE, KH;      // padded fp32 state row lengths (multiples of 24): E, H
     int KEo, KHo;    // padded operand row lengths (whole MMA K-steps of 2 VPC): E, H
@@ -55,7 +60,34 @@ struct TCArgs {
     uint32_t r2_offset;        // offset of the resident tile region
     int stall_test;            // nonzero: the phase kernel waits on a barrier nothing arrives at,
                                // gives up after a short limit, records a timeout and does no work
+    // layout 2 (resident-table kernels)
+    const float* geoF;         // [ntiles*128][16] floats: G^{-1} (6), G (6), eps, mu, sign det F, 0
+    const void* T2H;           // H-phase tables: curl D_d (3), lift (4 faces), trace (4 faces)
+    const void* T2E;           // E-phase tables: curl^T, lift, trace
+    int8_t tsgn[4][2][3];      // reference face tangents t_{f,i} (entries -1, 0, 1)
+    int upe;                   // update/trace threads per element (1 or 2)
 };
+
+// Byte sizes and shared-memory offsets of one layout-2 kernel instance.
+struct TC2Smem {
+    uint32_t curl, lift, trace;   // table bytes (curl: 3 tables; lift, trace: 4 faces each)
+    uint32_t tab;                 // all tables of the phase
+    uint32_t o_tab, o_sa, o_sf;   // offsets
+    uint32_t sa, sf;              // operand tile region (input, then updated field), flux blocks
+    uint32_t total;               // dynamic shared memory of the kernel
+};
+__host__ __device__ TC2Smem tc2_smem(const TCDims& d, bool is_h);
+// TMEM columns of the accumulator (3 Np_out) and the first trace column of a phase
+uint32_t tc2_tr0(const TCDims& d, bool is_h);
+int tc2_launch_phase(const TCArgs& a, bool is_h, int grid, double dt, double a_lo, double c_out, int energy,
+                     cudaStream_t s);
+// refresh the 2-byte operand copy of a field from its fp32 state, then its traces;
+// with energy (which = 0) also the energy partials of E; tiles [tile0, tile1)
+int tc2_launch_traces(const TCArgs& a, int which, int grid, int tile0, int tile1, int energy, cudaStream_t s);
+int tc2_launch_state_energy(const TCArgs& a, int grid, cudaStream_t s);
+int tc2_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt, int N, int Np, cudaStream_t s);
+int tc2_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int Np, cudaStream_t s);
+int tc_launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset);
 uint32_t tc_tmem_cols(const TCDims& d);
