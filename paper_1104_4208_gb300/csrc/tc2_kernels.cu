@@ -59,8 +59,10 @@ __host__ __device__ TC2Smem tc2_smem(const TCDims& d, bool is_h) {
     L.lift = 4u * npout * (uint32_t)d.G * 2u;
     L.trace = 4u * (uint32_t)d.G * npout * 2u;
     L.tab = L.curl + L.lift + L.trace;
-    L.sa = 3u * (npin > npout ? npin : npout) * 128u * 2u;
-    L.sf = 8u * (uint32_t)d.G * 128u * 2u;
+    L.sa = 3u * npin * 128u * 2u;
+    // flux blocks of the lift, then (after the lift) the updated field's operand tile
+    const uint32_t flux = 8u * (uint32_t)d.G * 128u * 2u, upd = 3u * npout * 128u * 2u;
+    L.sf = flux > upd ? flux : upd;
     L.o_tab = 1024u;   // control block first
     L.o_sa = (L.o_tab + L.tab + 1023u) / 1024u * 1024u;
     L.o_sf = (L.o_sa + L.sa + 1023u) / 1024u * 1024u;
@@ -142,6 +144,10 @@ __device__ bool wait2(Ctl2* c, uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
@@ -299,15 +305,26 @@ __global__ void __launch_bounds__(512, 1)
                     issued = 1;
                 }
             }
-            if (MODE == 0) {
-                for (int it = 0; it + 1 < ntile; ++it) {
-                    // the region is free once the trace MMAs of tile it completed
-                    if (!wait2(ctl, &ctl->tr_full, (uint32_t)it & 1u)) break;
-                    tc::mbar_expect_tx(&ctl->sa_full, in_tile_bytes);
-                    tc::bulk_g2s(s_sa, op_in + (size_t)(first + (it + 1) * stride) * in_tile_bytes, in_tile_bytes,
-                                 &ctl->sa_full);
-                    issued = it + 2;
-                }
+            // the epilogues' tile data, one tile ahead, into L2: the fp32 state of the
+            // updated field, the tile's own trace rows, the float geometry
+            auto prefetch_tile = [&](int tile) {
+                if (tile >= tile1) return;
+                prefetch_l2(st_out + (size_t)tile * (3 * q.Npout) * 128, (uint32_t)(3 * q.Npout) * 128u * 4u);
+                if (MODE == 0) prefetch_l2(tr_in + (size_t)tile * 128 * q.NT * 2, 128u * (uint32_t)q.NT * 2u);
+                prefetch_l2(A.geoF + (size_t)tile * 128 * 16, 128u * 64u);
+            };
+            if (!ctl->abort) {
+                prefetch_tile(first);
+                prefetch_tile(first + stride);
+            }
+            for (int it = 0; MODE == 0 && it + 1 < ntile; ++it) {
+                // the input region is free once the curl and lift MMAs of tile it completed
+                if (!wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u)) break;
+                tc::mbar_expect_tx(&ctl->sa_full, in_tile_bytes);
+                tc::bulk_g2s(s_sa, op_in + (size_t)(first + (it + 1) * stride) * in_tile_bytes, in_tile_bytes,
+                             &ctl->sa_full);
+                issued = it + 2;
+                prefetch_tile(first + (it + 2) * stride);
             }
             // nothing of ours may still be landing when shared memory is given up
             if (tab_issued) tc::mbar_wait(&ctl->tab_full, 0u, kDrain2);
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(512, 1)
                 // traces of the updated field: block (f, i) = sum_m t_{f,i,m} Tr_f X_m
                 const int ksout = q.Npout / 16;
                 for (int m = 0; m < 3; ++m) {
-                    const uint32_t abase = a_sa + (uint32_t)(m * q.Npout / 8) * kChunk;
+                    const uint32_t abase = a_sf + (uint32_t)(m * q.Npout / 8) * kChunk;
                     for (int f = 0; f < 4; ++f)
                         for (int i = 0; i < 2; ++i) {
                             const int c = A.tsgn[f][i][m];
@@ -402,77 +419,93 @@ __global__ void __launch_bounds__(512, 1)
             bool ok = true;
             float eloc = 0.f;
             if (MODE == 0) {
-                ok = wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u);
-                tc::tc_fence_after();
                 const float sT = IS_H ? -g3.z : g3.z;   // r = -s_T D (H-phase), s_T D (E-phase)
                 const float sc = (float)(dt / mat);
                 const float co = (float)c_out, alo = (float)a_lo;
-                for (int b = sub; b < nbat && ok; b += upe) {
+                const int nvb = (q.Nout + 7) / 8;        // batches holding coefficients
+                // the fp32 state of this thread's batches, one batch ahead of the arithmetic;
+                // the first one before the wait for the accumulator
+                float4 cur[6], nxt[6];
+                auto load_batch = [&](int b, float4* v) {
+                    const float4* s4 = reinterpret_cast<const float4*>(st) + ((size_t)(2 * b) * 128 + e);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        v[2 * m] = s4[(size_t)(m * q.Npout / 4) * 128];
+                        v[2 * m + 1] = s4[(size_t)(m * q.Npout / 4 + 1) * 128];
+                    }
+                };
+                if (sub < nvb) load_batch(sub, cur);
+                ok = wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u);
+                tc::tc_fence_after();
+                for (int b = sub; b < nvb && ok; b += upe) {
+                    if (b + upe < nvb) load_batch(b + upe, nxt);
                     float x[24], dd[24];
-                    const bool valid = 8 * b < q.Nout;
-                    if (valid) {
 #pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            const float4* s4 = reinterpret_cast<const float4*>(st) +
-                                               ((size_t)(m * q.Npout / 4 + 2 * b) * 128 + e);
-                            const float4 v0 = s4[0], v1 = s4[128];
-                            x[8 * m + 0] = v0.x; x[8 * m + 1] = v0.y; x[8 * m + 2] = v0.z; x[8 * m + 3] = v0.w;
-                            x[8 * m + 4] = v1.x; x[8 * m + 5] = v1.y; x[8 * m + 6] = v1.z; x[8 * m + 7] = v1.w;
-                        }
-                        tmem_ld3x8(lane_t + q.acc0 + (uint32_t)(8 * b), lane_t + q.acc0 + (uint32_t)(q.Npout + 8 * b),
-                                   lane_t + q.acc0 + (uint32_t)(2 * q.Npout + 8 * b), dd);
+                    for (int m = 0; m < 3; ++m) {
+                        const float4 v0 = cur[2 * m], v1 = cur[2 * m + 1];
+                        x[8 * m + 0] = v0.x; x[8 * m + 1] = v0.y; x[8 * m + 2] = v0.z; x[8 * m + 3] = v0.w;
+                        x[8 * m + 4] = v1.x; x[8 * m + 5] = v1.y; x[8 * m + 6] = v1.z; x[8 * m + 7] = v1.w;
+                    }
+                    tmem_ld3x8(lane_t + q.acc0 + (uint32_t)(8 * b), lane_t + q.acc0 + (uint32_t)(q.Npout + 8 * b),
+                               lane_t + q.acc0 + (uint32_t)(2 * q.Npout + 8 * b), dd);
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            if (8 * b + c >= q.Nout) break;
-                            const float r0 = sT * dd[c], r1 = sT * dd[8 + c], r2 = sT * dd[16 + c];
-                            const float d0 = sc * (Gi[0] * r0 + Gi[1] * r1 + Gi[2] * r2);
-                            const float d1 = sc * (Gi[1] * r0 + Gi[3] * r1 + Gi[4] * r2);
-                            const float d2 = sc * (Gi[2] * r0 + Gi[4] * r1 + Gi[5] * r2);
-                            float& h0 = x[c];
-                            float& h1 = x[8 + c];
-                            float& h2 = x[16 + c];
-                            if (IS_H) {
-                                if (energy) {   // staggered pair (H_lo, H_hi) of the modified energy
-                                    const float l0 = h0 - alo * d0, l1 = h1 - alo * d1, l2 = h2 - alo * d2;
-                                    const float u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
-                                    eloc += l0 * (Gm[0] * u0 + Gm[1] * u1 + Gm[2] * u2) +
-                                            l1 * (Gm[1] * u0 + Gm[3] * u1 + Gm[4] * u2) +
-                                            l2 * (Gm[2] * u0 + Gm[4] * u1 + Gm[5] * u2);
-                                }
-                                h0 += co * d0;
-                                h1 += co * d1;
-                                h2 += co * d2;
-                            } else {
-                                h0 += d0;
-                                h1 += d1;
-                                h2 += d2;
-                                if (energy)
-                                    eloc += h0 * (Gm[0] * h0 + Gm[1] * h1 + Gm[2] * h2) +
-                                            h1 * (Gm[1] * h0 + Gm[3] * h1 + Gm[4] * h2) +
-                                            h2 * (Gm[2] * h0 + Gm[4] * h1 + Gm[5] * h2);
+                    for (int c = 0; c < 8; ++c) {
+                        if (8 * b + c >= q.Nout) break;
+                        const float r0 = sT * dd[c], r1 = sT * dd[8 + c], r2 = sT * dd[16 + c];
+                        const float d0 = sc * (Gi[0] * r0 + Gi[1] * r1 + Gi[2] * r2);
+                        const float d1 = sc * (Gi[1] * r0 + Gi[3] * r1 + Gi[4] * r2);
+                        const float d2 = sc * (Gi[2] * r0 + Gi[4] * r1 + Gi[5] * r2);
+                        float& h0 = x[c];
+                        float& h1 = x[8 + c];
+                        float& h2 = x[16 + c];
+                        if (IS_H) {
+                            if (energy) {   // staggered pair (H_lo, H_hi) of the modified energy
+                                const float l0 = h0 - alo * d0, l1 = h1 - alo * d1, l2 = h2 - alo * d2;
+                                const float u0 = l0 + d0, u1 = l1 + d1, u2 = l2 + d2;
+                                eloc += l0 * (Gm[0] * u0 + Gm[1] * u1 + Gm[2] * u2) +
+                                        l1 * (Gm[1] * u0 + Gm[3] * u1 + Gm[4] * u2) +
+                                        l2 * (Gm[2] * u0 + Gm[4] * u1 + Gm[5] * u2);
                             }
+                            h0 += co * d0;
+                            h1 += co * d1;
+                            h2 += co * d2;
+                        } else {
+                            h0 += d0;
+                            h1 += d1;
+                            h2 += d2;
+                            if (energy)
+                                eloc += h0 * (Gm[0] * h0 + Gm[1] * h1 + Gm[2] * h2) +
+                                        h1 * (Gm[1] * h0 + Gm[3] * h1 + Gm[4] * h2) +
+                                        h2 * (Gm[2] * h0 + Gm[4] * h1 + Gm[5] * h2);
                         }
+                    }
+                    float4* s4 = reinterpret_cast<float4*>(st) + ((size_t)(2 * b) * 128 + e);
 #pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            float4* s4 = reinterpret_cast<float4*>(st) + ((size_t)(m * q.Npout / 4 + 2 * b) * 128 + e);
-                            s4[0] = make_float4(x[8 * m + 0], x[8 * m + 1], x[8 * m + 2], x[8 * m + 3]);
-                            s4[128] = make_float4(x[8 * m + 4], x[8 * m + 5], x[8 * m + 6], x[8 * m + 7]);
-                        }
+                    for (int m = 0; m < 3; ++m) {
+                        s4[(size_t)(m * q.Npout / 4) * 128] = make_float4(x[8 * m + 0], x[8 * m + 1], x[8 * m + 2], x[8 * m + 3]);
+                        s4[(size_t)(m * q.Npout / 4 + 1) * 128] =
+                            make_float4(x[8 * m + 4], x[8 * m + 5], x[8 * m + 6], x[8 * m + 7]);
                     }
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {
-                        uint4 o = make_uint4(0u, 0u, 0u, 0u);
-                        if (valid) {
-                            float v[8];
+                        float v[8];
 #pragma unroll
-                            for (int c = 0; c < 8; ++c) v[c] = 8 * b + c < q.Nout ? x[8 * m + c] : 0.f;
-                            o = make_uint4(OP::pack(v[0], v[1]), OP::pack(v[2], v[3]), OP::pack(v[4], v[5]),
-                                           OP::pack(v[6], v[7]));
-                            *reinterpret_cast<uint4*>(opg + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
-                        }
-                        *reinterpret_cast<uint4*>(s_sa + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
+                        for (int c = 0; c < 8; ++c) v[c] = 8 * b + c < q.Nout ? x[8 * m + c] : 0.f;
+                        const uint4 o = make_uint4(OP::pack(v[0], v[1]), OP::pack(v[2], v[3]), OP::pack(v[4], v[5]),
+                                                   OP::pack(v[6], v[7]));
+                        const size_t off = ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16;
+                        *reinterpret_cast<uint4*>(opg + off) = o;
+                        *reinterpret_cast<uint4*>(s_sf + off) = o;
                     }
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) cur[k] = nxt[k];
                 }
+                // batches of padding only: zero operand chunks for the trace GEMM
+                for (int b = nvb + ((sub - nvb) % upe + upe) % upe; b < nbat && ok; b += upe)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        *reinterpret_cast<uint4*>(s_sf + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) =
+                            make_uint4(0u, 0u, 0u, 0u);
                 eacc += 0.5 * mat * (double)eloc;
             } else {
                 // traces only: the operand copy of the field from its fp32 state
@@ -510,7 +543,7 @@ __global__ void __launch_bounds__(512, 1)
                                                    OP::pack(x[8 * m + 4], x[8 * m + 5]),
                                                    OP::pack(x[8 * m + 6], x[8 * m + 7]));
                         *reinterpret_cast<uint4*>(opg + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
-                        *reinterpret_cast<uint4*>(s_sa + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
+                        *reinterpret_cast<uint4*>(s_sf + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
                     }
                 }
                 eacc += 0.5 * mat * (double)eloc;
@@ -551,68 +584,78 @@ __global__ void __launch_bounds__(512, 1)
         }
     } else if (MODE == 0 && tid >= wg2_first && tid < wg2_first + 128) {
         // ------------------------------------------------------------ WG2: flux
+        // The flux region also carries the previous tile's updated operand tile
+        // until its trace MMAs complete; the first two faces' trace loads are
+        // issued before that wait, the last two after it.
         const int e = tid - wg2_first;
         const int nG8 = q.G8 / 8, nG = q.G / 8;
-        // the padding chunks of each flux block stay zero
-        for (int blk = 0; blk < 8; ++blk)
-            for (int c = nG8; c < nG; ++c)
-                *reinterpret_cast<uint4*>(s_sf + ((size_t)(blk * nG + c) * 128 + e) * 16) = make_uint4(0u, 0u, 0u, 0u);
+        uint4 ov[2][6], nv[2][6];
+        int4 nb4 = make_int4(-1, -1, -1, -1);
+        auto load_pair = [&](int64_t t, int fp) {
+#pragma unroll
+            for (int ff = 0; ff < 2; ++ff) {
+                const int f = 2 * fp + ff;
+                const int32_t nb = fp == 0 ? (ff == 0 ? nb4.x : nb4.y) : (ff == 0 ? nb4.z : nb4.w);
+                const uint4* own = reinterpret_cast<const uint4*>(tr_in + ((size_t)t * q.NT + f * 2 * q.G8) * 2);
+                const uint4* src =
+                    nb >= 0 ? reinterpret_cast<const uint4*>(tr_in + ((size_t)(nb >> 2) * q.NT + (nb & 3) * 2 * q.G8) * 2)
+                            : own;
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    if (c < 2 * nG8) {
+                        ov[ff][c] = own[c];
+                        nv[ff][c] = src[c];
+                    }
+            }
+        };
+        auto write_pair = [&](int fp) {
+#pragma unroll
+            for (int ff = 0; ff < 2; ++ff) {
+                const int f = 2 * fp + ff;
+                const bool pec = (fp == 0 ? (ff == 0 ? nb4.x : nb4.y) : (ff == 0 ? nb4.z : nb4.w)) < 0;
+                const float sh = (float)A.sigma_hat[f];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    if (c >= 2 * nG8) break;
+                    const uint32_t ow[4] = {ov[ff][c].x, ov[ff][c].y, ov[ff][c].z, ov[ff][c].w};
+                    const uint32_t nw[4] = {nv[ff][c].x, nv[ff][c].y, nv[ff][c].z, nv[ff][c].w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 v = OP::unpack(ow[k]), n = OP::unpack(nw[k]);
+                        float a, b2;
+                        if (IS_H) {   // jump: -sigma (v - n)/2, PEC ghost -sigma v
+                            a = pec ? -sh * v.x : -sh * 0.5f * (v.x - n.x);
+                            b2 = pec ? -sh * v.y : -sh * 0.5f * (v.y - n.y);
+                        } else {      // average: sigma (v + n)/2, PEC sigma v
+                            a = pec ? sh * v.x : sh * 0.5f * (v.x + n.x);
+                            b2 = pec ? sh * v.y : sh * 0.5f * (v.y + n.y);
+                        }
+                        o[k] = OP::pack(a, b2);
+                    }
+                    // chunk c of the face block = tangent i = c / nG8, chunk c % nG8
+                    const int i = c / nG8, cc = c - i * nG8;
+                    *reinterpret_cast<uint4*>(s_sf + ((size_t)((2 * f + i) * nG + cc) * 128 + e) * 16) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
+                // the block's padding chunks (the region held other data in between)
+                for (int i = 0; i < 2; ++i)
+                    for (int c = nG8; c < nG; ++c)
+                        *reinterpret_cast<uint4*>(s_sf + ((size_t)((2 * f + i) * nG + c) * 128 + e) * 16) =
+                            make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
         for (int it = 0; it < ntile; ++it) {
             const int tile = first + it * stride;
             const int64_t t = (int64_t)tile * 128 + e;
-            bool ok = true;
-            if (it > 0) ok = wait2(ctl, &ctl->m1_done, (uint32_t)(it - 1) & 1u);   // the flux blocks are free
+            nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
+            load_pair(t, 0);
+            // the region is free once the trace MMAs of the previous tile completed
+            const bool ok = it == 0 || wait2(ctl, &ctl->tr_full, (uint32_t)(it - 1) & 1u);
             if (ok) {
-                const int4 nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
-#pragma unroll 1
-                for (int fp = 0; fp < 2; ++fp) {
-                    uint4 ov[2][6], nv[2][6];
-#pragma unroll
-                    for (int ff = 0; ff < 2; ++ff) {
-                        const int f = 2 * fp + ff;
-                        const int32_t nb = fp == 0 ? (ff == 0 ? nb4.x : nb4.y) : (ff == 0 ? nb4.z : nb4.w);
-                        const uint4* own = reinterpret_cast<const uint4*>(tr_in + ((size_t)t * q.NT + f * 2 * q.G8) * 2);
-                        const uint4* src = nb >= 0 ? reinterpret_cast<const uint4*>(
-                                                         tr_in + ((size_t)(nb >> 2) * q.NT + (nb & 3) * 2 * q.G8) * 2)
-                                                   : own;
-#pragma unroll
-                        for (int c = 0; c < 6; ++c)
-                            if (c < 2 * nG8) {
-                                ov[ff][c] = own[c];
-                                nv[ff][c] = src[c];
-                            }
-                    }
-#pragma unroll
-                    for (int ff = 0; ff < 2; ++ff) {
-                        const int f = 2 * fp + ff;
-                        const bool pec = (fp == 0 ? (ff == 0 ? nb4.x : nb4.y) : (ff == 0 ? nb4.z : nb4.w)) < 0;
-                        const float sh = (float)A.sigma_hat[f];
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) {
-                            if (c >= 2 * nG8) break;
-                            const uint32_t ow[4] = {ov[ff][c].x, ov[ff][c].y, ov[ff][c].z, ov[ff][c].w};
-                            const uint32_t nw[4] = {nv[ff][c].x, nv[ff][c].y, nv[ff][c].z, nv[ff][c].w};
-                            uint32_t o[4];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float2 v = OP::unpack(ow[k]), n = OP::unpack(nw[k]);
-                                float a, b2;
-                                if (IS_H) {   // jump: -sigma (v - n)/2, PEC ghost -sigma v
-                                    a = pec ? -sh * v.x : -sh * 0.5f * (v.x - n.x);
-                                    b2 = pec ? -sh * v.y : -sh * 0.5f * (v.y - n.y);
-                                } else {      // average: sigma (v + n)/2, PEC sigma v
-                                    a = pec ? sh * v.x : sh * 0.5f * (v.x + n.x);
-                                    b2 = pec ? sh * v.y : sh * 0.5f * (v.y + n.y);
-                                }
-                                o[k] = OP::pack(a, b2);
-                            }
-                            // chunk c of the face block = tangent i = c / nG8, chunk c % nG8
-                            const int i = c / nG8, cc = c - i * nG8;
-                            *reinterpret_cast<uint4*>(s_sf + ((size_t)((2 * f + i) * nG + cc) * 128 + e) * 16) =
-                                make_uint4(o[0], o[1], o[2], o[3]);
-                        }
-                    }
-                }
+                write_pair(0);
+                load_pair(t, 1);
+                write_pair(1);
             }
             tc::fence_proxy_async();
             named_bar(2, 128);
