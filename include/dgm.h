@@ -244,8 +244,8 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * Candidates: CUDA-core kernels (FP64, FP32) -- 4, 8, 16 or 24 blocks per SM;
  * dense-operator tensor-core kernels (TC32, TC16 variant 1) -- 1 or 2 CTAs per
  * SM (2 only where the TMEM columns and shared memory of a CTA allow it);
- * resident-table tensor-core kernels (TC16, TCBF16) -- 1 or 2 threads per
- * element in the update and trace epilogues (one CTA per SM either way).  Every candidate computes
+ * resident-table tensor-core kernels (TC16, TCBF16) -- one configuration
+ * (one CTA per SM), timed and reported like the others.  Every candidate computes
  * each element with the same operations, so the fields of later runs do not
  * depend on the choice; the energy's last bits can (block partial sums).
  * Outputs (nullable): *ncand (<= DGM_AUTOTUNE_MAX), per candidate its

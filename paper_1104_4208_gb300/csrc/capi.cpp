@@ -1000,19 +1000,16 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
     std::vector<int> cand;
     const bool resident = P->tc && P->tca.d.layout == 2;
     if (resident) {
-        // resident-table kernels: one CTA per SM; update/trace threads per element
-        cand.push_back(1);
-        cand.push_back(2);
+        cand.push_back(1);   // resident-table kernels: one CTA per SM, nothing to choose
     } else if (P->tc) {
         cand.push_back(1);
         if (P->tc_grid_cap > sms) cand.push_back(2);   // two CTAs per SM allowed
     } else {
         for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b);
     }
-    const int keep_upe = P->tca.upe;
     auto apply = [&](int c) {
         if (resident) {
-            P->tca.upe = c;
+            (void)c;
         } else if (P->tc) {
             P->tc_grid = std::min(P->tc_grid_cap, sms * c);
             P->tca.partH = P->tca.partE + P->tc_grid;   // the reduction sums 2 tc_grid contiguous partials
@@ -1049,7 +1046,6 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
     if (rc) {
         P->grid = keep_grid;
         P->tc_grid = keep_tc;
-        P->tca.upe = keep_upe;
         if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
         return rc;
     }

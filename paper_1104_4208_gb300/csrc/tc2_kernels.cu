@@ -59,11 +59,10 @@ __host__ __device__ TC2Smem tc2_smem(const TCDims& d, bool is_h) {
     L.lift = 4u * npout * (uint32_t)d.G * 2u;
     L.trace = 4u * (uint32_t)d.G * npout * 2u;
     L.tab = L.curl + L.lift + L.trace;
-    L.sa = 3u * npin * 128u * 2u;
-    // flux blocks of the lift, then (after the lift) the updated field's operand tile
-    const uint32_t flux = 8u * (uint32_t)d.G * 128u * 2u, upd = 3u * npout * 128u * 2u;
-    L.sf = flux > upd ? flux : upd;
-    L.o_tab = 1024u;   // control block first
+    // the input field's operand tile, then (after the curl and lift) the updated field's
+    L.sa = 3u * (npin > npout ? npin : npout) * 128u * 2u;
+    L.sf = 8u * (uint32_t)d.G * 128u * 2u;
+    L.o_tab = 1024u + 4096u;   // control block, then the MMA programs (128 entries of 32 bytes)
     L.o_sa = (L.o_tab + L.tab + 1023u) / 1024u * 1024u;
     L.o_sf = (L.o_sa + L.sa + 1023u) / 1024u * 1024u;
     // at least 116 KB: a second CTA on the same SM would find no tensor memory left
@@ -146,10 +145,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // kind::f16 instruction descriptor: D fp32, A = B = fp16 or bf16, K-major, M = 128, B optionally negated
@@ -158,13 +153,21 @@ __device__ __forceinline__ uint32_t idesc2(uint32_t fmt, int n, bool neg_b) {
            ((uint32_t)(128 >> 4) << 24);
 }
 
-// D[tmem] (+)= A * B^T for one 16-wide K step: A = 128 rows in chunk layout
-// (LBO = one chunk column, SBO = 8 rows), B = `rows` rows in [K/8][rows][8]
-__device__ __forceinline__ void mma2(uint32_t fmt, uint32_t d, uint32_t a, uint32_t b, uint32_t rows, int n, bool neg,
-                                     bool acc) {
-    const uint64_t ad = tc::sdesc(a, kChunk, 128u);
-    const uint64_t bd = tc::sdesc(b, rows * 16u, 128u);
-    tc::mma_f16(d, ad, bd, idesc2(fmt, n, neg), acc ? 1u : 0u);
+// one MMA of a precomputed program: TMEM column, instruction descriptor,
+// accumulate flag, shared-memory descriptors of A and B
+struct MmaOp {
+    uint32_t d, idesc, acc, pad;
+    uint64_t a, b;
+};
+constexpr int kProgMax = 4096 / (int)sizeof(MmaOp);
+
+__device__ __forceinline__ void issue_op(const MmaOp& o, uint32_t tmem) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + o.d),
+        "l"(o.a), "l"(o.b), "r"(o.idesc), "r"(o.acc)
+        : "memory");
 }
 
 // three 8-column TMEM loads of this thread's lane, one wait
@@ -234,7 +237,7 @@ __device__ Dims2 dims2(const TCArgs& A, uint32_t tr0) {
 // MODE 0: phase (IS_H: H-phase, else E-phase); MODE 1: traces of the field
 // (IS_H: H, else E) from its fp32 state, refreshing its operand copy.
 template <bool IS_H, int MODE, bool BF>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(384, 1)
     k_tc2(TCArgs A, double dt, double a_lo, double c_out, int energy, uint32_t tr0, int tile0, int tile1) {
     using OP = Op2<BF>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -242,9 +245,6 @@ __global__ void __launch_bounds__(512, 1)
     const TC2Smem L = tc2_smem(A.d, IS_H);
     const Dims2 q = dims2<IS_H>(A, tr0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int upe = A.upe;
-    const int nU = 128 * upe;                  // WG1 threads
-    const int wg2_first = 128 + nU;            // WG2 threads start here
     uint8_t* s_tab = smem + L.o_tab;
     uint8_t* s_sa = smem + L.o_sa;
     uint8_t* s_sf = smem + L.o_sf;
@@ -305,26 +305,13 @@ __global__ void __launch_bounds__(512, 1)
                     issued = 1;
                 }
             }
-            // the epilogues' tile data, one tile ahead, into L2: the fp32 state of the
-            // updated field, the tile's own trace rows, the float geometry
-            auto prefetch_tile = [&](int tile) {
-                if (tile >= tile1) return;
-                prefetch_l2(st_out + (size_t)tile * (3 * q.Npout) * 128, (uint32_t)(3 * q.Npout) * 128u * 4u);
-                if (MODE == 0) prefetch_l2(tr_in + (size_t)tile * 128 * q.NT * 2, 128u * (uint32_t)q.NT * 2u);
-                prefetch_l2(A.geoF + (size_t)tile * 128 * 16, 128u * 64u);
-            };
-            if (!ctl->abort) {
-                prefetch_tile(first);
-                prefetch_tile(first + stride);
-            }
             for (int it = 0; MODE == 0 && it + 1 < ntile; ++it) {
-                // the input region is free once the curl and lift MMAs of tile it completed
-                if (!wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u)) break;
+                // the operand region is free once the trace MMAs of tile it completed
+                if (!wait2(ctl, &ctl->tr_full, (uint32_t)it & 1u)) break;
                 tc::mbar_expect_tx(&ctl->sa_full, in_tile_bytes);
                 tc::bulk_g2s(s_sa, op_in + (size_t)(first + (it + 1) * stride) * in_tile_bytes, in_tile_bytes,
                              &ctl->sa_full);
                 issued = it + 2;
-                prefetch_tile(first + (it + 2) * stride);
             }
             // nothing of ours may still be landing when shared memory is given up
             if (tab_issued) tc::mbar_wait(&ctl->tab_full, 0u, kDrain2);
@@ -333,79 +320,146 @@ __global__ void __launch_bounds__(512, 1)
     } else if (warp == 0) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = wait2(ctl, &ctl->tab_full, 0u);
+            // The MMA programs are the same for every tile (fixed shared-memory
+            // operands, fixed TMEM columns): build them once, then issue each
+            // entry with a handful of instructions.
+            MmaOp* prog = reinterpret_cast<MmaOp*>(smem + 1024);
+            int n1 = 0, n2 = 0;
             const uint32_t fmt = OP::fmt;
+            auto mk = [&](uint32_t dcol, uint32_t a, uint32_t b, uint32_t rows, int n, bool neg, bool acc) {
+                MmaOp o;
+                o.d = dcol;
+                o.idesc = idesc2(fmt, n, neg);
+                o.acc = acc ? 1u : 0u;
+                o.pad = 0u;
+                o.a = tc::sdesc(a, kChunk, 128u);
+                o.b = tc::sdesc(b, rows * 16u, 128u);
+                return o;
+            };
+            // Consecutive MMAs into one accumulator wait for each other; the
+            // programs interleave independent accumulators round-robin: the
+            // three output components (curl, then lift), the eight trace blocks.
+            if (MODE == 0) {
+                const int ksin = q.Npin / 16, ksg = q.G / 16;
+                // entries of component m: 2 ksin curl steps, then ksg per lift block
+                auto nlift = [&](int m) {
+                    int c = 0;
+                    for (int f = 0; f < 4; ++f) c += (A.tsgn[f][1][m] != 0) + (A.tsgn[f][0][m] != 0);
+                    return c;
+                };
+                int len[3], lmax = 0;
+                for (int m = 0; m < 3; ++m) {
+                    len[m] = 2 * ksin + ksg * nlift(m);
+                    lmax = len[m] > lmax ? len[m] : lmax;
+                }
+                for (int jj = 0; jj < lmax; ++jj)
+                    for (int m = 0; m < 3; ++m) {
+                        if (jj >= len[m]) continue;
+                        const uint32_t dcol = q.acc0 + (uint32_t)(m * q.Npout);
+                        if (jj < 2 * ksin) {
+                            const int j = jj / ksin, s = jj % ksin;
+                            int in, dd;
+                            bool neg;
+                            curl_chain(IS_H, m, j, in, dd, neg);
+                            const uint32_t abase = a_sa + (uint32_t)(in * q.Npin / 8) * kChunk;
+                            const uint32_t bbase = a_curl + (uint32_t)(dd * q.Npin * q.Npout * 2);
+                            prog[n1++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
+                                            bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout, q.Npout, neg,
+                                            jj > 0);
+                        } else {
+                            // lift: block (f, 0) with t2_{f,m}, block (f, 1) with -t1_{f,m}
+                            int r = (jj - 2 * ksin) / ksg;
+                            const int s = (jj - 2 * ksin) % ksg;
+                            for (int f = 0; f < 4; ++f)
+                                for (int i = 0; i < 2; ++i) {
+                                    const int c = i == 0 ? A.tsgn[f][1][m] : -A.tsgn[f][0][m];
+                                    if (c == 0) continue;
+                                    if (r-- != 0) continue;
+                                    const uint32_t abase = a_sf + (uint32_t)((2 * f + i) * (q.G / 8)) * kChunk;
+                                    const uint32_t bbase = a_lift + (uint32_t)(f * q.Npout * q.G * 2);
+                                    prog[n1++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
+                                                    bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout,
+                                                    q.Npout, c < 0, true);
+                                }
+                        }
+                    }
+            }
+            // traces of the updated field: block (f, i) = sum_m t_{f,i,m} Tr_f X_m
+            {
+                const int ksout = q.Npout / 16;
+                int len[8], lmax = 0;
+                for (int blk = 0; blk < 8; ++blk) {
+                    int nc = 0;
+                    for (int m = 0; m < 3; ++m) nc += A.tsgn[blk >> 1][blk & 1][m] != 0;
+                    len[blk] = nc * ksout;
+                    lmax = len[blk] > lmax ? len[blk] : lmax;
+                }
+                for (int jj = 0; jj < lmax; ++jj)
+                    for (int blk = 0; blk < 8; ++blk) {
+                        if (jj >= len[blk]) continue;
+                        const int f = blk >> 1, i = blk & 1;
+                        int r = jj / ksout;
+                        const int s = jj % ksout;
+                        for (int m = 0; m < 3; ++m) {
+                            const int c = A.tsgn[f][i][m];
+                            if (c == 0) continue;
+                            if (r-- != 0) continue;
+                            const uint32_t abase = a_sa + (uint32_t)(m * q.Npout / 8) * kChunk;
+                            const uint32_t dcol = q.tr0 + (uint32_t)(blk * q.G);
+                            const uint32_t bbase = a_trace + (uint32_t)(f * q.G * q.Npout * 2);
+                            prog[n1 + n2++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
+                                                 bbase + (uint32_t)(2 * s * q.G * 16), (uint32_t)q.G, q.G, c < 0, jj > 0);
+                        }
+                    }
+            }
+            if (n1 + n2 > kProgMax) ctl->abort = 1;   // cannot happen for p <= 6 (at most 104 entries)
+            bool ok = wait2(ctl, &ctl->tab_full, 0u);
             for (int it = 0; it < ntile && ok; ++it) {
                 if (MODE == 0) {
                     ok = wait2(ctl, &ctl->sa_full, (uint32_t)it & 1u) && wait2(ctl, &ctl->sf_full, (uint32_t)it & 1u);
                     if (ok && q.overlap && it > 0) ok = wait2(ctl, &ctl->tr_empty, (uint32_t)(it - 1) & 1u);
                     if (!ok) break;
                     tc::tc_fence_after();
-                    const int ksin = q.Npin / 16, ksg = q.G / 16;
-                    for (int m = 0; m < 3; ++m) {
-                        const uint32_t dcol = tmem + q.acc0 + (uint32_t)(m * q.Npout);
-                        for (int j = 0; j < 2; ++j) {
-                            int in, dd;
-                            bool neg;
-                            curl_chain(IS_H, m, j, in, dd, neg);
-                            const uint32_t abase = a_sa + (uint32_t)(in * q.Npin / 8) * kChunk;
-                            const uint32_t bbase = a_curl + (uint32_t)(dd * q.Npin * q.Npout * 2);
-                            for (int s = 0; s < ksin; ++s)
-                                mma2(fmt, dcol, abase + (uint32_t)(2 * s) * kChunk,
-                                     bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout, q.Npout, neg,
-                                     j > 0 || s > 0);
-                        }
-                        // lift: block (f, 0) with t2_{f,m}, block (f, 1) with -t1_{f,m}
-                        for (int f = 0; f < 4; ++f)
-                            for (int i = 0; i < 2; ++i) {
-                                const int c = i == 0 ? A.tsgn[f][1][m] : -A.tsgn[f][0][m];
-                                if (c == 0) continue;
-                                const uint32_t abase = a_sf + (uint32_t)((2 * f + i) * (q.G / 8)) * kChunk;
-                                const uint32_t bbase = a_lift + (uint32_t)(f * q.Npout * q.G * 2);
-                                for (int s = 0; s < ksg; ++s)
-                                    mma2(fmt, dcol, abase + (uint32_t)(2 * s) * kChunk,
-                                         bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout, q.Npout, c < 0,
-                                         true);
-                            }
-                    }
+                    for (int k = 0; k < n1; ++k) issue_op(prog[k], tmem);
                     tc::mma_commit(&ctl->m1_done);
                 }
                 ok = wait2(ctl, &ctl->u_done, (uint32_t)it & 1u);
                 if (ok && (MODE == 1 || !q.overlap) && it > 0) ok = wait2(ctl, &ctl->tr_empty, (uint32_t)(it - 1) & 1u);
                 if (!ok) break;
                 tc::tc_fence_after();
-                // traces of the updated field: block (f, i) = sum_m t_{f,i,m} Tr_f X_m
-                const int ksout = q.Npout / 16;
-                for (int m = 0; m < 3; ++m) {
-                    const uint32_t abase = a_sf + (uint32_t)(m * q.Npout / 8) * kChunk;
-                    for (int f = 0; f < 4; ++f)
-                        for (int i = 0; i < 2; ++i) {
-                            const int c = A.tsgn[f][i][m];
-                            if (c == 0) continue;
-                            bool first_m = true;
-                            for (int mm = 0; mm < m; ++mm)
-                                if (A.tsgn[f][i][mm] != 0) first_m = false;
-                            const uint32_t dcol = tmem + q.tr0 + (uint32_t)((2 * f + i) * q.G);
-                            const uint32_t bbase = a_trace + (uint32_t)(f * q.G * q.Npout * 2);
-                            for (int s = 0; s < ksout; ++s)
-                                mma2(fmt, dcol, abase + (uint32_t)(2 * s) * kChunk, bbase + (uint32_t)(2 * s * q.G * 16),
-                                     (uint32_t)q.G, q.G, c < 0, !(first_m && s == 0));
-                        }
-                }
+                for (int k = n1; k < n1 + n2; ++k) issue_op(prog[k], tmem);
                 tc::mma_commit(&ctl->tr_full);
             }
             tc::mma_commit(&ctl->fin);
             tc::mbar_wait(&ctl->fin, 0u, kDrain2);
         }
-    } else if (tid >= 128 && tid < 128 + nU) {
-        // ------------------------------------------------------------ WG1: update and traces
-        const int u = tid - 128;
-        const int w = u >> 5;                  // warp within WG1
-        const int quarter = (warp & 3);        // TMEM lanes of this warp
-        const int e = quarter * 32 + lane;     // element row of the tile
-        const int sub = w >> 2;                // which share of the element's work
-        const uint32_t lane_t = tmem + ((uint32_t)(quarter * 32) << 16);
+    } else if (tid >= 128 && tid < 256) {
+        // ------------------------------------------------------------ WG1: update
+        // One thread per element (TMEM lane).  The fp32 state comes in 8-coefficient
+        // batches (three components, six 16-byte loads) through a four-deep register
+        // ring; the ring's first four batches of the next tile are loaded as soon as
+        // this tile's update is done, so they land while the traces are computed.
+        const int e = tid - 128;
+        const uint32_t lane_t = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int nvb = (q.Nout + 7) / 8;   // batches holding coefficients
         double eacc = 0.0;
+        float4 r0[6], r1[6], r2[6], r3[6];
+        auto tile_state = [&](int it) { return st_out + (size_t)(first + it * stride) * (3 * q.Npout) * 128; };
+        auto load_b = [&](const float* st, int b, float4* v) {
+            const float4* s4 = reinterpret_cast<const float4*>(st) + ((size_t)(2 * b) * 128 + e);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                v[2 * m] = s4[(size_t)(m * q.Npout / 4) * 128];
+                v[2 * m + 1] = s4[(size_t)(m * q.Npout / 4 + 1) * 128];
+            }
+        };
+        auto load_ring = [&](const float* st) {
+            if (0 < nvb) load_b(st, 0, r0);
+            if (1 < nvb) load_b(st, 1, r1);
+            if (2 < nvb) load_b(st, 2, r2);
+            if (3 < nvb) load_b(st, 3, r3);
+        };
+        if (MODE == 0 && ntile > 0) load_ring(tile_state(0));
         for (int it = 0; it < ntile; ++it) {
             const int tile = first + it * stride;
             const int64_t t = (int64_t)tile * 128 + e;
@@ -416,45 +470,26 @@ __global__ void __launch_bounds__(512, 1)
             const float Gi[6] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y};
             const float Gm[6] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w};
             const double mat = IS_H ? (double)g3.y : (double)g3.x;
-            bool ok = true;
             float eloc = 0.f;
             if (MODE == 0) {
+                const bool ok = wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u);
+                tc::tc_fence_after();
                 const float sT = IS_H ? -g3.z : g3.z;   // r = -s_T D (H-phase), s_T D (E-phase)
                 const float sc = (float)(dt / mat);
                 const float co = (float)c_out, alo = (float)a_lo;
-                const int nvb = (q.Nout + 7) / 8;        // batches holding coefficients
-                // the fp32 state of this thread's batches, one batch ahead of the arithmetic;
-                // the first one before the wait for the accumulator
-                float4 cur[6], nxt[6];
-                auto load_batch = [&](int b, float4* v) {
-                    const float4* s4 = reinterpret_cast<const float4*>(st) + ((size_t)(2 * b) * 128 + e);
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        v[2 * m] = s4[(size_t)(m * q.Npout / 4) * 128];
-                        v[2 * m + 1] = s4[(size_t)(m * q.Npout / 4 + 1) * 128];
-                    }
-                };
-                if (sub < nvb) load_batch(sub, cur);
-                ok = wait2(ctl, &ctl->m1_done, (uint32_t)it & 1u);
-                tc::tc_fence_after();
-                for (int b = sub; b < nvb && ok; b += upe) {
-                    if (b + upe < nvb) load_batch(b + upe, nxt);
-                    float x[24], dd[24];
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        const float4 v0 = cur[2 * m], v1 = cur[2 * m + 1];
-                        x[8 * m + 0] = v0.x; x[8 * m + 1] = v0.y; x[8 * m + 2] = v0.z; x[8 * m + 3] = v0.w;
-                        x[8 * m + 4] = v1.x; x[8 * m + 5] = v1.y; x[8 * m + 6] = v1.z; x[8 * m + 7] = v1.w;
-                    }
+                auto process = [&](int b, float4* v) {
+                    // the batch's values, updated in place: x[8 m + c] = coefficient 8 b + c of component m
+                    float* x = reinterpret_cast<float*>(v);
+                    float dd[24];
                     tmem_ld3x8(lane_t + q.acc0 + (uint32_t)(8 * b), lane_t + q.acc0 + (uint32_t)(q.Npout + 8 * b),
                                lane_t + q.acc0 + (uint32_t)(2 * q.Npout + 8 * b), dd);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         if (8 * b + c >= q.Nout) break;
-                        const float r0 = sT * dd[c], r1 = sT * dd[8 + c], r2 = sT * dd[16 + c];
-                        const float d0 = sc * (Gi[0] * r0 + Gi[1] * r1 + Gi[2] * r2);
-                        const float d1 = sc * (Gi[1] * r0 + Gi[3] * r1 + Gi[4] * r2);
-                        const float d2 = sc * (Gi[2] * r0 + Gi[4] * r1 + Gi[5] * r2);
+                        const float rr0 = sT * dd[c], rr1 = sT * dd[8 + c], rr2 = sT * dd[16 + c];
+                        const float d0 = sc * (Gi[0] * rr0 + Gi[1] * rr1 + Gi[2] * rr2);
+                        const float d1 = sc * (Gi[1] * rr0 + Gi[3] * rr1 + Gi[4] * rr2);
+                        const float d2 = sc * (Gi[2] * rr0 + Gi[4] * rr1 + Gi[5] * rr2);
                         float& h0 = x[c];
                         float& h1 = x[8 + c];
                         float& h2 = x[16 + c];
@@ -482,35 +517,49 @@ __global__ void __launch_bounds__(512, 1)
                     float4* s4 = reinterpret_cast<float4*>(st) + ((size_t)(2 * b) * 128 + e);
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {
-                        s4[(size_t)(m * q.Npout / 4) * 128] = make_float4(x[8 * m + 0], x[8 * m + 1], x[8 * m + 2], x[8 * m + 3]);
-                        s4[(size_t)(m * q.Npout / 4 + 1) * 128] =
-                            make_float4(x[8 * m + 4], x[8 * m + 5], x[8 * m + 6], x[8 * m + 7]);
+                        s4[(size_t)(m * q.Npout / 4) * 128] = v[2 * m];
+                        s4[(size_t)(m * q.Npout / 4 + 1) * 128] = v[2 * m + 1];
                     }
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {
-                        float v[8];
+                        float w[8];
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) v[c] = 8 * b + c < q.Nout ? x[8 * m + c] : 0.f;
-                        const uint4 o = make_uint4(OP::pack(v[0], v[1]), OP::pack(v[2], v[3]), OP::pack(v[4], v[5]),
-                                                   OP::pack(v[6], v[7]));
+                        for (int c = 0; c < 8; ++c) w[c] = 8 * b + c < q.Nout ? x[8 * m + c] : 0.f;
+                        const uint4 o = make_uint4(OP::pack(w[0], w[1]), OP::pack(w[2], w[3]), OP::pack(w[4], w[5]),
+                                                   OP::pack(w[6], w[7]));
                         const size_t off = ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16;
                         *reinterpret_cast<uint4*>(opg + off) = o;
-                        *reinterpret_cast<uint4*>(s_sf + off) = o;
+                        *reinterpret_cast<uint4*>(s_sa + off) = o;
                     }
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) cur[k] = nxt[k];
+                };
+                for (int k0 = 0; k0 < nvb && ok; k0 += 4) {
+                    process(k0, r0);
+                    if (k0 + 4 < nvb) load_b(st, k0 + 4, r0);
+                    if (k0 + 1 < nvb) {
+                        process(k0 + 1, r1);
+                        if (k0 + 5 < nvb) load_b(st, k0 + 5, r1);
+                    }
+                    if (k0 + 2 < nvb) {
+                        process(k0 + 2, r2);
+                        if (k0 + 6 < nvb) load_b(st, k0 + 6, r2);
+                    }
+                    if (k0 + 3 < nvb) {
+                        process(k0 + 3, r3);
+                        if (k0 + 7 < nvb) load_b(st, k0 + 7, r3);
+                    }
                 }
                 // batches of padding only: zero operand chunks for the trace GEMM
-                for (int b = nvb + ((sub - nvb) % upe + upe) % upe; b < nbat && ok; b += upe)
+                for (int b = nvb; b < nbat && ok; ++b)
 #pragma unroll
                     for (int m = 0; m < 3; ++m)
-                        *reinterpret_cast<uint4*>(s_sf + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) =
+                        *reinterpret_cast<uint4*>(s_sa + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) =
                             make_uint4(0u, 0u, 0u, 0u);
-                eacc += 0.5 * mat * (double)eloc;
+                // the first batches of the next tile, while this tile's traces are computed
+                if (it + 1 < ntile) load_ring(tile_state(it + 1));
             } else {
                 // traces only: the operand copy of the field from its fp32 state
                 // (changed from outside: import, sources, checkpoints)
-                for (int b = sub; b < nbat; b += upe) {
+                for (int b = 0; b < nbat; ++b) {
                     const bool valid = 8 * b < q.Nout;
                     float x[24];
 #pragma unroll
@@ -521,13 +570,10 @@ __global__ void __launch_bounds__(512, 1)
                             const float4 v0 = s4[0], v1 = s4[128];
                             x[8 * m + 0] = v0.x; x[8 * m + 1] = v0.y; x[8 * m + 2] = v0.z; x[8 * m + 3] = v0.w;
                             x[8 * m + 4] = v1.x; x[8 * m + 5] = v1.y; x[8 * m + 6] = v1.z; x[8 * m + 7] = v1.w;
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) x[8 * m + c] = 0.f;
                         }
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
-                            if (8 * b + c >= q.Nout) x[8 * m + c] = 0.f;
+                            if (!valid || 8 * b + c >= q.Nout) x[8 * m + c] = 0.f;
                     }
                     if (energy && !IS_H && valid) {
 #pragma unroll
@@ -542,52 +588,38 @@ __global__ void __launch_bounds__(512, 1)
                         const uint4 o = make_uint4(OP::pack(x[8 * m], x[8 * m + 1]), OP::pack(x[8 * m + 2], x[8 * m + 3]),
                                                    OP::pack(x[8 * m + 4], x[8 * m + 5]),
                                                    OP::pack(x[8 * m + 6], x[8 * m + 7]));
-                        *reinterpret_cast<uint4*>(opg + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
-                        *reinterpret_cast<uint4*>(s_sf + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) = o;
+                        const size_t off = ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16;
+                        *reinterpret_cast<uint4*>(opg + off) = o;
+                        *reinterpret_cast<uint4*>(s_sa + off) = o;
                     }
                 }
-                eacc += 0.5 * mat * (double)eloc;
             }
+            eacc += 0.5 * mat * (double)eloc;
             // the updated operand tile in shared memory goes to the tensor cores
             tc::fence_proxy_async();
             tc::tc_fence_before();
-            named_bar(1, nU);
-            if (u == 0) mbar_arrive(&ctl->u_done);
-            // trace epilogue: blocks (f, i) of the trace columns -> trace buffer row of t
-            ok = wait2(ctl, &ctl->tr_full, (uint32_t)it & 1u);
-            tc::tc_fence_after();
-            if (ok) {
-                uint8_t* row = tr_out + (size_t)t * q.NT * 2;
-                for (int blk = sub; blk < 8; blk += upe)
-                    for (int c = 0; c < q.G8 / 8; ++c) {
-                        float v[8];
-                        tmem_ld8(lane_t + q.tr0 + (uint32_t)(blk * q.G + 8 * c), v);
-                        *reinterpret_cast<uint4*>(row + (size_t)(blk * q.G8 + 8 * c) * 2) =
-                            make_uint4(OP::pack(v[0], v[1]), OP::pack(v[2], v[3]), OP::pack(v[4], v[5]),
-                                       OP::pack(v[6], v[7]));
-                    }
-            }
-            tc::tc_fence_before();
-            named_bar(1, nU);
-            if (u == 0) mbar_arrive(&ctl->tr_empty);
+            named_bar(1, 128);
+            if (e == 0) mbar_arrive(&ctl->u_done);
         }
         if (energy) {
             for (int o = 16; o > 0; o >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, o);
-            if (lane == 0) ctl->red[w] = eacc;
-            named_bar(1, nU);
-            if (u == 0) {
-                double sum = 0.0;
-                for (int i = 0; i < nU / 32; ++i) sum += ctl->red[i];
+            if (lane == 0) ctl->red[warp & 3] = eacc;
+            named_bar(1, 128);
+            if (e == 0) {
+                const double sum = ((ctl->red[0] + ctl->red[1]) + ctl->red[2]) + ctl->red[3];
                 const bool h = MODE == 0 ? IS_H : false;
                 (h ? A.partH : A.partE)[blockIdx.x] = sum;
             }
         }
-    } else if (MODE == 0 && tid >= wg2_first && tid < wg2_first + 128) {
-        // ------------------------------------------------------------ WG2: flux
-        // The flux region also carries the previous tile's updated operand tile
-        // until its trace MMAs complete; the first two faces' trace loads are
-        // issued before that wait, the last two after it.
-        const int e = tid - wg2_first;
+    } else if (tid >= 256 && tid < 384) {
+        // ------------------------------------------------------------ WG2: flux and traces
+        // For tile it + 1: the jump (H-phase) or average (E-phase) of the
+        // element's and its neighbours' tangential traces, written as the A
+        // operand of the lift (the first two faces' loads are issued before the
+        // wait for the flux blocks to be free, the last two after it).  Then,
+        // for tile it: the traces of the updated field into the trace buffer.
+        const int e = tid - 256;
+        const uint32_t lane_t = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const int nG8 = q.G8 / 8, nG = q.G / 8;
         uint4 ov[2][6], nv[2][6];
         int4 nb4 = make_int4(-1, -1, -1, -1);
@@ -638,20 +670,14 @@ __global__ void __launch_bounds__(512, 1)
                     *reinterpret_cast<uint4*>(s_sf + ((size_t)((2 * f + i) * nG + cc) * 128 + e) * 16) =
                         make_uint4(o[0], o[1], o[2], o[3]);
                 }
-                // the block's padding chunks (the region held other data in between)
-                for (int i = 0; i < 2; ++i)
-                    for (int c = nG8; c < nG; ++c)
-                        *reinterpret_cast<uint4*>(s_sf + ((size_t)((2 * f + i) * nG + c) * 128 + e) * 16) =
-                            make_uint4(0u, 0u, 0u, 0u);
             }
         };
-        for (int it = 0; it < ntile; ++it) {
-            const int tile = first + it * stride;
-            const int64_t t = (int64_t)tile * 128 + e;
+        auto flux = [&](int it) {
+            const int64_t t = (int64_t)(first + it * stride) * 128 + e;
             nb4 = *reinterpret_cast<const int4*>(A.nbr + t * 4);
             load_pair(t, 0);
-            // the region is free once the trace MMAs of the previous tile completed
-            const bool ok = it == 0 || wait2(ctl, &ctl->tr_full, (uint32_t)(it - 1) & 1u);
+            // the flux blocks are free once the lift of the previous tile completed
+            const bool ok = it == 0 || wait2(ctl, &ctl->m1_done, (uint32_t)(it - 1) & 1u);
             if (ok) {
                 write_pair(0);
                 load_pair(t, 1);
@@ -660,6 +686,34 @@ __global__ void __launch_bounds__(512, 1)
             tc::fence_proxy_async();
             named_bar(2, 128);
             if (e == 0) mbar_arrive(&ctl->sf_full);
+        };
+        if (MODE == 0) {
+            // the padding chunks of each flux block stay zero
+            for (int blk = 0; blk < 8; ++blk)
+                for (int c = nG8; c < nG; ++c)
+                    *reinterpret_cast<uint4*>(s_sf + ((size_t)(blk * nG + c) * 128 + e) * 16) = make_uint4(0u, 0u, 0u, 0u);
+            if (ntile > 0) flux(0);
+        }
+        for (int it = 0; it < ntile; ++it) {
+            if (MODE == 0 && it + 1 < ntile) flux(it + 1);
+            // trace epilogue of tile it: blocks (f, i) of the trace columns -> trace buffer row
+            const int64_t t = (int64_t)(first + it * stride) * 128 + e;
+            const bool ok = wait2(ctl, &ctl->tr_full, (uint32_t)it & 1u);
+            tc::tc_fence_after();
+            if (ok) {
+                uint8_t* row = tr_out + (size_t)t * q.NT * 2;
+                for (int blk = 0; blk < 8; ++blk)
+                    for (int c = 0; c < nG8; ++c) {
+                        float v[8];
+                        tmem_ld8(lane_t + q.tr0 + (uint32_t)(blk * q.G + 8 * c), v);
+                        *reinterpret_cast<uint4*>(row + (size_t)(blk * q.G8 + 8 * c) * 2) =
+                            make_uint4(OP::pack(v[0], v[1]), OP::pack(v[2], v[3]), OP::pack(v[4], v[5]),
+                                       OP::pack(v[6], v[7]));
+                    }
+            }
+            tc::tc_fence_before();
+            named_bar(2, 128);
+            if (e == 0) mbar_arrive(&ctl->tr_empty);
         }
     }
     tc::tc_fence_before();
@@ -752,7 +806,7 @@ int launch2(const TCArgs& a, int grid, double dt, double a_lo, double c_out, int
     const TC2Smem L = tc2_smem(a.d, IS_H);
     const void* fn = (const void*)k_tc2<IS_H, MODE, BF>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) return -1;
-    const int threads = 128 * (2 + a.upe) - (MODE == 1 ? 128 : 0);
+    const int threads = 384;
     k_tc2<IS_H, MODE, BF><<<grid, threads, L.total, s>>>(a, dt, a_lo, c_out, energy, tc2_tr0(a.d, IS_H), tile0, tile1);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

@@ -392,7 +392,6 @@ int tc2_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double
     A.partH = part + P->tc_grid;
     A.err = P->dErr;
     for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
-    A.upe = 2;
     P->tc = true;
     P->trE_valid = P->trH_valid = false;
     return DGM_OK;

@@ -65,7 +65,6 @@ struct TCArgs {
     const void* T2H;           // H-phase tables: curl D_d (3), lift (4 faces), trace (4 faces)
     const void* T2E;           // E-phase tables: curl^T, lift, trace
     int8_t tsgn[4][2][3];      // reference face tangents t_{f,i} (entries -1, 0, 1)
-    int upe;                   // update/trace threads per element (1 or 2)
 };
 
 // Byte sizes and shared-memory offsets of one layout-2 kernel instance.
