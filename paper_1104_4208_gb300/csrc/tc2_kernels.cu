@@ -145,6 +145,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
+// this thread's 16 bytes (and the line holding them) into L2, no register or wait
+__device__ __forceinline__ void prefetch_l2_line(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // kind::f16 instruction descriptor: D fp32, A = B = fp16 or bf16, K-major, M = 128, B optionally negated
@@ -336,79 +341,56 @@ __global__ void __launch_bounds__(384, 1)
                 o.b = tc::sdesc(b, rows * 16u, 128u);
                 return o;
             };
-            // Consecutive MMAs into one accumulator wait for each other; the
-            // programs interleave independent accumulators round-robin: the
-            // three output components (curl, then lift), the eight trace blocks.
+            // Each accumulator's chain is issued in one run (the tensor cores were
+            // measured faster on consecutive MMAs into one accumulator than on
+            // MMAs interleaved across accumulators).
             if (MODE == 0) {
                 const int ksin = q.Npin / 16, ksg = q.G / 16;
-                // entries of component m: 2 ksin curl steps, then ksg per lift block
-                auto nlift = [&](int m) {
-                    int c = 0;
-                    for (int f = 0; f < 4; ++f) c += (A.tsgn[f][1][m] != 0) + (A.tsgn[f][0][m] != 0);
-                    return c;
-                };
-                int len[3], lmax = 0;
                 for (int m = 0; m < 3; ++m) {
-                    len[m] = 2 * ksin + ksg * nlift(m);
-                    lmax = len[m] > lmax ? len[m] : lmax;
-                }
-                for (int jj = 0; jj < lmax; ++jj)
-                    for (int m = 0; m < 3; ++m) {
-                        if (jj >= len[m]) continue;
-                        const uint32_t dcol = q.acc0 + (uint32_t)(m * q.Npout);
-                        if (jj < 2 * ksin) {
-                            const int j = jj / ksin, s = jj % ksin;
-                            int in, dd;
-                            bool neg;
-                            curl_chain(IS_H, m, j, in, dd, neg);
-                            const uint32_t abase = a_sa + (uint32_t)(in * q.Npin / 8) * kChunk;
-                            const uint32_t bbase = a_curl + (uint32_t)(dd * q.Npin * q.Npout * 2);
+                    const uint32_t dcol = q.acc0 + (uint32_t)(m * q.Npout);
+                    for (int j = 0; j < 2; ++j) {
+                        int in, dd;
+                        bool neg;
+                        curl_chain(IS_H, m, j, in, dd, neg);
+                        const uint32_t abase = a_sa + (uint32_t)(in * q.Npin / 8) * kChunk;
+                        const uint32_t bbase = a_curl + (uint32_t)(dd * q.Npin * q.Npout * 2);
+                        for (int s = 0; s < ksin; ++s)
                             prog[n1++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
                                             bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout, q.Npout, neg,
-                                            jj > 0);
-                        } else {
-                            // lift: block (f, 0) with t2_{f,m}, block (f, 1) with -t1_{f,m}
-                            int r = (jj - 2 * ksin) / ksg;
-                            const int s = (jj - 2 * ksin) % ksg;
-                            for (int f = 0; f < 4; ++f)
-                                for (int i = 0; i < 2; ++i) {
-                                    const int c = i == 0 ? A.tsgn[f][1][m] : -A.tsgn[f][0][m];
-                                    if (c == 0) continue;
-                                    if (r-- != 0) continue;
-                                    const uint32_t abase = a_sf + (uint32_t)((2 * f + i) * (q.G / 8)) * kChunk;
-                                    const uint32_t bbase = a_lift + (uint32_t)(f * q.Npout * q.G * 2);
-                                    prog[n1++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
-                                                    bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout,
-                                                    q.Npout, c < 0, true);
-                                }
-                        }
+                                            j > 0 || s > 0);
                     }
+                    // lift: block (f, 0) with t2_{f,m}, block (f, 1) with -t1_{f,m}
+                    for (int f = 0; f < 4; ++f)
+                        for (int i = 0; i < 2; ++i) {
+                            const int c = i == 0 ? A.tsgn[f][1][m] : -A.tsgn[f][0][m];
+                            if (c == 0) continue;
+                            const uint32_t abase = a_sf + (uint32_t)((2 * f + i) * (q.G / 8)) * kChunk;
+                            const uint32_t bbase = a_lift + (uint32_t)(f * q.Npout * q.G * 2);
+                            for (int s = 0; s < ksg; ++s)
+                                prog[n1++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
+                                                bbase + (uint32_t)(2 * s * q.Npout * 16), (uint32_t)q.Npout, q.Npout,
+                                                c < 0, true);
+                        }
+                }
             }
             // traces of the updated field: block (f, i) = sum_m t_{f,i,m} Tr_f X_m
             {
                 const int ksout = q.Npout / 16;
-                int len[8], lmax = 0;
-                for (int blk = 0; blk < 8; ++blk) {
-                    int nc = 0;
-                    for (int m = 0; m < 3; ++m) nc += A.tsgn[blk >> 1][blk & 1][m] != 0;
-                    len[blk] = nc * ksout;
-                    lmax = len[blk] > lmax ? len[blk] : lmax;
-                }
-                for (int jj = 0; jj < lmax; ++jj)
-                    for (int blk = 0; blk < 8; ++blk) {
-                        if (jj >= len[blk]) continue;
-                        const int f = blk >> 1, i = blk & 1;
-                        int r = jj / ksout;
-                        const int s = jj % ksout;
+                for (int f = 0; f < 4; ++f)
+                    for (int i = 0; i < 2; ++i) {
+                        bool first = true;
                         for (int m = 0; m < 3; ++m) {
                             const int c = A.tsgn[f][i][m];
                             if (c == 0) continue;
-                            if (r-- != 0) continue;
                             const uint32_t abase = a_sa + (uint32_t)(m * q.Npout / 8) * kChunk;
-                            const uint32_t dcol = q.tr0 + (uint32_t)(blk * q.G);
+                            const uint32_t dcol = q.tr0 + (uint32_t)((2 * f + i) * q.G);
                             const uint32_t bbase = a_trace + (uint32_t)(f * q.G * q.Npout * 2);
-                            prog[n1 + n2++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
-                                                 bbase + (uint32_t)(2 * s * q.G * 16), (uint32_t)q.G, q.G, c < 0, jj > 0);
+                            for (int s = 0; s < ksout; ++s) {
+                                prog[n1 + n2++] = mk(dcol, abase + (uint32_t)(2 * s) * kChunk,
+                                                     bbase + (uint32_t)(2 * s * q.G * 16), (uint32_t)q.G, q.G, c < 0,
+                                                     !first);
+                                first = false;
+                            }
                         }
                     }
             }
@@ -437,8 +419,9 @@ __global__ void __launch_bounds__(384, 1)
         // ------------------------------------------------------------ WG1: update
         // One thread per element (TMEM lane).  The fp32 state comes in 8-coefficient
         // batches (three components, six 16-byte loads) through a four-deep register
-        // ring; the ring's first four batches of the next tile are loaded as soon as
-        // this tile's update is done, so they land while the traces are computed.
+        // ring.  As soon as this tile's update is done the ring takes the next tile's
+        // first four batches and the rest of that tile's state is prefetched into L2,
+        // so both land while the traces and the next curl are computed.
         const int e = tid - 128;
         const uint32_t lane_t = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const int nvb = (q.Nout + 7) / 8;   // batches holding coefficients
@@ -532,21 +515,17 @@ __global__ void __launch_bounds__(384, 1)
                         *reinterpret_cast<uint4*>(s_sa + off) = o;
                     }
                 };
+                auto step = [&](int k, float4* v) {
+                    if (k < nvb) {
+                        process(k, v);
+                        if (k + 4 < nvb) load_b(st, k + 4, v);
+                    }
+                };
                 for (int k0 = 0; k0 < nvb && ok; k0 += 4) {
-                    process(k0, r0);
-                    if (k0 + 4 < nvb) load_b(st, k0 + 4, r0);
-                    if (k0 + 1 < nvb) {
-                        process(k0 + 1, r1);
-                        if (k0 + 5 < nvb) load_b(st, k0 + 5, r1);
-                    }
-                    if (k0 + 2 < nvb) {
-                        process(k0 + 2, r2);
-                        if (k0 + 6 < nvb) load_b(st, k0 + 6, r2);
-                    }
-                    if (k0 + 3 < nvb) {
-                        process(k0 + 3, r3);
-                        if (k0 + 7 < nvb) load_b(st, k0 + 7, r3);
-                    }
+                    step(k0, r0);
+                    step(k0 + 1, r1);
+                    step(k0 + 2, r2);
+                    step(k0 + 3, r3);
                 }
                 // batches of padding only: zero operand chunks for the trace GEMM
                 for (int b = nvb; b < nbat && ok; ++b)
@@ -554,12 +533,25 @@ __global__ void __launch_bounds__(384, 1)
                     for (int m = 0; m < 3; ++m)
                         *reinterpret_cast<uint4*>(s_sa + ((size_t)(m * q.Npout / 8 + b) * 128 + e) * 16) =
                             make_uint4(0u, 0u, 0u, 0u);
-                // the first batches of the next tile, while this tile's traces are computed
-                if (it + 1 < ntile) load_ring(tile_state(it + 1));
+                // the next tile: its first batches into the ring, the rest into L2
+                if (it + 1 < ntile) {
+                    const float* stn = tile_state(it + 1);
+                    load_ring(stn);
+                    for (int b = 4; b < nvb; ++b) {
+                        const float* p4 = stn + ((size_t)(2 * b) * 128 + e) * 4;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            prefetch_l2_line(p4 + (size_t)(m * q.Npout / 4) * 128 * 4);
+                            prefetch_l2_line(p4 + (size_t)(m * q.Npout / 4 + 1) * 128 * 4);
+                        }
+                    }
+                }
             } else {
                 // traces only: the operand copy of the field from its fp32 state
-                // (changed from outside: import, sources, checkpoints)
-                for (int b = 0; b < nbat; ++b) {
+                // (changed from outside: import, sources, checkpoints), into the
+                // operand region once the previous tile's trace MMAs have read it
+                const bool ok = it == 0 || wait2(ctl, &ctl->tr_full, (uint32_t)(it - 1) & 1u);
+                for (int b = 0; b < nbat && ok; ++b) {
                     const bool valid = 8 * b < q.Nout;
                     float x[24];
 #pragma unroll
