@@ -37,12 +37,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DoF-steps/s at p=4/6 (mixed vs FP64 plain, same GB300); % HBM roofline; err"
-DTYPE = {"tc32": "tf32", "tc16": "f16", "tcbf16": "bf16", "fp32": "f32", "fp64": "f64"}
+DTYPE = {"tc32": "tf32", "tc16": "f16", "tcbf16": "bf16", "tc16x2": "f16", "fp32": "f32", "fp64": "f64"}
 ARITH = {"tc32": "fp32 state, TF32 tensor-core operators (tcgen05), fp32 accumulate, fp64 geometry and energy",
          "tc16": "fp32 state with fp16 operand copies, fp16 tables and trace buffers, fp16 tensor-core operators "
                  "(tcgen05 kind::f16), fp32 accumulate, fp64 geometry and energy",
          "tcbf16": "fp32 state with bf16 operand copies, bf16 tables and trace buffers, bf16 tensor-core "
                    "operators (tcgen05 kind::f16, bf16 encoding), fp32 accumulate, fp64 energy sums",
+         "tc16x2": "fp32 state with fp16 operand copies, two-term fp16 tables (hi + lo, two MMAs per table "
+                   "K-step), fp16 trace buffers, tcgen05 kind::f16, fp32 accumulate, fp64 energy sums",
          "fp32": "fp32 state and CUDA-core arithmetic, fp64 geometry and energy",
          "fp64": "fp64 throughout"}
 UNIT = "DoF-steps/s"
@@ -108,7 +110,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="planewave_n32_p6")
-    ap.add_argument("--precision", default="tc16", choices=["tc16", "tcbf16", "tc32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tc16", choices=["tc16", "tcbf16", "tc16x2", "tc32", "fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
                     help="TC16 only: 0 resident-table kernels (default), 1 dense-operator kernels")
     ap.add_argument("--no-p4", action="store_true", help="skip the p = 4 sub-block of the default workload")
@@ -433,7 +435,7 @@ def run_gpu(args, rank, world, local):
     bytes_H, bytes_E = phase_bytes(w.nt, w.p, b)
     tH = stats.h_phase_ms / max(stats.h_launches, 1)
     tE = stats.e_phase_ms / max(stats.e_launches, 1)
-    tcp = args.precision in ("tc32", "tc16", "tcbf16")
+    tcp = args.precision in ("tc32", "tc16", "tcbf16", "tc16x2")
     resident = args.precision in ("tc16", "tcbf16") and args.variant == 0
     kpre = "k_tc2_phase" if resident else ("k_tc_phase" if tcp else "k_phase")
     if stats.h_phase_ms >= stats.e_phase_ms:

@@ -90,13 +90,21 @@ enum dgm_flux { DGM_FLUX_CENTRAL = 0, DGM_FLUX_STABILIZED = 1 };
  * operands (the operators streamed through a copy ring per tile).
  * TCBF16: the resident-table kernels with bf16 operands (8-bit mantissa,
  * fp32's range: no scaling needed; operand rounding 8x coarser than fp16).
+ * TC16X2: the dense-operator kernels with fp16 field operands and two-term
+ * reference tables: every table value v is held as hi = fp16(v) plus
+ * lo = fp16(v - hi) (about 22 significant bits), and every table MMA runs
+ * twice, hi and lo, into the same FP32 accumulator.  The rounding of the
+ * tables, which perturbs the operator itself and accumulates as a phase error
+ * over long runs, drops by about three orders of magnitude; the fields'
+ * operand rounding stays that of TC16.  About twice the table traffic of TC16.
  * Central flux, p <= 6 for every tensor-core precision. */
 enum dgm_precision {
     DGM_PREC_FP64 = 0,
     DGM_PREC_FP32 = 1,
     DGM_PREC_TC32 = 2,
     DGM_PREC_TC16 = 3,
-    DGM_PREC_TCBF16 = 4
+    DGM_PREC_TCBF16 = 4,
+    DGM_PREC_TC16X2 = 5
 };
 
 typedef struct dgm_options {
@@ -242,7 +250,7 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * after one warm-up step) on this problem's own fields with dt = 0, which
  * leaves the fields unchanged; the fastest is kept for all later calls.
  * Candidates: CUDA-core kernels (FP64, FP32) -- 4, 8, 16 or 24 blocks per SM;
- * dense-operator tensor-core kernels (TC32, TC16 variant 1) -- 1 or 2 CTAs per
+ * dense-operator tensor-core kernels (TC32, TC16X2, TC16 variant 1) -- 1 or 2 CTAs per
  * SM (2 only where the TMEM columns and shared memory of a CTA allow it);
  * resident-table tensor-core kernels (TC16, TCBF16) -- one configuration
  * (one CTA per SM), timed and reported like the others.  Every candidate computes

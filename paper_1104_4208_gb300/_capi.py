@@ -25,7 +25,7 @@ DGM_ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE", -5: "TIMEOU
 (DGM_ERR_INVALID_ARG, DGM_ERR_OOM, DGM_ERR_CUDA, DGM_ERR_UNSTABLE, DGM_ERR_TIMEOUT,
  DGM_ERR_UNSUPPORTED) = -1, -2, -3, -4, -5, -6
 DGM_FLUX_CENTRAL, DGM_FLUX_STABILIZED = 0, 1
-DGM_PREC_FP64, DGM_PREC_FP32, DGM_PREC_TC32, DGM_PREC_TC16, DGM_PREC_TCBF16 = 0, 1, 2, 3, 4
+DGM_PREC_FP64, DGM_PREC_FP32, DGM_PREC_TC32, DGM_PREC_TC16, DGM_PREC_TCBF16, DGM_PREC_TC16X2 = 0, 1, 2, 3, 4, 5
 DGM_PMAX = 8
 
 

@@ -305,7 +305,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         return DGM_ERR_INVALID_ARG;
     }
     if (o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32 && o.precision != DGM_PREC_TC32 &&
-        o.precision != DGM_PREC_TC16 && o.precision != DGM_PREC_TCBF16) {
+        o.precision != DGM_PREC_TC16 && o.precision != DGM_PREC_TCBF16 && o.precision != DGM_PREC_TC16X2) {
         set_error("dgm_problem_create: unknown precision");
         return DGM_ERR_INVALID_ARG;
     }
@@ -352,7 +352,8 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaSetDevice"));
     const size_t rs = P->fp32 ? sizeof(float) : sizeof(double);
     const int64_t nE = m.nt * 3 * P->NE, nH = m.nt * 3 * P->NH;
-    const bool tc = o.precision == DGM_PREC_TC32 || o.precision == DGM_PREC_TC16 || o.precision == DGM_PREC_TCBF16;
+    const bool tc = o.precision == DGM_PREC_TC32 || o.precision == DGM_PREC_TC16 || o.precision == DGM_PREC_TCBF16 ||
+                    o.precision == DGM_PREC_TC16X2;
     cudaError_t e;
     if (!tc) {
         if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc E"));

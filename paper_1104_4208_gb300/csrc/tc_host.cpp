@@ -76,9 +76,10 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     if ((P->opt.precision == DGM_PREC_TC16 && P->opt.variant != 1) || P->opt.precision == DGM_PREC_TCBF16)
         return tc2_problem_init(P, m, geo, nbr);
     const RefTables& T = P->tab;
-    const bool f16 = P->opt.precision == DGM_PREC_TC16;
-    const char* name = f16 ? "TC16" : "TC32";
-    const TCDims d = tc_dims(T.NE, T.NH, T.N2H, f16);
+    const bool split = P->opt.precision == DGM_PREC_TC16X2;
+    const bool f16 = P->opt.precision == DGM_PREC_TC16 || split;
+    const char* name = split ? "TC16X2" : f16 ? "TC16" : "TC32";
+    const TCDims d = tc_dims(T.NE, T.NH, T.N2H, f16, split);
     uint32_t stage = 0, r2 = 0;
     const size_t smem = tc_smem_bytes(d, &stage, &r2);
     if (P->p > 6 || smem + 1024 > 227 * 1024 || tc_tmem_cols(d) > 512) {
@@ -107,7 +108,9 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     const size_t b1e = (size_t)d.KHo * d.NCE, ble = (size_t)d.NT * d.NCE, bte = (size_t)d.KEo * d.NT;
     const size_t ntab = b1h + blh + bth + b1e + ble + bte;
     const size_t o_state = 0, o_Eo = bE + bH, o_Ho = o_Eo + bEo, o_tr = o_Ho + bHo, o_tab = o_tr + 2 * bTr;
-    const size_t total = o_tab + ntab * esz;
+    // two-term tables: the lo terms follow the hi terms, at one offset for all tables
+    const size_t lo_off = split ? round_up(ntab * esz, 1024) : 0;
+    const size_t total = o_tab + (split ? 2 * lo_off : ntab * esz);
     cudaError_t e;
     if ((e = cudaMalloc(&P->dTc, total)) != cudaSuccess) return cuda_err(e, "alloc");
     if ((e = cudaMemset(P->dTc, 0, o_tab)) != cudaSuccess) return cuda_err(e, "memset");
@@ -159,11 +162,15 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
         if ((e = cudaMemcpy(dtab, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_err(e, "tables");
     } else {
-        // fp32 staging copy, rounded to fp16 on the device
+        // fp32 staging copy, rounded to fp16 (or split into two fp16 terms) on the device
         float* stage32 = nullptr;
         if ((e = cudaMalloc(&stage32, ntab * sizeof(float))) != cudaSuccess) return cuda_err(e, "alloc tables");
         e = cudaMemcpy(stage32, tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && tc_launch_to_half(stage32, dtab, ntab, 0)) e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            const int r = split ? tc_launch_split_half(stage32, dtab, dtab + lo_off, ntab, 0)
+                                : tc_launch_to_half(stage32, dtab, ntab, 0);
+            if (r) e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(stage32);
         if (e != cudaSuccess) return cuda_err(e, "tables");
@@ -218,6 +225,7 @@ int tc_problem_init(dgm_problem* P, const MeshData& m, const std::vector<double>
     A.BtrE = dtab + o_bte * esz;
     A.partE = part;
     A.partH = part + P->tc_grid;   // contiguous with partE for the reduction; moves with tc_grid
+    A.tab_lo = (int64_t)lo_off;
     A.err = P->dErr;
     for (int f = 0; f < 4; ++f) A.sigma_hat[f] = (float)T.sigma_hat[f];
     A.stage_bytes = stage;

@@ -120,6 +120,7 @@ struct GemmDesc {
     int n[3];
     uint32_t dcol[3];
     int acc_first;     // accumulate onto D from the first step
+    int64_t lo_off;    // two-term tables: byte offset of B's lo term (0: one term)
 };
 
 // Producer + MMA issuer (thread 0).  g counts ring uses across GEMMs.  A
@@ -129,6 +130,7 @@ __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_
                           uint32_t tmem) {
     const uint32_t a_bytes = G.gA ? (uint32_t)(kTcRows * 32) : 0u;
     const uint32_t b_bytes = (uint32_t)G.brows * 32u;
+    const uint32_t lo_bytes = G.lo_off ? b_bytes : 0u;   // the lo slice follows the hi slice
     int produced = 0, consumed = 0;
     bool ok = true;
     auto produce = [&](int c) -> bool {
@@ -137,9 +139,11 @@ __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_
         const uint32_t use = gg / kStages;
         if (use > 0 && !tc::mbar_wait(&ctl->empty[st], (use - 1) & 1u, kLimit)) return false;
         uint8_t* sp = ring + (size_t)st * stage_bytes;
-        tc::mbar_expect_tx(&ctl->full[st], a_bytes + b_bytes);
+        tc::mbar_expect_tx(&ctl->full[st], a_bytes + b_bytes + lo_bytes);
         if (G.gA) tc::bulk_g2s(sp, G.gA + (size_t)c * kTcRows * 32, a_bytes, &ctl->full[st]);
         tc::bulk_g2s(sp + a_bytes, G.gB + (size_t)c * G.brows * 32, b_bytes, &ctl->full[st]);
+        if (lo_bytes)
+            tc::bulk_g2s(sp + a_bytes + b_bytes, G.gB + G.lo_off + (size_t)c * G.brows * 32, lo_bytes, &ctl->full[st]);
         ++produced;
         return true;
     };
@@ -155,6 +159,10 @@ __device__ bool ring_gemm(Ctl* ctl, uint8_t* ring, uint32_t stage_bytes, uint32_
         for (int j = 0; j < G.nmma; ++j) {
             const uint64_t bd = tc::sdesc(baddr + (uint32_t)G.row0[j] * 16u, (uint32_t)G.brows * 16u, 128u);
             OP::mma(tmem + G.dcol[j], ad, bd, G.n[j], (c > 0 || G.acc_first) ? 1u : 0u);
+            if (lo_bytes) {   // the table's lo term into the same accumulator
+                const uint64_t bl = tc::sdesc(baddr + b_bytes + (uint32_t)G.row0[j] * 16u, (uint32_t)G.brows * 16u, 128u);
+                OP::mma(tmem + G.dcol[j], ad, bl, G.n[j], 1u);
+            }
         }
         tc::mma_commit(&ctl->empty[st]);
         ++consumed;
@@ -418,6 +426,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
             GemmDesc G{};
             G.gA = in + (size_t)tile * Kin * kTcRows * sizeof(T);
             G.gB = Bc;
+            G.lo_off = A.tab_lo;
             G.brows = Nout;
             G.nk = Kin / (2 * OP::VPC);
             add_mmas(G, 0, Nout, 0);
@@ -434,6 +443,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
                 GemmDesc G{};
                 G.sA = tc::smem_u32(r2);
                 G.gB = Bl + (size_t)h * half_steps * Nout * 32;
+                G.lo_off = A.tab_lo;
                 G.brows = Nout;
                 G.nk = half_steps;
                 G.acc_first = 1;
@@ -494,6 +504,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_phase(TCArgs A, double dt, double
             GemmDesc G{};
             G.gA = reinterpret_cast<const uint8_t*>(out_op + (size_t)tile * Kop * kTcRows);
             G.gB = Bt;
+            G.lo_off = A.tab_lo;
             G.brows = d.NT;
             G.nk = Kop / (2 * OP::VPC);
             add_mmas(G, 0, d.NT, 0);
@@ -553,6 +564,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_traces(TCArgs A, int which, int t
             GemmDesc G{};
             G.gA = reinterpret_cast<const uint8_t*>(fo);
             G.gB = static_cast<const uint8_t*>(which == 0 ? A.BtrE : A.BtrH);
+            G.lo_off = A.tab_lo;
             G.brows = d.NT;
             G.nk = Ko / (2 * OP::VPC);
             add_mmas(G, 0, d.NT, 0);
@@ -656,6 +668,14 @@ __global__ void k_tc_unpack(const float* __restrict__ src, double* __restrict__ 
     }
 }
 
+__global__ void k_split_half(const float* __restrict__ src, __half* __restrict__ hi, __half* __restrict__ lo, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const __half h = __float2half_rn(src[i]);
+        hi[i] = h;
+        lo[i] = __float2half_rn(src[i] - __half2float(h));
+    }
+}
+
 __global__ void k_to_half(const float* __restrict__ src, __half* __restrict__ dst, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = __float2half_rn(src[i]);
@@ -672,7 +692,7 @@ size_t smem_of(const TCArgs& a) {
 
 }  // namespace
 
-TCDims tc_dims(int NE, int NH, int N2H, bool f16) {
+TCDims tc_dims(int NE, int NH, int N2H, bool f16, bool split) {
     TCDims d;
     d.NE = NE;
     d.NH = NH;
@@ -681,6 +701,7 @@ TCDims tc_dims(int NE, int NH, int N2H, bool f16) {
     d.f16 = f16 ? 1 : 0;
     d.bf16 = 0;
     d.NEp = d.NHp = d.G8 = d.G = 0;
+    d.split = split && f16 ? 1 : 0;
     d.VPC = f16 ? 8 : 4;
     d.KE = padto(3 * NE, 24);
     d.KH = padto(3 * NH, 24);
@@ -714,7 +735,8 @@ uint32_t tc_tmem_reach(const TCDims& d) {
 
 size_t tc_smem_bytes(const TCDims& d, uint32_t* stage_bytes, uint32_t* r2_offset) {
     const int maxB = std::max(std::max(d.NC, d.NCE), d.NT);
-    const uint32_t stage = (uint32_t)(kTcRows + maxB) * 32u;   // A slice (128 x 8) + B slice (rows x 8)
+    // A slice (128 rows) + B slice (rows), + the B lo slice with two-term tables
+    const uint32_t stage = (uint32_t)(kTcRows + maxB * (d.split ? 2 : 1)) * 32u;
     const uint32_t r2 = (uint32_t)kTcRows * (uint32_t)(2 * d.FB) * (d.f16 ? 2u : 4u);   // flux of two faces
     *stage_bytes = stage;
     *r2_offset = kHead + kStages * stage;
@@ -772,6 +794,13 @@ int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s) {
     if (n == 0) return 0;
     const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
     k_to_half<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(dst), n);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_launch_split_half(const float* src, void* hi, void* lo, size_t n, cudaStream_t s) {
+    if (n == 0) return 0;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    k_split_half<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(hi), static_cast<__half*>(lo), n);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -21,6 +21,7 @@ struct TCDims {
     int bf16;        // 2-byte operands are bf16 (8-bit mantissa, fp32 range)
     int NEp, NHp;    // layout 2: per-component padded lengths (multiples of 16)
     int G8, G;       // layout 2: face modes per tangent block, padded to 8 (trace buffer) and 16 (MMA)
+    int split;       // layout 1, fp16: two-term tables (hi + lo), two MMAs per table K-step
     int VPC;         // operand values per 16-byte chunk: 4 (TF32) or 8 (fp16)
     int KE, KH;      // padded fp32 state row lengths (multiples of 24): E, H
     int KEo, KHo;    // padded operand row lengths (whole MMA K-steps of 2 VPC): E, H
@@ -30,7 +31,7 @@ struct TCDims {
     int NCE;         // E-output columns (12 ceil(NE/4) padded to 16)
 };
 
-TCDims tc_dims(int NE, int NH, int N2H, bool f16);
+TCDims tc_dims(int NE, int NH, int N2H, bool f16, bool split = false);
 
 struct TCArgs {
     int64_t nt;
@@ -58,6 +59,7 @@ struct TCArgs {
     uint32_t stage_bytes;      // bytes of one ring stage
     uint32_t tmem_cols;        // TMEM columns allocated per CTA (power of two)
     uint32_t r2_offset;        // offset of the resident tile region
+    int64_t tab_lo;            // two-term tables: byte offset from each hi table to its lo table
     int stall_test;            // nonzero: the phase kernel waits on a barrier nothing arrives at,
                                // gives up after a short limit, records a timeout and does no work
     // layout 2 (resident-table kernels)
@@ -107,5 +109,7 @@ int tc_launch_pack(const double* src, float* dst, const double* nrm, int64_t nt,
 int tc_launch_unpack(const float* src, double* dst, const double* nrm, int64_t nt, int N, int K, cudaStream_t s);
 // fp32 -> fp16, round to nearest even (tables of the fp16 operand path)
 int tc_launch_to_half(const float* src, void* dst, size_t n, cudaStream_t s);
+// fp32 -> two fp16 terms: hi = fp16(x), lo = fp16(x - hi), both round to nearest even
+int tc_launch_split_half(const float* src, void* hi, void* lo, size_t n, cudaStream_t s);
 
 }  // namespace dgm

@@ -19,7 +19,7 @@ class Solver:
         opt = capi.dgm_default_options()
         opt.precision = {"fp64": capi.DGM_PREC_FP64, "fp32": capi.DGM_PREC_FP32,
                          "tc32": capi.DGM_PREC_TC32, "tc16": capi.DGM_PREC_TC16,
-                         "tcbf16": capi.DGM_PREC_TCBF16}[precision]
+                         "tcbf16": capi.DGM_PREC_TCBF16, "tc16x2": capi.DGM_PREC_TC16X2}[precision]
         opt.variant = variant
         opt.flux = {"central": capi.DGM_FLUX_CENTRAL, "stabilized": capi.DGM_FLUX_STABILIZED}[flux]
         opt.alpha0 = alpha0

@@ -34,7 +34,7 @@ def _solver(m, p, eps, precision):
     return Solver(m.xyz, m.tets, p, eps, 1.0, precision=precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16", "tc16x2"])
 def test_unstable_time_step_is_reported(capi, precision):
     m = kuhn_cube_mesh(3, jitter=0.1, seed=31)
     eps = np.random.default_rng(32).uniform(1, 4, m.nt)
@@ -53,7 +53,7 @@ def test_unstable_time_step_is_reported(capi, precision):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["tc32", "tc16", "tcbf16"])
+@pytest.mark.parametrize("precision", ["tc32", "tc16", "tcbf16", "tc16x2"])
 def test_injected_wait_timeout_is_reported_and_recovered(capi, precision):
     m = kuhn_cube_mesh(4, jitter=0.1, seed=41)          # 384 tets: 3 tiles
     eps = np.random.default_rng(42).uniform(1, 4, m.nt)

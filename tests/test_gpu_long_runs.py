@@ -18,6 +18,8 @@ Bounds, per precision (stated before the tests, from the arithmetic):
   TC32   dev_fp64 2e-2, drift 1e-4
   TC16   dev_fp64 2e-2, drift 1e-4
   TCBF16 dev_fp64 0.16, drift 8e-4 (bf16: 8 mantissa bits, 8x the rounding of fp16)
+  TC16X2 dev_fp64 5e-3, drift 1e-4 (two-term tables: the operator's own rounding,
+         which a halved time step showed to dominate TC16's 1.3e-2, nearly gone)
 The tensor-core operands carry 10 mantissa bits (unit roundoff 4.9e-4); a
 table entry's rounding perturbs the operator once (C_h and C_h^T stay exact
 transposes, so the scheme stays energy conserving), while the state's
@@ -32,8 +34,8 @@ from workloads.fields import plane_wave_fields
 
 pytestmark = pytest.mark.gpu
 
-BOUND_DEV = {"fp32": 1e-4, "tc32": 2e-2, "tc16": 2e-2, "tcbf16": 0.16}
-BOUND_DRIFT = {"fp64": 1e-11, "fp32": 1e-5, "tc32": 1e-4, "tc16": 1e-4, "tcbf16": 8e-4}
+BOUND_DEV = {"fp32": 1e-4, "tc32": 2e-2, "tc16": 2e-2, "tcbf16": 0.16, "tc16x2": 5e-3}
+BOUND_DRIFT = {"fp64": 1e-11, "fp32": 1e-5, "tc32": 1e-4, "tc16": 1e-4, "tcbf16": 8e-4, "tc16x2": 1e-4}
 
 
 def _log(name, **kw):
@@ -76,7 +78,7 @@ def runs():
     w = make_workload("planewave_n32_p6")
     m = w.mesh
     out = {}
-    for prec in ("fp64", "fp32", "tc32", "tc16", "tcbf16"):
+    for prec in ("fp64", "fp32", "tc32", "tc16", "tcbf16", "tc16x2"):
         S = Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=prec)
         _project(capi, S, w, 0.0, torch)
         W = S.run(w.dt, w.steps, energies=True)
@@ -107,7 +109,7 @@ def runs():
     return res
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16", "tc16x2"])
 def test_planewave_full_horizon(runs, precision):
     """planewave_n32_p6 over its stated 2,000 steps: deviation from the FP64 path,
     error against the analytic wave and energy drift within each precision's bound."""

@@ -17,7 +17,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc32", "tc16", "tcbf16", "tc16x2"])
 def test_energy_noalloc_matches_dgm_energy(precision):
     import torch
     if not torch.cuda.is_available():
