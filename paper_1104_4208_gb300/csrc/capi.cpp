@@ -125,6 +125,8 @@ void fill_params(dgm_problem* P, dgm::KParams<real>& K) {
     K.K = stab ? (real*)P->dK : nullptr;
     K.fgeo = P->dFaceGeo;
     K.fid = P->dFid;
+    K.trE = (real*)P->dTrE;
+    K.trH = (real*)P->dTrH;
 }
 
 int ensure_energy(dgm_problem* P, int64_t n) {
@@ -137,12 +139,73 @@ int ensure_energy(dgm_problem* P, int64_t n) {
     return DGM_OK;
 }
 
+// CUDA-core precisions with the central flux keep face-trace buffers: the phase
+// that updates a field writes its traces, the other phase reads them
+bool cc_buffered(const dgm_problem* P) { return !P->tc && P->dTrE != nullptr; }
+
+int cc_traces(dgm_problem* P, int which, int64_t e0, int64_t e1, cudaStream_t s) {
+    const int r = P->fp32 ? dgm::launch_traces2<float>(P->kf, P->grid, which, e0, e1, s)
+                          : dgm::launch_traces2<double>(P->kd, P->grid, which, e0, e1, s);
+    return r ? cuda_fail(cudaGetLastError(), "traces launch") : DGM_OK;
+}
+
+// E traces current before an H-phase: all elements if invalid, else the blocks of
+// 128 elements that point sources changed
+int cc_ensure_traces_E(dgm_problem* P, cudaStream_t s) {
+    int rc = DGM_OK;
+    if (!P->trE_valid) {
+        rc = cc_traces(P, 0, 0, P->nt, s);
+    } else {
+        for (int i = 0; i < P->trE_ndirty && !rc; ++i) {
+            const int64_t e0 = (int64_t)P->trE_dirty[i] * dgm::kTcRows;
+            rc = cc_traces(P, 0, e0, std::min<int64_t>(P->nt, e0 + dgm::kTcRows), s);
+        }
+    }
+    if (rc) return rc;
+    P->trE_valid = true;
+    P->trE_ndirty = 0;
+    return DGM_OK;
+}
+
+int cc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* partials, cudaStream_t s) {
+    if (!cc_buffered(P)) {
+        const int r = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
+                              : dgm::launch_phase_H<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s);
+        return r ? cuda_fail(cudaGetLastError(), "H-phase launch") : DGM_OK;
+    }
+    int rc = cc_ensure_traces_E(P, s);
+    if (rc) return rc;
+    const int r = P->fp32 ? dgm::launch_phase_H2<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
+                          : dgm::launch_phase_H2<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s);
+    if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
+    P->trH_valid = true;
+    return DGM_OK;
+}
+
+int cc_phase_E(dgm_problem* P, double dt, cudaStream_t s) {
+    if (!cc_buffered(P)) {
+        const int r = P->fp32 ? dgm::launch_phase_E<float>(P->kf, P->grid, dt, s)
+                              : dgm::launch_phase_E<double>(P->kd, P->grid, dt, s);
+        return r ? cuda_fail(cudaGetLastError(), "E-phase launch") : DGM_OK;
+    }
+    if (!P->trH_valid) {
+        int rc = cc_traces(P, 1, 0, P->nt, s);
+        if (rc) return rc;
+        P->trH_valid = true;
+    }
+    const int r = P->fp32 ? dgm::launch_phase_E2<float>(P->kf, P->grid, dt, s)
+                          : dgm::launch_phase_E2<double>(P->kd, P->grid, dt, s);
+    if (r) return cuda_fail(cudaGetLastError(), "E-phase launch");
+    P->trE_valid = true;
+    P->trE_ndirty = 0;
+    return DGM_OK;
+}
+
 int phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy_slot, cudaStream_t s) {
     if (P->tc) return dgm::tc_phase_H(P, dt, a_lo, c_out, energy_slot, s);
     double* partials = energy_slot ? P->dPartials : nullptr;
-    int rc = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
-                     : dgm::launch_phase_H<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s);
-    if (rc) return cuda_fail(cudaGetLastError(), "H-phase launch");
+    int rc = cc_phase_H(P, dt, a_lo, c_out, partials, s);
+    if (rc) return rc;
     if (energy_slot && dgm::launch_energy_reduce(P->dPartials, P->grid, energy_slot, s))
         return cuda_fail(cudaGetLastError(), "energy reduce launch");
     return DGM_OK;
@@ -150,14 +213,13 @@ int phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* energy
 
 int phase_E(dgm_problem* P, double dt, cudaStream_t s, bool energy = false) {
     if (P->tc) return dgm::tc_phase_E(P, dt, energy, s);
-    int rc = P->fp32 ? dgm::launch_phase_E<float>(P->kf, P->grid, dt, s)
-                     : dgm::launch_phase_E<double>(P->kd, P->grid, dt, s);
-    if (rc) return cuda_fail(cudaGetLastError(), "E-phase launch");
-    return DGM_OK;
+    return cc_phase_E(P, dt, s);
 }
 
 int import_fields(dgm_problem* P, const double* dEsrc, const double* dHsrc, cudaStream_t s) {
     if (P->tc) return dgm::tc_import(P, dEsrc, dHsrc, P->dNrmE, P->dNrmH, s);
+    if (dEsrc) P->trE_valid = false;
+    if (dHsrc) P->trH_valid = false;
     const int64_t nE = P->nt * 3 * P->NE, nH = P->nt * 3 * P->NH;
     int rc = 0;
     if (P->fp32) {
@@ -201,7 +263,7 @@ int export_fields(dgm_problem* P, double* dEdst, double* dHdst, cudaStream_t s) 
 void free_problem(dgm_problem* P) {
     void* ptrs[] = {P->dE, P->dH, P->dTables, P->dGeo, P->dNbr, P->dNrmE, P->dNrmH,
                     P->dPartials, P->dEnergy, P->dStage, P->dMaps, P->dWphiE, P->dWphiH, P->dPhiE, P->dPhiH,
-                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF, P->dSrc, P->dSrcF};
+                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF, P->dSrc, P->dSrcF, P->dTrE, P->dTrH};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->tc) dgm::tc_problem_free(P);
@@ -418,6 +480,15 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         for (int g = 0; g < P->N2E; ++g) nrmF[g] = std::sqrt(dgm::dubiner2_norm2(i2[2 * g], i2[2 * g + 1]));
         if ((e = cudaMalloc(&P->dNrmF, P->N2E * sizeof(double))) != cudaSuccess) return fail(cuda_fail(e, "alloc nrm"));
         cudaMemcpy(P->dNrmF, nrmF.data(), P->N2E * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (!tc && !stab) {
+        // tangential face-trace buffers of the trace-buffer phase kernels
+        const size_t nTr = (size_t)m.nt * 8 * P->N2H;
+        if ((e = cudaMalloc(&P->dTrE, nTr * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc traces"));
+        if ((e = cudaMalloc(&P->dTrH, nTr * rs)) != cudaSuccess) return fail(cuda_fail(e, "alloc traces"));
+        cudaMemset(P->dTrE, 0, nTr * rs);
+        cudaMemset(P->dTrH, 0, nTr * rs);
+        P->trE_valid = P->trH_valid = false;
     }
     if ((e = cudaMalloc(&P->dStage, std::max(std::max(nE, nH), nK) * sizeof(double))) != cudaSuccess)
         return fail(cuda_fail(e, "alloc staging"));
@@ -680,9 +751,7 @@ int dgm_run_timed(dgm_problem* P, double dt, int64_t nsteps, void* stream, doubl
             }
             return DGM_OK;
         }
-        r = P->fp32 ? dgm::launch_phase_H<float>(P->kf, P->grid, dt, a_lo, c_out, slot ? P->dPartials : nullptr, s)
-                    : dgm::launch_phase_H<double>(P->kd, P->grid, dt, a_lo, c_out, slot ? P->dPartials : nullptr, s);
-        if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
+        if ((r = cc_phase_H(P, dt, a_lo, c_out, slot ? P->dPartials : nullptr, s))) return r;
         if ((r = done())) return r;
         if (slot) {
             if ((r = mark(2))) return r;
@@ -882,10 +951,8 @@ int apply_source(dgm_problem* P, void* E, int64_t n, double dt, cudaStream_t s) 
                                                      P->dSrcF, n, dt, s)
                       : dgm::add_point_source<double>((double*)E, P->NE, K, tiled, P->src_elem, P->dSrc + 3, P->dSrc,
                                                       P->dSrcF, n, dt, s);
-    if (P->tc) {
-        // the source changes E in one element: only its tile's E traces are stale
-        dgm::tc_mark_tile_dirty(P, P->src_elem / dgm::kTcRows);
-    }
+    // the source changes E in one element: only its block's E traces are stale
+    dgm::tc_mark_tile_dirty(P, P->src_elem / dgm::kTcRows);
     return r ? cuda_fail(cudaGetLastError(), "source launch") : DGM_OK;
 }
 
@@ -1318,8 +1385,7 @@ int dgm_adjoint_grad(dgm_problem* P, double dt, int64_t nsteps, int nobs, const 
             int r = v.f32 ? dgm::adj_source<float>(O, (const float*)Em, (float*)aE, N, K, tiled, 0)
                           : dgm::adj_source<double>(O, (const double*)Em, (double*)aE, N, K, tiled, 0);
             // the observation sources change e^ only in the observed elements' tiles
-            if (P->tc)
-                for (int o = 0; o < nobs; ++o) dgm::tc_mark_tile_dirty(P, oe[o] / dgm::kTcRows);
+            for (int o = 0; o < nobs; ++o) dgm::tc_mark_tile_dirty(P, oe[o] / dgm::kTcRows);
             r |= v.f32 ? dgm::adj_grad<float>(P->nt, geo, (const float*)aE, (const float*)Em, (const float*)Emm, N,
                                               K, tiled, dGrad, 0)
                        : dgm::adj_grad<double>(P->nt, geo, (const double*)aE, (const double*)Em, (const double*)Emm,
@@ -1564,7 +1630,7 @@ namespace {
 // must have been prepared.  Energies (optional) go to the problem's device array.
 int enqueue_run(dgm_problem* P, double dt, int64_t nsteps, cudaStream_t s, bool want) {
     double* W = P->dEnergy;
-    if (P->tc) P->trE_valid = false;   // the first H-phase recomputes E traces (and E^0's energy)
+    P->trE_valid = false;   // the first H-phase recomputes E traces (tensor cores: and E^0's energy)
     int rc = phase_H(P, dt, 0.5, 0.5, want ? W : nullptr, s);
     for (int64_t n = 0; n < nsteps && !rc; ++n) {
         rc = phase_E(P, dt, s, want);
@@ -1790,6 +1856,8 @@ int dgm_project_device(dgm_problem* P, int q1d, const double* E_pts, const doubl
         }
         return r ? cuda_fail(cudaGetLastError(), "project") : DGM_OK;
     }
+    if (E_pts) P->trE_valid = false;
+    if (H_pts) P->trH_valid = false;
     if (P->fp32) {
         if (E_pts) r |= dgm::launch_project<float>(P->nt, P->NE, nq, P->dMaps, P->dWphiE, E_pts, (float*)P->dE, s);
         if (H_pts) r |= dgm::launch_project<float>(P->nt, P->NH, nq, P->dMaps, P->dWphiH, H_pts, (float*)P->dH, s);

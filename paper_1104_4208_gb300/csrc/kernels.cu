@@ -538,7 +538,280 @@ int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// Trace-buffer phase kernels (central flux).  The kernels above recompute, per
+// element and face, the neighbour's trace from the neighbour's coefficients:
+// every face trace is computed twice per phase.  Here the phase that updates a
+// field also writes that field's tangential face traces (degree <= p-1 face
+// modes, the only ones the central flux needs, Sec. 3.2.3) once per element
+// into a buffer, and the other phase reads its own and its neighbours' traces
+// from there.  Lanes run over (face, face mode) pairs -- 4 N2(p-1) of them --
+// for the flux and the traces, and over coefficients for curl, lift and update.
+// The traces are the same sums in the same order as above.
+
+namespace {
+
+// tangential traces J_i = sum_m t_{f,i,m} sum_a Tr_f[g, a] X_m[a] of the field
+// staged in sX [3][N] (one warp), TT = [4][N][N2H] -> row [4][2][N2H]
+template <typename real>
+__device__ void warp_traces(const real* sX, int N, const real* __restrict__ TT, int N2H, real* row, int lane) {
+    for (int item = lane; item < 4 * N2H; item += 32) {
+        const int f = item / N2H, gm = item - f * N2H;
+        const real* T = TT + (size_t)f * N * N2H + gm;
+        real t0 = 0, t1 = 0, t2 = 0;
+        for (int a = 0; a < N; ++a) {
+            const real w = ld(T + (size_t)a * N2H);
+            t0 += w * sX[a];
+            t1 += w * sX[N + a];
+            t2 += w * sX[2 * N + a];
+        }
+        row[(2 * f) * N2H + gm] = (real)c_that[f][0][0] * t0 + (real)c_that[f][0][1] * t1 + (real)c_that[f][0][2] * t2;
+        row[(2 * f + 1) * N2H + gm] =
+            (real)c_that[f][1][0] * t0 + (real)c_that[f][1][1] * t1 + (real)c_that[f][1][2] * t2;
+    }
+}
+
+// flux values of the element's four faces from the trace buffer tr: jump
+// (1/2) sigma_f (J - K) for the H-phase, average (1/2) sigma_f (J + K) for the
+// E-phase; PEC faces use the ghost state (sigma_f J)
+template <typename real, bool JUMP>
+__device__ void warp_flux(const real* __restrict__ tr, const int32_t* __restrict__ nbr, int64_t t, double sT, int N2H,
+                          real* sF, int lane) {
+    for (int item = lane; item < 4 * N2H; item += 32) {
+        const int f = item / N2H, gm = item - f * N2H;
+        const int32_t nb = nbr[t * 4 + f];
+        const double sig = sT * c_sigma_hat[f];
+        const real* own = tr + (t * 4 + f) * 2 * N2H;
+        const real J0 = own[gm], J1 = own[N2H + gm];
+        real a0, a1;
+        if (nb >= 0) {
+            const real* nbt = tr + ((int64_t)(nb >> 2) * 4 + (nb & 3)) * 2 * N2H;
+            const real K0 = nbt[gm], K1 = nbt[N2H + gm];
+            a0 = (real)(0.5 * sig) * (JUMP ? J0 - K0 : J0 + K0);
+            a1 = (real)(0.5 * sig) * (JUMP ? J1 - K1 : J1 + K1);
+        } else {
+            a0 = (real)sig * J0;
+            a1 = (real)sig * J1;
+        }
+        sF[(2 * f) * N2H + gm] = a0;
+        sF[(2 * f + 1) * N2H + gm] = a1;
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kWarps * 32)
+k_phase_H2(KParams<real> P, double dt, double a_lo, double c_out, double* __restrict__ partials) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int NE = P.NE, NH = P.NH, N2H = P.N2H;
+    real* sE = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
+    real* sA = sE + 3 * NE;
+    real* sHn = sA + 8 * N2H;
+    double eacc = 0.0;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + wib; t < P.nt; t += nwarps) {
+        const real* Et = P.E + t * 3 * NE;
+        for (int k = lane; k < 3 * NE; k += 32) sE[k] = Et[k];
+        const double* g = P.geo + t * kGeoStride;
+        const double sT = g[kGeoSign];
+        warp_flux<real, true>(P.trE, P.nbr, t, sT, N2H, sA, lane);
+        __syncwarp();
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double gm6[6] = {g[6], g[7], g[8], g[9], g[10], g[11]};
+        const double inv_mu = g[kGeoInvMu], mu = g[kGeoMu];
+        real* Ht = P.H + t * 3 * NH;
+        for (int b = lane; b < NH; b += 32) {
+            real cx = 0, cy = 0, cz = 0;
+            const real* Dx = P.DT + b;
+            const real* Dy = Dx + (size_t)NE * NH;
+            const real* Dz = Dy + (size_t)NE * NH;
+            for (int a = 0; a < NE; ++a) {
+                const real dx = ld(Dx + (size_t)a * NH), dy = ld(Dy + (size_t)a * NH), dz = ld(Dz + (size_t)a * NH);
+                const real ex = sE[a], ey = sE[NE + a], ez = sE[2 * NE + a];
+                cx += dy * ez - dz * ey;
+                cy += dz * ex - dx * ez;
+                cz += dx * ey - dy * ex;
+            }
+            real r0 = -(real)sT * cx, r1 = -(real)sT * cy, r2 = -(real)sT * cz;
+            for (int f = 0; f < 4; ++f) {
+                const real* L = P.TrH + (size_t)f * N2H * NH + b;
+                const real* A0 = sA + (2 * f) * N2H;
+                const real* A1 = A0 + N2H;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < N2H; ++gm) {
+                    const real l = ld(L + (size_t)gm * NH);
+                    u0 += l * A0[gm];
+                    u1 += l * A1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real s = (real)(dt * inv_mu);
+            const real d0 = s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real d1 = s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real d2 = s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            const real h0 = Ht[b], h1 = Ht[NH + b], h2 = Ht[2 * NH + b];
+            if (partials) {
+                const double l0 = (double)h0 - a_lo * (double)d0, l1 = (double)h1 - a_lo * (double)d1,
+                             l2 = (double)h2 - a_lo * (double)d2;
+                const double u0 = l0 + (double)d0, u1 = l1 + (double)d1, u2 = l2 + (double)d2;
+                eacc += 0.5 * mu *
+                        (l0 * (gm6[0] * u0 + gm6[1] * u1 + gm6[2] * u2) + l1 * (gm6[1] * u0 + gm6[3] * u1 + gm6[4] * u2) +
+                         l2 * (gm6[2] * u0 + gm6[4] * u1 + gm6[5] * u2));
+            }
+            const real n0 = h0 + (real)c_out * d0, n1 = h1 + (real)c_out * d1, n2 = h2 + (real)c_out * d2;
+            Ht[b] = n0;
+            Ht[NH + b] = n1;
+            Ht[2 * NH + b] = n2;
+            sHn[b] = n0;
+            sHn[NH + b] = n1;
+            sHn[2 * NH + b] = n2;
+        }
+        if (partials) {
+            const double eps = g[kGeoEps];
+            for (int a = lane; a < NE; a += 32) {
+                const double e0 = sE[a], e1 = sE[NE + a], e2 = sE[2 * NE + a];
+                eacc += 0.5 * eps *
+                        (e0 * (gm6[0] * e0 + gm6[1] * e1 + gm6[2] * e2) + e1 * (gm6[1] * e0 + gm6[3] * e1 + gm6[4] * e2) +
+                         e2 * (gm6[2] * e0 + gm6[4] * e1 + gm6[5] * e2));
+            }
+        }
+        __syncwarp();
+        warp_traces(sHn, NH, P.TrHT, N2H, P.trH + t * 8 * N2H, lane);
+        __syncwarp();
+    }
+    if (partials) block_energy_store(eacc, partials);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kWarps * 32)
+k_phase_E2(KParams<real> P, double dt) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int NE = P.NE, NH = P.NH, N2H = P.N2H;
+    real* sH = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
+    real* sB = sH + 3 * NH;
+    real* sEn = sB + 8 * N2H;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + wib; t < P.nt; t += nwarps) {
+        const real* Ht = P.H + t * 3 * NH;
+        for (int k = lane; k < 3 * NH; k += 32) sH[k] = Ht[k];
+        const double* g = P.geo + t * kGeoStride;
+        const double sT = g[kGeoSign];
+        warp_flux<real, false>(P.trH, P.nbr, t, sT, N2H, sB, lane);
+        __syncwarp();
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double inv_eps = g[kGeoInvEps];
+        real* Et = P.E + t * 3 * NE;
+        for (int a = lane; a < NE; a += 32) {
+            real rx = 0, ry = 0, rz = 0;
+            const real* Dx = P.D + a;
+            const real* Dy = Dx + (size_t)NH * NE;
+            const real* Dz = Dy + (size_t)NH * NE;
+            for (int b = 0; b < NH; ++b) {
+                const real dx = ld(Dx + (size_t)b * NE), dy = ld(Dy + (size_t)b * NE), dz = ld(Dz + (size_t)b * NE);
+                const real hx = sH[b], hy = sH[NH + b], hz = sH[2 * NH + b];
+                rx += dz * hy - dy * hz;
+                ry += dx * hz - dz * hx;
+                rz += dy * hx - dx * hy;
+            }
+            real r0 = (real)sT * rx, r1 = (real)sT * ry, r2 = (real)sT * rz;
+            for (int f = 0; f < 4; ++f) {
+                const real* L = P.TrEq + (size_t)f * N2H * NE + a;
+                const real* B0 = sB + (2 * f) * N2H;
+                const real* B1 = B0 + N2H;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < N2H; ++gm) {
+                    const real l = ld(L + (size_t)gm * NE);
+                    u0 += l * B0[gm];
+                    u1 += l * B1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real s = (real)(dt * inv_eps);
+            const real n0 = Et[a] + s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real n1 = Et[NE + a] + s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real n2 = Et[2 * NE + a] + s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            Et[a] = n0;
+            Et[NE + a] = n1;
+            Et[2 * NE + a] = n2;
+            sEn[a] = n0;
+            sEn[NE + a] = n1;
+            sEn[2 * NE + a] = n2;
+        }
+        __syncwarp();
+        warp_traces(sEn, NE, P.TrEqT, N2H, P.trE + t * 8 * N2H, lane);
+        __syncwarp();
+    }
+}
+
+// traces of the current E (which = 0) or H (which = 1) of elements [e0, e1)
+template <typename real>
+__global__ void __launch_bounds__(kWarps * 32) k_traces2(KParams<real> P, int which, int64_t e0, int64_t e1) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int N = which == 0 ? P.NE : P.NH, N2H = P.N2H;
+    real* sX = reinterpret_cast<real*>(smem_raw) + (size_t)wib * P.warp_smem;
+    const real* X = which == 0 ? P.E : P.H;
+    real* tr = which == 0 ? P.trE : P.trH;
+    const real* TT = which == 0 ? P.TrEqT : P.TrHT;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t t = e0 + (int64_t)blockIdx.x * kWarps + wib; t < e1; t += nwarps) {
+        const real* Xt = X + t * 3 * N;
+        for (int k = lane; k < 3 * N; k += 32) sX[k] = Xt[k];
+        __syncwarp();
+        warp_traces(sX, N, TT, N2H, tr + t * 8 * N2H, lane);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
 int phase_warps_per_block() { return kWarps; }
+
+template <typename real>
+int launch_phase_H2(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
+                    cudaStream_t s) {
+    const size_t smem = phase_smem_bytes(P);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_phase_H2<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_phase_H2<real><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_phase_E2(const KParams<real>& P, int grid, double dt, cudaStream_t s) {
+    const size_t smem = phase_smem_bytes(P);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_phase_E2<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_phase_E2<real><<<grid, kWarps * 32, smem, s>>>(P, dt);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_traces2(const KParams<real>& P, int grid, int which, int64_t e0, int64_t e1, cudaStream_t s) {
+    if (e1 <= e0) return 0;
+    const int64_t need = (e1 - e0 + kWarps - 1) / kWarps;
+    const int g = (int)(need < grid ? need : grid);
+    const size_t smem = phase_smem_bytes(P);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_traces2<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_traces2<real><<<g, kWarps * 32, smem, s>>>(P, which, e0, e1);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template int launch_phase_H2<double>(const KParams<double>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_H2<float>(const KParams<float>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_E2<double>(const KParams<double>&, int, double, cudaStream_t);
+template int launch_phase_E2<float>(const KParams<float>&, int, double, cudaStream_t);
+template int launch_traces2<double>(const KParams<double>&, int, int, int64_t, int64_t, cudaStream_t);
+template int launch_traces2<float>(const KParams<float>&, int, int, int64_t, int64_t, cudaStream_t);
 
 template int launch_phase_H<double>(const KParams<double>&, int, double, double, double, double*, cudaStream_t);
 template int launch_phase_H<float>(const KParams<float>&, int, double, double, double, double*, cudaStream_t);

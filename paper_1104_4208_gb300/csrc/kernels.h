@@ -36,6 +36,11 @@ struct KParams {
     const int32_t* fid;         // [nt][4] = 2*face + (1 if this element side updates the face)
     const real* TrEfT;          // [4][NE][N2E]  E trace onto all degree <= p face modes, transposed
     const real* TrEf;           // [4][N2E][NE]
+    // central flux, trace-buffer kernels: tangential face traces of E and H on the
+    // degree <= p-1 face modes, [nt][4 faces][2 tangents][N2H], written by the phase
+    // that updates the field and read (own and neighbour side) by the other phase
+    real* trE;
+    real* trH;
 };
 
 // Per-face record of the stabilized flux (FP64), kFaceGeoStride doubles:
@@ -63,6 +68,16 @@ template <typename real>
 int launch_eval(int64_t nt, int N, int nq, const double* maps, const double* phi, const real* c, double* pts,
                 cudaStream_t s);
 int launch_energy_reduce(const double* partials, int n, double* out, cudaStream_t s);
+// trace-buffer phase kernels (central flux): as launch_phase_H / _E, reading the other
+// field's traces from its buffer and writing the traces of the updated field
+template <typename real>
+int launch_phase_H2(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
+                    cudaStream_t s);
+template <typename real>
+int launch_phase_E2(const KParams<real>& P, int grid, double dt, cudaStream_t s);
+// traces of the current E (which = 0) or H (which = 1) of elements [e0, e1) into the buffer
+template <typename real>
+int launch_traces2(const KParams<real>& P, int grid, int which, int64_t e0, int64_t e1, cudaStream_t s);
 template <typename real>
 int launch_axpby(int64_t n, double a, const real* x, double b, real* y, cudaStream_t s);
 int phase_warps_per_block();

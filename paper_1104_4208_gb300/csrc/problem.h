@@ -52,12 +52,17 @@ struct dgm_problem {
     double* dFaceGeo = nullptr;          // [nfaces][kFaceGeoStride]
     int32_t* dFid = nullptr;             // [nt][4]
     double* dNrmF = nullptr;             // [N2E] ||psi_g||
+    // CUDA-core precisions, central flux: tangential face-trace buffers of E and H
+    // ([nt][4][2][N2(p-1)]), valid per the trE_valid / trH_valid flags below
+    void* dTrE = nullptr;
+    void* dTrH = nullptr;
     // tensor-core path (precisions TC32, TC16)
     bool tc = false;
     int tc_grid = 0;                     // CTAs of the tensor-core kernels (autotuned)
     int tc_grid_cap = 0;                 // largest tc_grid the partial sums are sized for
-    // with trE_valid: tiles whose E traces are stale (point sources, adjoint observation
-    // sources); more than kMaxDirtyTiles of them clear trE_valid instead (one-tile
+    // with trE_valid: tiles (blocks of 128 elements) whose E traces are stale (point
+    // sources, adjoint observation sources); more than kMaxDirtyTiles of them clear
+    // trE_valid instead (one-tile
     // refreshes are separate launches: beyond two, one pass over all tiles was faster
     // on a 192-tile mesh)
     static constexpr int kMaxDirtyTiles = 2;
