@@ -459,6 +459,11 @@ def run_gpu(args, rank, world, local):
         S.close()
         S64 = make_solver(w, "fp64")
         project_initial(S64, w, torch, q1d)
+        tune64 = None
+        if not args.no_autotune:   # the FP64 path in its own fastest configuration (dense or sparse curl)
+            cfg64, tms64, ch64 = S64.autotune(2)
+            tune64 = {"per_sm": cfg64, "ms_per_step": [round(x, 3) for x in tms64], "chosen": cfg64[ch64],
+                      "note": "configurations >= 1000: sparse curl, blocks per SM = value - 1000"}
         ms64, st64, W64 = timed_run(S64, torch, dt, args.steps, args.warmup)
         v64 = world * dofs * args.steps / (dist_max(ms64) * 1e-3)
         kept64 = []
@@ -469,7 +474,7 @@ def run_gpu(args, rank, world, local):
         fp64 = {"value": v64, "ms_per_step": ms64 / args.steps, "speedup_of_mixed": value / v64,
                 "energy_drift": float(np.abs(W64 - W64[0]).max() / W64[0]),
                 "l2_rel_E_vs_analytic": err64, "mixed_minus_fp64_l2_rel": dev,
-                "roofline": alu_roofline(w, ms64 / args.steps, local)}
+                "roofline": alu_roofline(w, ms64 / args.steps, local), "launch": tune64}
         S64.close()
         S = make_solver(w, args.precision, args.variant)
         project_initial(S, w, torch, q1d)

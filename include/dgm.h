@@ -111,7 +111,10 @@ typedef struct dgm_options {
     int flux;           /* dgm_flux */
     double alpha0;      /* alpha = alpha0 * p^2 (Sec. 2.1: alpha grows like p^2) */
     int precision;      /* dgm_precision */
-    int variant;        /* 0 = automatic kernel choice; TC16 only: 1 = dense-operator kernels */
+    int variant;        /* 0 = automatic kernel choice (dgm_autotune may change it);
+                           TC16: 1 = dense-operator kernels; FP64/FP32 with the central flux:
+                           1 = dense curl, 2 = sparse curl (the exact zeros of D_x, D_y, D_z
+                           skipped, Sec. 4.2.2) */
     int checks;         /* reserved: accepted, no effect.  Inputs are always validated at
                            creation; an unstable dt shows as DGM_ERR_UNSTABLE from the energy
                            watchdog of dgm_run (energies requested), and dgm_estimate_dt
@@ -250,12 +253,16 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * after one warm-up step) on this problem's own fields with dt = 0, which
  * leaves the fields unchanged; the fastest is kept for all later calls.
  * Candidates: CUDA-core kernels (FP64, FP32) -- 4, 8, 16 or 24 blocks per SM;
+ * with the central flux and variant 0 each also with the sparse curl, reported
+ * as 1000 + blocks per SM (the dense and the sparse curl sum the same nonzero
+ * products in different orders: fields then agree to round-off, not bitwise);
  * dense-operator tensor-core kernels (TC32, TC16X2, TC16 variant 1) -- 1 or 2 CTAs per
  * SM (2 only where the TMEM columns and shared memory of a CTA allow it);
  * resident-table tensor-core kernels (TC16, TCBF16) -- one configuration
- * (one CTA per SM), timed and reported like the others.  Every candidate computes
- * each element with the same operations, so the fields of later runs do not
- * depend on the choice; the energy's last bits can (block partial sums).
+ * (one CTA per SM), timed and reported like the others.  Candidates that differ
+ * only in launch shape compute each element with the same operations, so the
+ * fields of later runs do not depend on that choice; the energy's last bits can
+ * (block partial sums).
  * Outputs (nullable): *ncand (<= DGM_AUTOTUNE_MAX), per candidate its
  * configuration value (blocks or CTAs per SM) and ms per step, and the index
  * of the chosen one.  Errors: DGM_ERR_INVALID_ARG for steps < 1. */

@@ -95,8 +95,55 @@ int upload_tables(dgm_problem* P, dgm::KParams<real>& K) {
                     TrEf[(size_t)f * N2E * NE + (size_t)g * NE + a] = v;
                 }
     }
+    // sparse form of D_x, D_y, D_z (exact zeros skipped) for the sparse-curl kernels:
+    // rows b for the H-phase, columns a for the E-phase
+    std::vector<int32_t> ptrH(3 * (NH + 1)), ptrE(3 * (NE + 1)), idxH, idxE;
+    std::vector<real> valH, valE;
+    for (int d = 0; d < 3; ++d) {
+        for (int b = 0; b < NH; ++b) {
+            ptrH[d * (NH + 1) + b] = (int32_t)idxH.size();
+            for (int a = 0; a < NE; ++a)
+                if (t.D[d][(size_t)b * NE + a] != 0.0) {
+                    idxH.push_back(a);
+                    valH.push_back((real)t.D[d][(size_t)b * NE + a]);
+                }
+        }
+        ptrH[d * (NH + 1) + NH] = (int32_t)idxH.size();
+        for (int a = 0; a < NE; ++a) {
+            ptrE[d * (NE + 1) + a] = (int32_t)idxE.size();
+            for (int b = 0; b < NH; ++b)
+                if (t.D[d][(size_t)b * NE + a] != 0.0) {
+                    idxE.push_back(b);
+                    valE.push_back((real)t.D[d][(size_t)b * NE + a]);
+                }
+        }
+        ptrE[d * (NE + 1) + NE] = (int32_t)idxE.size();
+    }
+    const size_t nI = ptrH.size() + ptrE.size() + idxH.size() + idxE.size();
+    const size_t nIr = (nI * sizeof(int32_t) + sizeof(real) - 1) / sizeof(real);   // ints, in reals
+    const size_t o_sp = buf.size();
+    buf.resize(o_sp + nIr + valH.size() + valE.size());
+    {
+        int32_t* ip = reinterpret_cast<int32_t*>(buf.data() + o_sp);
+        for (auto* v : {&ptrH, &ptrE, &idxH, &idxE}) {
+            std::copy(v->begin(), v->end(), ip);
+            ip += v->size();
+        }
+        std::copy(valH.begin(), valH.end(), buf.begin() + (o_sp + nIr));
+        std::copy(valE.begin(), valE.end(), buf.begin() + (o_sp + nIr + valH.size()));
+    }
     DGM_CUDA(cudaMalloc(&P->dTables, buf.size() * sizeof(real)));
     DGM_CUDA(cudaMemcpy(P->dTables, buf.data(), buf.size() * sizeof(real), cudaMemcpyHostToDevice));
+    {
+        const int32_t* ib = reinterpret_cast<const int32_t*>((real*)P->dTables + o_sp);
+        K.ptrH = ib;
+        K.ptrE = ib + ptrH.size();
+        K.idxH = ib + ptrH.size() + ptrE.size();
+        K.idxE = K.idxH + idxH.size();
+        K.valH = (real*)P->dTables + o_sp + nIr;
+        K.valE = K.valH + valH.size();
+        K.sparse = P->opt.variant == 2 ? 1 : 0;
+    }
     real* base = (real*)P->dTables;
     K.DT = base;
     K.D = base + nD;
@@ -371,9 +418,16 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         set_error("dgm_problem_create: unknown precision");
         return DGM_ERR_INVALID_ARG;
     }
-    if (o.variant != 0 && !(o.variant == 1 && o.precision == DGM_PREC_TC16)) {
-        set_error("dgm_problem_create: variant 1 (dense-operator kernels) exists for TC16 only; else use 0");
-        return DGM_ERR_INVALID_ARG;
+    {
+        const bool cc_central = (o.precision == DGM_PREC_FP64 || o.precision == DGM_PREC_FP32) &&
+                                o.flux == DGM_FLUX_CENTRAL;
+        const bool ok = o.variant == 0 || (o.variant == 1 && (o.precision == DGM_PREC_TC16 || cc_central)) ||
+                        (o.variant == 2 && cc_central);
+        if (!ok) {
+            set_error("dgm_problem_create: variant 1 exists for TC16 and for FP64/FP32 with the central flux, "
+                      "variant 2 for FP64/FP32 with the central flux; else use 0");
+            return DGM_ERR_INVALID_ARG;
+        }
     }
     const dgm::MeshData& m = mesh->m;
     for (int64_t t = 0; t < m.nt; ++t)
@@ -1073,7 +1127,13 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
         cand.push_back(1);
         if (P->tc_grid_cap > sms) cand.push_back(2);   // two CTAs per SM allowed
     } else {
-        for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b);
+        // trace-buffer kernels: the dense and the sparse curl (configuration + 1000)
+        // are timed unless the variant option fixed one
+        const bool both = cc_buffered(P) && P->opt.variant == 0;
+        const int fixed = cc_buffered(P) && P->opt.variant == 2 ? 1000 : 0;
+        for (int v : {0, 1000})
+            if (both || v == fixed)
+                for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b + v);
     }
     auto apply = [&](int c) {
         if (resident) {
@@ -1082,10 +1142,11 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
             P->tc_grid = std::min(P->tc_grid_cap, sms * c);
             P->tca.partH = P->tca.partE + P->tc_grid;   // the reduction sums 2 tc_grid contiguous partials
         } else {
-            P->grid = std::min(P->grid_cap, sms * c);
+            P->grid = std::min(P->grid_cap, sms * (c % 1000));
+            P->kd.sparse = P->kf.sparse = c >= 1000 ? 1 : 0;
         }
     };
-    const int keep_grid = P->grid, keep_tc = P->tc_grid;
+    const int keep_grid = P->grid, keep_tc = P->tc_grid, keep_sparse = P->kd.sparse | P->kf.sparse;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DGM_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1114,6 +1175,7 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
     if (rc) {
         P->grid = keep_grid;
         P->tc_grid = keep_tc;
+        P->kd.sparse = P->kf.sparse = keep_sparse;
         if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
         return rc;
     }

@@ -598,7 +598,7 @@ __device__ void warp_flux(const real* __restrict__ tr, const int32_t* __restrict
     }
 }
 
-template <typename real>
+template <typename real, bool SPARSE>
 __global__ void __launch_bounds__(kWarps * 32)
 k_phase_H2(KParams<real> P, double dt, double a_lo, double c_out, double* __restrict__ partials) {
     extern __shared__ unsigned char smem_raw[];
@@ -623,15 +623,38 @@ k_phase_H2(KParams<real> P, double dt, double a_lo, double c_out, double* __rest
         real* Ht = P.H + t * 3 * NH;
         for (int b = lane; b < NH; b += 32) {
             real cx = 0, cy = 0, cz = 0;
-            const real* Dx = P.DT + b;
-            const real* Dy = Dx + (size_t)NE * NH;
-            const real* Dz = Dy + (size_t)NE * NH;
-            for (int a = 0; a < NE; ++a) {
-                const real dx = ld(Dx + (size_t)a * NH), dy = ld(Dy + (size_t)a * NH), dz = ld(Dz + (size_t)a * NH);
-                const real ex = sE[a], ey = sE[NE + a], ez = sE[2 * NE + a];
-                cx += dy * ez - dz * ey;
-                cy += dz * ex - dx * ez;
-                cz += dx * ey - dy * ex;
+            if (SPARSE) {
+                // the nonzeros of row b of D_x, D_y, D_z (Sec. 4.2.2: each derivative of
+                // a Dubiner function has few components): curl = (D_y e_z - D_z e_y, ...)
+                for (int k = ld(P.ptrH + b), k1 = ld(P.ptrH + b + 1); k < k1; ++k) {
+                    const int a = ld(P.idxH + k);
+                    const real v = ld(P.valH + k);
+                    cy -= v * sE[2 * NE + a];
+                    cz += v * sE[NE + a];
+                }
+                for (int k = ld(P.ptrH + (NH + 1) + b), k1 = ld(P.ptrH + (NH + 1) + b + 1); k < k1; ++k) {
+                    const int a = ld(P.idxH + k);
+                    const real v = ld(P.valH + k);
+                    cx += v * sE[2 * NE + a];
+                    cz -= v * sE[a];
+                }
+                for (int k = ld(P.ptrH + 2 * (NH + 1) + b), k1 = ld(P.ptrH + 2 * (NH + 1) + b + 1); k < k1; ++k) {
+                    const int a = ld(P.idxH + k);
+                    const real v = ld(P.valH + k);
+                    cx -= v * sE[NE + a];
+                    cy += v * sE[a];
+                }
+            } else {
+                const real* Dx = P.DT + b;
+                const real* Dy = Dx + (size_t)NE * NH;
+                const real* Dz = Dy + (size_t)NE * NH;
+                for (int a = 0; a < NE; ++a) {
+                    const real dx = ld(Dx + (size_t)a * NH), dy = ld(Dy + (size_t)a * NH), dz = ld(Dz + (size_t)a * NH);
+                    const real ex = sE[a], ey = sE[NE + a], ez = sE[2 * NE + a];
+                    cx += dy * ez - dz * ey;
+                    cy += dz * ex - dx * ez;
+                    cz += dx * ey - dy * ex;
+                }
             }
             real r0 = -(real)sT * cx, r1 = -(real)sT * cy, r2 = -(real)sT * cz;
             for (int f = 0; f < 4; ++f) {
@@ -685,7 +708,7 @@ k_phase_H2(KParams<real> P, double dt, double a_lo, double c_out, double* __rest
     if (partials) block_energy_store(eacc, partials);
 }
 
-template <typename real>
+template <typename real, bool SPARSE>
 __global__ void __launch_bounds__(kWarps * 32)
 k_phase_E2(KParams<real> P, double dt) {
     extern __shared__ unsigned char smem_raw[];
@@ -708,15 +731,37 @@ k_phase_E2(KParams<real> P, double dt) {
         real* Et = P.E + t * 3 * NE;
         for (int a = lane; a < NE; a += 32) {
             real rx = 0, ry = 0, rz = 0;
-            const real* Dx = P.D + a;
-            const real* Dy = Dx + (size_t)NH * NE;
-            const real* Dz = Dy + (size_t)NH * NE;
-            for (int b = 0; b < NH; ++b) {
-                const real dx = ld(Dx + (size_t)b * NE), dy = ld(Dy + (size_t)b * NE), dz = ld(Dz + (size_t)b * NE);
-                const real hx = sH[b], hy = sH[NH + b], hz = sH[2 * NH + b];
-                rx += dz * hy - dy * hz;
-                ry += dx * hz - dz * hx;
-                rz += dy * hx - dx * hy;
+            if (SPARSE) {
+                // the nonzeros of column a of D_x, D_y, D_z: curl^T = (D_z^T h_y - D_y^T h_z, ...)
+                for (int k = ld(P.ptrE + a), k1 = ld(P.ptrE + a + 1); k < k1; ++k) {
+                    const int b = ld(P.idxE + k);
+                    const real v = ld(P.valE + k);
+                    ry += v * sH[2 * NH + b];
+                    rz -= v * sH[NH + b];
+                }
+                for (int k = ld(P.ptrE + (NE + 1) + a), k1 = ld(P.ptrE + (NE + 1) + a + 1); k < k1; ++k) {
+                    const int b = ld(P.idxE + k);
+                    const real v = ld(P.valE + k);
+                    rx -= v * sH[2 * NH + b];
+                    rz += v * sH[b];
+                }
+                for (int k = ld(P.ptrE + 2 * (NE + 1) + a), k1 = ld(P.ptrE + 2 * (NE + 1) + a + 1); k < k1; ++k) {
+                    const int b = ld(P.idxE + k);
+                    const real v = ld(P.valE + k);
+                    rx += v * sH[NH + b];
+                    ry -= v * sH[b];
+                }
+            } else {
+                const real* Dx = P.D + a;
+                const real* Dy = Dx + (size_t)NH * NE;
+                const real* Dz = Dy + (size_t)NH * NE;
+                for (int b = 0; b < NH; ++b) {
+                    const real dx = ld(Dx + (size_t)b * NE), dy = ld(Dy + (size_t)b * NE), dz = ld(Dz + (size_t)b * NE);
+                    const real hx = sH[b], hy = sH[NH + b], hz = sH[2 * NH + b];
+                    rx += dz * hy - dy * hz;
+                    ry += dx * hz - dz * hx;
+                    rz += dy * hx - dx * hy;
+                }
             }
             real r0 = (real)sT * rx, r1 = (real)sT * ry, r2 = (real)sT * rz;
             for (int f = 0; f < 4; ++f) {
@@ -780,8 +825,12 @@ int launch_phase_H2(const KParams<real>& P, int grid, double dt, double a_lo, do
                     cudaStream_t s) {
     const size_t smem = phase_smem_bytes(P);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_phase_H2<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_phase_H2<real><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+        cudaFuncSetAttribute(P.sparse ? k_phase_H2<real, true> : k_phase_H2<real, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (P.sparse)
+        k_phase_H2<real, true><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+    else
+        k_phase_H2<real, false><<<grid, kWarps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -789,8 +838,12 @@ template <typename real>
 int launch_phase_E2(const KParams<real>& P, int grid, double dt, cudaStream_t s) {
     const size_t smem = phase_smem_bytes(P);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_phase_E2<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_phase_E2<real><<<grid, kWarps * 32, smem, s>>>(P, dt);
+        cudaFuncSetAttribute(P.sparse ? k_phase_E2<real, true> : k_phase_E2<real, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (P.sparse)
+        k_phase_E2<real, true><<<grid, kWarps * 32, smem, s>>>(P, dt);
+    else
+        k_phase_E2<real, false><<<grid, kWarps * 32, smem, s>>>(P, dt);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -41,6 +41,16 @@ struct KParams {
     // that updates the field and read (own and neighbour side) by the other phase
     real* trE;
     real* trH;
+    // sparse form of the derivative tables (their exact zeros skipped): per direction d,
+    // H-phase rows b: entries [ptrH[d][b], ptrH[d][b+1]) of (a, D_d[b][a]);
+    // E-phase columns a: entries [ptrE[d][a], ptrE[d][a+1]) of (b, D_d[b][a])
+    int sparse;                 // 1: the trace-buffer kernels apply the curl in sparse form
+    const int32_t* ptrH;        // [3][NH+1]
+    const int32_t* idxH;
+    const real* valH;
+    const int32_t* ptrE;        // [3][NE+1]
+    const int32_t* idxE;
+    const real* valE;
 };
 
 // Per-face record of the stabilized flux (FP64), kFaceGeoStride doubles:

@@ -329,6 +329,19 @@ int build_ref_tables(int p, RefTables& t) {
             for (int d = 0; d < 3; ++d) t.D[d][(size_t)bb * t.NE + aa] /= (na * nb);
         }
     }
+    // Exact zeros: d/dx_d phi_a has no component on phi_b for most pairs (the
+    // sparsity the recurrences of Sec. 4.2.2 express); quadrature leaves such
+    // entries at round-off level (below 1e-13 of the largest entry, against 5e-6 for
+    // the smallest genuine entry at p = 8).  They are set to exactly zero, so that
+    // sparse and dense applications of the tables are the same operator.
+    {
+        double mx = 0.0;
+        for (int d = 0; d < 3; ++d)
+            for (double x : t.D[d]) mx = std::max(mx, std::fabs(x));
+        for (int d = 0; d < 3; ++d)
+            for (double& x : t.D[d])
+                if (std::fabs(x) < 1e-12 * mx) x = 0.0;
+    }
     for (int f = 0; f < 4; ++f) {
         face_trace(p, f, t.TrE[f]);
         face_trace(p - 1, f, t.TrH[f]);
