@@ -28,6 +28,7 @@ def test_alu_roofline_arithmetic():
     class W:
         nt, p = 196608, 6
     r = bench.alu_roofline(W, 83.76)
+    assert r["dense_equivalent"]["flops_per_element_step"] == 225792
     expect = W.nt * 225792 / 83.76e-3 / 1e12
     assert abs(r["achieved"] - expect) < 1e-12 and r["unit"] == "TFLOP/s" and r["bound"] == "alu"
     assert abs(r["frac"] - expect / r["peak"]) < 1e-12
@@ -51,3 +52,8 @@ def test_phase_bytes_at_the_default_workload():
     assert be == 196608 * (4 * (6 * 84 + 3 * 56) + 84) and round(be / 1e6, 1) == 545.0
     # one step: 3 b D_e + 2 (g + c) per element
     assert bh + be == 196608 * (3 * 4 * bench.dof_per_elem(6) + 2 * 84)
+
+
+def test_executed_flops_of_the_trace_buffer_kernels():
+    # p = 6 dense: 2 x (2 x 6 x 56 x 84 + 20 x 21 x (56 + 84)) = 230,496 flops per element and step
+    assert bench.executed_flops_per_elem_step(6, False) == 2 * (2 * 6 * 56 * 84 + 20 * 21 * 140) == 230496
