@@ -119,6 +119,12 @@ typedef struct dgm_options {
                            creation; an unstable dt shows as DGM_ERR_UNSTABLE from the energy
                            watchdog of dgm_run (energies requested), and dgm_estimate_dt
                            gives the bound */
+    int compensated;    /* FP32 with the central flux only (else DGM_ERR_UNSUPPORTED if set):
+                           Kahan-compensated time-step update.  Every coefficient of E and H
+                           carries a float compensation term holding the rounding error of its
+                           last update, which is fed back into the next one, so the state
+                           accumulates increments to about twice float precision; 8 extra
+                           bytes of traffic per coefficient and step.  Default 0 */
 } dgm_options;
 
 typedef struct dgm_ctx dgm_ctx;
@@ -131,7 +137,8 @@ int dgm_version(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char* dgm_last_error(void);
 
-/* Fill *opt with defaults: central flux, alpha0 = 1, FP64, automatic variant. */
+/* Fill *opt with defaults: central flux, alpha0 = 1, FP64, automatic variant,
+ * no compensation. */
 void dgm_default_options(dgm_options* opt);
 
 /* Context bound to CUDA device `device`.  DGM_ERR_CUDA if the device is absent. */

@@ -174,6 +174,13 @@ void fill_params(dgm_problem* P, dgm::KParams<real>& K) {
     K.fid = P->dFid;
     K.trE = (real*)P->dTrE;
     K.trH = (real*)P->dTrH;
+    K.cE = P->dComp ? (real*)P->dComp : nullptr;
+    K.cH = P->dComp ? (real*)P->dComp + P->nt * 3 * P->NE : nullptr;
+}
+
+// the compensation terms restart at zero whenever the state is replaced from outside
+void reset_comp(dgm_problem* P) {
+    if (P->dComp) cudaMemset(P->dComp, 0, (size_t)P->nt * 3 * (P->NE + P->NH) * sizeof(float));
 }
 
 int ensure_energy(dgm_problem* P, int64_t n) {
@@ -267,6 +274,7 @@ int import_fields(dgm_problem* P, const double* dEsrc, const double* dHsrc, cuda
     if (P->tc) return dgm::tc_import(P, dEsrc, dHsrc, P->dNrmE, P->dNrmH, s);
     if (dEsrc) P->trE_valid = false;
     if (dHsrc) P->trH_valid = false;
+    reset_comp(P);
     const int64_t nE = P->nt * 3 * P->NE, nH = P->nt * 3 * P->NH;
     int rc = 0;
     if (P->fp32) {
@@ -310,7 +318,7 @@ int export_fields(dgm_problem* P, double* dEdst, double* dHdst, cudaStream_t s) 
 void free_problem(dgm_problem* P) {
     void* ptrs[] = {P->dE, P->dH, P->dTables, P->dGeo, P->dNbr, P->dNrmE, P->dNrmH,
                     P->dPartials, P->dEnergy, P->dStage, P->dMaps, P->dWphiE, P->dWphiH, P->dPhiE, P->dPhiH,
-                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF, P->dSrc, P->dSrcF, P->dTrE, P->dTrH};
+                    P->dK, P->dFaceGeo, P->dFid, P->dNrmF, P->dSrc, P->dSrcF, P->dTrE, P->dTrH, P->dComp};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->tc) dgm::tc_problem_free(P);
@@ -331,6 +339,7 @@ void dgm_default_options(dgm_options* opt) {
     opt->precision = DGM_PREC_FP64;
     opt->variant = 0;
     opt->checks = 1;
+    opt->compensated = 0;
 }
 
 int dgm_create(dgm_ctx** ctx, int device) {
@@ -428,6 +437,10 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
                       "variant 2 for FP64/FP32 with the central flux; else use 0");
             return DGM_ERR_INVALID_ARG;
         }
+    }
+    if (o.compensated && !(o.precision == DGM_PREC_FP32 && o.flux == DGM_FLUX_CENTRAL)) {
+        set_error("dgm_problem_create: the compensated update exists for FP32 with the central flux");
+        return DGM_ERR_UNSUPPORTED;
     }
     const dgm::MeshData& m = mesh->m;
     for (int64_t t = 0; t < m.nt; ++t)
@@ -534,6 +547,11 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         for (int g = 0; g < P->N2E; ++g) nrmF[g] = std::sqrt(dgm::dubiner2_norm2(i2[2 * g], i2[2 * g + 1]));
         if ((e = cudaMalloc(&P->dNrmF, P->N2E * sizeof(double))) != cudaSuccess) return fail(cuda_fail(e, "alloc nrm"));
         cudaMemcpy(P->dNrmF, nrmF.data(), P->N2E * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (o.compensated) {
+        const size_t nC = (size_t)m.nt * 3 * (P->NE + P->NH);
+        if ((e = cudaMalloc(&P->dComp, nC * sizeof(float))) != cudaSuccess) return fail(cuda_fail(e, "alloc comp"));
+        cudaMemset(P->dComp, 0, nC * sizeof(float));
     }
     if (!tc && !stab) {
         // tangential face-trace buffers of the trace-buffer phase kernels
@@ -1210,6 +1228,7 @@ int dgm_estimate_dt(dgm_problem* P, int iters, double* rho_out, double* dt_out) 
     auto fin = [&](int code) {
         cudaFree(tmp);
         P->trE_valid = P->trH_valid = false;
+        reset_comp(P);
         return code;
     };
     if (cudaMemcpy(saveE, v.E, v.nE * es, cudaMemcpyDeviceToDevice) != cudaSuccess ||
@@ -1288,6 +1307,7 @@ void set_state_ptrs(dgm_problem* P, void* E, void* H) {
         P->kd.H = (double*)H;
     }
     P->trE_valid = P->trH_valid = false;
+    reset_comp(P);
 }
 
 struct DevBuf {
@@ -1920,6 +1940,7 @@ int dgm_project_device(dgm_problem* P, int q1d, const double* E_pts, const doubl
     }
     if (E_pts) P->trE_valid = false;
     if (H_pts) P->trH_valid = false;
+    reset_comp(P);
     if (P->fp32) {
         if (E_pts) r |= dgm::launch_project<float>(P->nt, P->NE, nq, P->dMaps, P->dWphiE, E_pts, (float*)P->dE, s);
         if (H_pts) r |= dgm::launch_project<float>(P->nt, P->NH, nq, P->dMaps, P->dWphiH, H_pts, (float*)P->dH, s);

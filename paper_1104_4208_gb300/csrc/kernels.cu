@@ -684,7 +684,22 @@ k_phase_H2(KParams<real> P, double dt, double a_lo, double c_out, double* __rest
                         (l0 * (gm6[0] * u0 + gm6[1] * u1 + gm6[2] * u2) + l1 * (gm6[1] * u0 + gm6[3] * u1 + gm6[4] * u2) +
                          l2 * (gm6[2] * u0 + gm6[4] * u1 + gm6[5] * u2));
             }
-            const real n0 = h0 + (real)c_out * d0, n1 = h1 + (real)c_out * d1, n2 = h2 + (real)c_out * d2;
+            real n0, n1, n2;
+            if (P.cH) {
+                // Kahan: the last update's rounding error re-enters this one
+                real* c = P.cH + t * 3 * NH + b;
+                const real y0 = (real)c_out * d0 - c[0], y1 = (real)c_out * d1 - c[NH], y2 = (real)c_out * d2 - c[2 * NH];
+                n0 = h0 + y0;
+                n1 = h1 + y1;
+                n2 = h2 + y2;
+                c[0] = (n0 - h0) - y0;
+                c[NH] = (n1 - h1) - y1;
+                c[2 * NH] = (n2 - h2) - y2;
+            } else {
+                n0 = h0 + (real)c_out * d0;
+                n1 = h1 + (real)c_out * d1;
+                n2 = h2 + (real)c_out * d2;
+            }
             Ht[b] = n0;
             Ht[NH + b] = n1;
             Ht[2 * NH + b] = n2;
@@ -779,9 +794,26 @@ k_phase_E2(KParams<real> P, double dt) {
                 r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
             }
             const real s = (real)(dt * inv_eps);
-            const real n0 = Et[a] + s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
-            const real n1 = Et[NE + a] + s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
-            const real n2 = Et[2 * NE + a] + s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            const real d0 = s * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real d1 = s * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real d2 = s * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            const real e0 = Et[a], e1 = Et[NE + a], e2 = Et[2 * NE + a];
+            real n0, n1, n2;
+            if (P.cE) {
+                // Kahan: the last update's rounding error re-enters this one
+                real* c = P.cE + t * 3 * NE + a;
+                const real y0 = d0 - c[0], y1 = d1 - c[NE], y2 = d2 - c[2 * NE];
+                n0 = e0 + y0;
+                n1 = e1 + y1;
+                n2 = e2 + y2;
+                c[0] = (n0 - e0) - y0;
+                c[NE] = (n1 - e1) - y1;
+                c[2 * NE] = (n2 - e2) - y2;
+            } else {
+                n0 = e0 + d0;
+                n1 = e1 + d1;
+                n2 = e2 + d2;
+            }
             Et[a] = n0;
             Et[NE + a] = n1;
             Et[2 * NE + a] = n2;

@@ -44,6 +44,10 @@ struct KParams {
     // sparse form of the derivative tables (their exact zeros skipped): per direction d,
     // H-phase rows b: entries [ptrH[d][b], ptrH[d][b+1]) of (a, D_d[b][a]);
     // E-phase columns a: entries [ptrE[d][a], ptrE[d][a+1]) of (b, D_d[b][a])
+    // compensated update (FP32 option): the rounding error of each coefficient's last
+    // update, [nt][3][N] like the fields (nullptr: plain update)
+    real* cE;
+    real* cH;
     int sparse;                 // 1: the trace-buffer kernels apply the curl in sparse form
     const int32_t* ptrH;        // [3][NH+1]
     const int32_t* idxH;

@@ -56,6 +56,7 @@ struct dgm_problem {
     // ([nt][4][2][N2(p-1)]), valid per the trE_valid / trH_valid flags below
     void* dTrE = nullptr;
     void* dTrH = nullptr;
+    void* dComp = nullptr;               // compensated update: [nE + nH] floats (E terms, then H)
     // tensor-core path (precisions TC32, TC16)
     bool tc = false;
     int tc_grid = 0;                     // CTAs of the tensor-core kernels (autotuned)

@@ -46,8 +46,10 @@ def _log(name, **kw):
             fh.write(json.dumps(dict(test=name, **kw)) + "\n")
 
 
-def _project(capi, S, w, T, torch):
-    """E, H of the solver := L2 projections of the plane wave at time T (device path)."""
+def _project(capi, S, w, T, torch, fn=None):
+    """E, H of the solver := L2 projections of the plane wave at time T, or of
+    fn(x) -> (E, H) (device path)."""
+    fn = fn or (lambda x: plane_wave_fields(x, T))
     q1d = w.p + 1
     xh, _ = capi.dgm_quad_rule(q1d)
     maps = capi.dgm_element_maps(S.mesh, S.nt)
@@ -57,7 +59,7 @@ def _project(capi, S, w, T, torch):
     for s in range(0, S.nt, 16384):
         e = min(S.nt, s + 16384)
         x = maps[s:e, None, :3] + np.einsum("tij,qj->tqi", F[s:e], xh)
-        Ex, Hx = plane_wave_fields(x, T)
+        Ex, Hx = fn(x)
         Ed[s:e].copy_(torch.from_numpy(Ex))
         Hd[s:e].copy_(torch.from_numpy(Hx))
     capi.dgm_project_device(S.prob, q1d, Ed.data_ptr(), Hd.data_ptr(), torch.cuda.current_stream().cuda_stream)
@@ -123,3 +125,65 @@ def test_planewave_full_horizon(runs, precision):
         assert r["dev_fp64"] < BOUND_DEV[precision]
         # the triangle inequality ties each error against the wave to the FP64 path's
         assert abs(r["err_wave"] - runs["fp64"]["err_wave"]) <= r["dev_fp64"] * 1.0001 + 1e-12
+
+
+# pulse_n16_p4 over its stated 1,000 steps: jittered PEC cube, eps ~ U[1,4], Gaussian
+# pulse; FP32 with and without the compensated (Kahan) update, and the tensor-core
+# modes, against the FP64 path.  Deviation in the energy norm (eps-weighted L2).
+PULSE = {"fp32": dict(precision="fp32"), "fp32k": dict(precision="fp32", compensated=True),
+         "tc16": dict(precision="tc16"), "tc16x2": dict(precision="tc16x2")}
+BOUND_DEV_PULSE = {"fp32": 1e-4, "fp32k": 1e-4, "tc16": 2e-2, "tc16x2": 5e-3}
+BOUND_DRIFT_PULSE = {"fp64": 1e-11, "fp32": 1e-5, "fp32k": 1e-5, "tc16": 1e-4, "tc16x2": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def pulse_runs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_4208_gb300 import build
+    build.build()
+    from paper_1104_4208_gb300 import _capi as capi
+    from paper_1104_4208_gb300.solver import Solver
+    from workloads.fields import gaussian_pulse_fields
+    w = make_workload("pulse_n16_p4")
+    m = w.mesh
+    fn = lambda x: gaussian_pulse_fields(x, w.centre)
+    out = {}
+    S64 = Solver(m.xyz, m.tets, w.p, w.eps, w.mu, precision="fp64")
+    _project(capi, S64, w, 0.0, torch, fn)
+    W64 = S64.run(w.dt, w.steps, energies=True)
+    E64, _ = S64.get_fields()
+    out["fp64"] = (E64, W64)
+    for name, kw in PULSE.items():
+        S = Solver(m.xyz, m.tets, w.p, w.eps, w.mu, **kw)
+        _project(capi, S, w, 0.0, torch, fn)
+        W = S.run(w.dt, w.steps, energies=True)
+        out[name] = (S.get_fields()[0], W)
+        S.close()
+    zH = np.zeros(S64.nH)
+
+    def enorm(X):
+        S64.set_fields(X, zH)
+        return np.sqrt(2.0 * S64.energy())
+
+    n64 = enorm(E64)
+    res = {}
+    for name, (E, W) in out.items():
+        res[name] = dict(dev_fp64=enorm(E - E64) / n64, drift=float(np.abs(W - W[0]).max() / W[0]))
+        _log("pulse_1000_steps", precision=name, **res[name])
+    S64.close()
+    return res
+
+
+@pytest.mark.parametrize("name", ["fp64", "fp32", "fp32k", "tc16", "tc16x2"])
+def test_pulse_full_horizon(pulse_runs, name):
+    """pulse_n16_p4 over its stated 1,000 steps: energy drift and deviation from the FP64
+    path within each mode's bound; the compensated FP32 update is no less accurate than
+    the plain one."""
+    r = pulse_runs[name]
+    assert r["drift"] < BOUND_DRIFT_PULSE[name]
+    if name != "fp64":
+        assert r["dev_fp64"] < BOUND_DEV_PULSE[name]
+    if name == "fp32k":
+        assert r["dev_fp64"] <= pulse_runs["fp32"]["dev_fp64"] * 1.05

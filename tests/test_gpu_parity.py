@@ -36,8 +36,8 @@ pytestmark = pytest.mark.gpu
 # fp16; the 100-step cavity trajectory deviates 0.32 (max-coefficient measure),
 # bounded by 0.4.  "tc16x2": fp16 field operands with two-term (hi + lo) fp16 tables:
 # the field rounding, and so the per-kick bound, stays that of fp16
-TOL = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-5, "fp32s": 2e-5, "tc32": 3e-3, "tc16": 3e-3, "tc16d": 3e-3, "tcbf16": 2.4e-2, "tc16x2": 3e-3}
-TOL_TRAJ = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-4, "fp32s": 2e-4, "tc32": 3e-2, "tc16": 3e-2, "tc16d": 3e-2, "tcbf16": 0.4, "tc16x2": 3e-2}
+TOL = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-5, "fp32s": 2e-5, "fp32k": 2e-5, "tc32": 3e-3, "tc16": 3e-3, "tc16d": 3e-3, "tcbf16": 2.4e-2, "tc16x2": 3e-3}
+TOL_TRAJ = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-4, "fp32s": 2e-4, "fp32k": 2e-4, "tc32": 3e-2, "tc16": 3e-2, "tc16d": 3e-2, "tcbf16": 0.4, "tc16x2": 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -57,11 +57,13 @@ def _rel(a, b):
 
 def _solver(capi, m, p, eps, mu=1.0, precision="fp64", flux="central"):
     """precision names as the Solver's, plus: "tc16d" = TC16 on the dense-operator
-    kernels (variant 1), "fp64s"/"fp32s" = the sparse-curl CUDA-core kernels (variant 2)."""
+    kernels (variant 1), "fp64s"/"fp32s" = the sparse-curl CUDA-core kernels (variant 2),
+    "fp32k" = FP32 with the compensated (Kahan) update."""
     from paper_1104_4208_gb300.solver import Solver
     variant = 1 if precision == "tc16d" else 2 if precision in ("fp64s", "fp32s") else 0
-    base = {"tc16d": "tc16", "fp64s": "fp64", "fp32s": "fp32"}.get(precision, precision)
-    return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=base, flux=flux, variant=variant)
+    base = {"tc16d": "tc16", "fp64s": "fp64", "fp32s": "fp32", "fp32k": "fp32"}.get(precision, precision)
+    return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=base, flux=flux, variant=variant,
+                  compensated=precision == "fp32k")
 
 
 def _cases():
@@ -85,7 +87,7 @@ def _mesh(name):
     return kuhn_cube_mesh(1, jitter=0.0, seed=1, shuffle_local=True)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32s"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32s", "fp32k"])
 @pytest.mark.parametrize("name,p", _cases())
 def test_kick_parity(capi, name, p, precision):
     """One H-kick and one E-kick (Sec. 3 symplectic Euler halves) vs the oracle."""
@@ -113,7 +115,7 @@ def test_kick_parity(capi, name, p, precision):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32k"])
 def test_cavity_trajectory_parity(capi, precision):
     """Workload cavity_n4_p3 (384 tets, p=3, TE110, dt = 0.2h/p^2, 100 steps):
     fields and the per-step discrete energy vs the oracle; energy conserved."""
@@ -283,6 +285,11 @@ def test_invalid_arguments(capi):
         assert e.value.code == capi.DGM_ERR_UNSUPPORTED
         with pytest.raises(capi.DgmError) as e:
             Solver(m.xyz, m.tets, 3, 1.0, 1.0, precision=prec, flux="stabilized")
+        assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+    # the compensated update exists for FP32 with the central flux only
+    for kw in (dict(precision="fp64"), dict(precision="tc16"), dict(precision="fp32", flux="stabilized")):
+        with pytest.raises(capi.DgmError) as e:
+            Solver(m.xyz, m.tets, 2, 1.0, 1.0, compensated=True, **kw)
         assert e.value.code == capi.DGM_ERR_UNSUPPORTED
     # autotune needs at least one timed step
     S = Solver(m.xyz, m.tets, 2, 1.0, 1.0, precision="tc16")
