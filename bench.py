@@ -137,7 +137,8 @@ def parse():
     ap.add_argument("--workload", default="planewave_n32_p6")
     ap.add_argument("--precision", default="tc16", choices=["tc16", "tcbf16", "tc16x2", "tc32", "fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
-                    help="TC16 only: 0 resident-table kernels (default), 1 dense-operator kernels")
+                    help="TC16: 0 resident-table kernels (default), 1 dense-operator kernels; FP64/FP32: "
+                         "0 automatic (autotuned), 1 dense curl, 2 sparse curl")
     ap.add_argument("--no-p4", action="store_true", help="skip the p = 4 sub-block of the default workload")
     ap.add_argument("--fp64-steps", type=int, default=1, help="nonzero: also run the FP64 path over the same steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
@@ -247,7 +248,7 @@ def make_solver(w, precision, variant=0):
     from paper_1104_4208_gb300.solver import Solver
     m = w.mesh
     return Solver(m.xyz, m.tets, w.p, w.eps, w.mu, vertex_key=m.vertex_key, precision=precision,
-                  variant=variant if precision == "tc16" else 0)
+                  variant=variant if precision in ("tc16", "fp64", "fp32") else 0)
 
 
 def project_initial(S, w, torch, q1d):
@@ -469,7 +470,8 @@ def run_gpu(args, rank, world, local):
         kname, kbytes, kms = kpre + "_E", bytes_E, tE
     peak, peak_src = measured_peak_hbm()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    roof = alu_roofline(w, ms / args.steps, local, bool(tune and tune["chosen"] >= 1000)) if args.precision == "fp64" else \
+    sparse64 = bool(tune and tune["chosen"] >= 1000) or (not tune and args.variant == 2)
+    roof = alu_roofline(w, ms / args.steps, local, sparse64) if args.precision == "fp64" else \
         {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
             "traffic": profile_traffic(f"{kname}/{args.precision}" if tcp else f"{kname}<{'float' if b == 4 else 'double'}>"),
