@@ -138,7 +138,7 @@ def parse():
     ap.add_argument("--precision", default="tc16", choices=["tc16", "tcbf16", "tc16x2", "tc32", "fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=0,
                     help="TC16: 0 resident-table kernels (default), 1 dense-operator kernels; FP64/FP32: "
-                         "0 automatic (autotuned), 1 dense curl, 2 sparse curl")
+                         "0 automatic (autotuned), 1 dense curl, 2 sparse curl, 3 element-group kernels (sparse curl)")
     ap.add_argument("--no-p4", action="store_true", help="skip the p = 4 sub-block of the default workload")
     ap.add_argument("--fp64-steps", type=int, default=1, help="nonzero: also run the FP64 path over the same steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
@@ -470,7 +470,7 @@ def run_gpu(args, rank, world, local):
         kname, kbytes, kms = kpre + "_E", bytes_E, tE
     peak, peak_src = measured_peak_hbm()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    sparse64 = bool(tune and tune["chosen"] >= 1000) or (not tune and args.variant == 2)
+    sparse64 = bool(tune and tune["chosen"] >= 1000) or (not tune and args.variant in (2, 3))
     roof = alu_roofline(w, ms / args.steps, local, sparse64) if args.precision == "fp64" else \
         {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
@@ -490,7 +490,8 @@ def run_gpu(args, rank, world, local):
         if not args.no_autotune:   # the FP64 path in its own fastest configuration (dense or sparse curl)
             cfg64, tms64, ch64 = S64.autotune(2)
             tune64 = {"per_sm": cfg64, "ms_per_step": [round(x, 3) for x in tms64], "chosen": cfg64[ch64],
-                      "note": "configurations >= 1000: sparse curl, blocks per SM = value - 1000"}
+                      "note": "configurations 1000-1999: sparse curl, blocks per SM = value - 1000; >= 2000: "
+                              "element-group kernels (sparse curl), blocks per SM = value - 2000"}
         ms64, st64, W64 = timed_run(S64, torch, dt, args.steps, args.warmup)
         v64 = world * dofs * args.steps / (dist_max(ms64) * 1e-3)
         kept64 = []

@@ -114,7 +114,11 @@ typedef struct dgm_options {
     int variant;        /* 0 = automatic kernel choice (dgm_autotune may change it);
                            TC16: 1 = dense-operator kernels; FP64/FP32 with the central flux:
                            1 = dense curl, 2 = sparse curl (the exact zeros of D_x, D_y, D_z
-                           skipped, Sec. 4.2.2) */
+                           skipped, Sec. 4.2.2), 3 = element-group kernels (sparse curl; a block
+                           takes 32 elements at a time, lane e of each warp working on element
+                           e, so every multiply-add has all 32 lanes busy; not with the
+                           compensated update, DGM_ERR_UNSUPPORTED where a block's shared
+                           memory cannot hold 32 elements at this degree) */
     int checks;         /* reserved: accepted, no effect.  Inputs are always validated at
                            creation; an unstable dt shows as DGM_ERR_UNSTABLE from the energy
                            watchdog of dgm_run (energies requested), and dgm_estimate_dt
@@ -263,6 +267,9 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * with the central flux and variant 0 each also with the sparse curl, reported
  * as 1000 + blocks per SM (the dense and the sparse curl sum the same nonzero
  * products in different orders: fields then agree to round-off, not bitwise);
+ * with the central flux, variant 0 or 3 and no compensated update also the
+ * element-group kernels, reported as 2000 + blocks per SM (1 or 2, where that many
+ * blocks' shared memory fits in an SM; the same sums as the sparse curl);
  * dense-operator tensor-core kernels (TC32, TC16X2, TC16 variant 1) -- 1 or 2 CTAs per
  * SM (2 only where the TMEM columns and shared memory of a CTA allow it);
  * resident-table tensor-core kernels (TC16, TCBF16) -- one configuration
@@ -273,7 +280,7 @@ int dgm_tridiag_eig(int k, const double* d, const double* e, int i0, int i1, dou
  * Outputs (nullable): *ncand (<= DGM_AUTOTUNE_MAX), per candidate its
  * configuration value (blocks or CTAs per SM) and ms per step, and the index
  * of the chosen one.  Errors: DGM_ERR_INVALID_ARG for steps < 1. */
-#define DGM_AUTOTUNE_MAX 8
+#define DGM_AUTOTUNE_MAX 12
 int dgm_autotune(dgm_problem* prob, int steps, int* ncand, int* cand_config, double* cand_ms, int* chosen);
 
 /* Point dipole current J(x, t) = dir delta(x - xs) f(t) with the zero-mean

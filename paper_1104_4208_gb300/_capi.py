@@ -244,7 +244,7 @@ def dgm_tridiag_eig(d, e, i0, i1, vectors=False):
     return (vals, vecs) if vectors else vals
 
 
-AUTOTUNE_MAX = 8
+AUTOTUNE_MAX = 12
 
 
 def dgm_autotune(prob, steps=5):

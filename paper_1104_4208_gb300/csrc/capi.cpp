@@ -142,7 +142,8 @@ int upload_tables(dgm_problem* P, dgm::KParams<real>& K) {
         K.idxE = K.idxH + idxH.size();
         K.valH = (real*)P->dTables + o_sp + nIr;
         K.valE = K.valH + valH.size();
-        K.sparse = P->opt.variant == 2 ? 1 : 0;
+        K.sparse = P->opt.variant == 2 || P->opt.variant == 3 ? 1 : 0;
+        K.eg = P->opt.variant == 3 ? 1 : 0;
     }
     real* base = (real*)P->dTables;
     K.DT = base;
@@ -197,6 +198,16 @@ int ensure_energy(dgm_problem* P, int64_t n) {
 // that updates a field writes its traces, the other phase reads them
 bool cc_buffered(const dgm_problem* P) { return !P->tc && P->dTrE != nullptr; }
 
+// element-group kernels: do `blocks` resident blocks fit in an SM's shared memory?
+bool eg_fits(const dgm_problem* P, int blocks) {
+    const size_t need = P->fp32 ? dgm::phase_eg_smem_bytes<float>(P->kf) : dgm::phase_eg_smem_bytes<double>(P->kd);
+    int per_block = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->ctx->device) != cudaSuccess)
+        return false;
+    return need + 1024 <= (size_t)per_block && (size_t)blocks * (need + 1024) <= (size_t)per_sm;
+}
+
 int cc_traces(dgm_problem* P, int which, int64_t e0, int64_t e1, cudaStream_t s) {
     const int r = P->fp32 ? dgm::launch_traces2<float>(P->kf, P->grid, which, e0, e1, s)
                           : dgm::launch_traces2<double>(P->kd, P->grid, which, e0, e1, s);
@@ -229,8 +240,11 @@ int cc_phase_H(dgm_problem* P, double dt, double a_lo, double c_out, double* par
     }
     int rc = cc_ensure_traces_E(P, s);
     if (rc) return rc;
-    const int r = P->fp32 ? dgm::launch_phase_H2<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
-                          : dgm::launch_phase_H2<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s);
+    const bool eg = P->fp32 ? P->kf.eg != 0 : P->kd.eg != 0;
+    const int r = eg ? (P->fp32 ? dgm::launch_phase_H3<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
+                                : dgm::launch_phase_H3<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s))
+                     : (P->fp32 ? dgm::launch_phase_H2<float>(P->kf, P->grid, dt, a_lo, c_out, partials, s)
+                                : dgm::launch_phase_H2<double>(P->kd, P->grid, dt, a_lo, c_out, partials, s));
     if (r) return cuda_fail(cudaGetLastError(), "H-phase launch");
     P->trH_valid = true;
     return DGM_OK;
@@ -247,8 +261,11 @@ int cc_phase_E(dgm_problem* P, double dt, cudaStream_t s) {
         if (rc) return rc;
         P->trH_valid = true;
     }
-    const int r = P->fp32 ? dgm::launch_phase_E2<float>(P->kf, P->grid, dt, s)
-                          : dgm::launch_phase_E2<double>(P->kd, P->grid, dt, s);
+    const bool eg = P->fp32 ? P->kf.eg != 0 : P->kd.eg != 0;
+    const int r = eg ? (P->fp32 ? dgm::launch_phase_E3<float>(P->kf, P->grid, dt, s)
+                                : dgm::launch_phase_E3<double>(P->kd, P->grid, dt, s))
+                     : (P->fp32 ? dgm::launch_phase_E2<float>(P->kf, P->grid, dt, s)
+                                : dgm::launch_phase_E2<double>(P->kd, P->grid, dt, s));
     if (r) return cuda_fail(cudaGetLastError(), "E-phase launch");
     P->trE_valid = true;
     P->trE_ndirty = 0;
@@ -431,11 +448,15 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         const bool cc_central = (o.precision == DGM_PREC_FP64 || o.precision == DGM_PREC_FP32) &&
                                 o.flux == DGM_FLUX_CENTRAL;
         const bool ok = o.variant == 0 || (o.variant == 1 && (o.precision == DGM_PREC_TC16 || cc_central)) ||
-                        (o.variant == 2 && cc_central);
+                        ((o.variant == 2 || o.variant == 3) && cc_central);
         if (!ok) {
             set_error("dgm_problem_create: variant 1 exists for TC16 and for FP64/FP32 with the central flux, "
-                      "variant 2 for FP64/FP32 with the central flux; else use 0");
+                      "variants 2 and 3 for FP64/FP32 with the central flux; else use 0");
             return DGM_ERR_INVALID_ARG;
+        }
+        if (o.variant == 3 && o.compensated) {
+            set_error("dgm_problem_create: the element-group kernels (variant 3) have no compensated update");
+            return DGM_ERR_UNSUPPORTED;
         }
     }
     if (o.compensated && !(o.precision == DGM_PREC_FP32 && o.flux == DGM_FLUX_CENTRAL)) {
@@ -651,6 +672,14 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
         rc = upload_tables<double>(P, P->kd);
     }
     if (rc) return fail(rc);
+    if (!tc && o.variant == 3) {
+        if (!eg_fits(P, 1)) {
+            set_error("dgm_problem_create: the element-group kernels (variant 3) need more shared memory than a "
+                      "block may have at this degree");
+            return fail(DGM_ERR_UNSUPPORTED);
+        }
+        P->grid = std::min(P->grid_cap, ctx->num_sms);
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(cuda_fail(e, "setup"));
     *out = P;
     return DGM_OK;
@@ -1149,10 +1178,18 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
         // are timed unless the variant option fixed one
         const bool both = cc_buffered(P) && P->opt.variant == 0;
         const int fixed = cc_buffered(P) && P->opt.variant == 2 ? 1000 : 0;
-        for (int v : {0, 1000})
-            if (both || v == fixed)
-                for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b + v);
+        if (P->opt.variant != 3)
+            for (int v : {0, 1000})
+                if (both || v == fixed)
+                    for (int b : {4, 8, 16, kAutotuneMaxBlocksPerSm}) cand.push_back(b + v);
+        // element-group kernels (configuration 2000 + blocks per SM), which have no
+        // compensated update
+        const bool comp = P->fp32 && P->kf.cE != nullptr;
+        if (cc_buffered(P) && !comp && (P->opt.variant == 0 || P->opt.variant == 3))
+            for (int b : {1, 2})
+                if (eg_fits(P, b)) cand.push_back(2000 + b);
     }
+    if (cand.size() > DGM_AUTOTUNE_MAX) cand.resize(DGM_AUTOTUNE_MAX);
     auto apply = [&](int c) {
         if (resident) {
             (void)c;
@@ -1162,9 +1199,11 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
         } else {
             P->grid = std::min(P->grid_cap, sms * (c % 1000));
             P->kd.sparse = P->kf.sparse = c >= 1000 ? 1 : 0;
+            P->kd.eg = P->kf.eg = c >= 2000 ? 1 : 0;
         }
     };
-    const int keep_grid = P->grid, keep_tc = P->tc_grid, keep_sparse = P->kd.sparse | P->kf.sparse;
+    const int keep_grid = P->grid, keep_tc = P->tc_grid, keep_sparse = P->kd.sparse | P->kf.sparse,
+              keep_eg = P->kd.eg | P->kf.eg;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DGM_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1194,6 +1233,7 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
         P->grid = keep_grid;
         P->tc_grid = keep_tc;
         P->kd.sparse = P->kf.sparse = keep_sparse;
+        P->kd.eg = P->kf.eg = keep_eg;
         if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
         return rc;
     }

@@ -907,4 +907,354 @@ template int launch_import<float>(const double*, float*, const double*, int64_t,
 template int launch_export<double>(const double*, double*, const double*, int64_t, int, cudaStream_t);
 template int launch_export<float>(const float*, double*, const double*, int64_t, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Element-group phase kernels (central flux, trace buffers, sparse curl).
+// The kernels above give one warp one element and spread its coefficients and
+// (face, mode) pairs over the lanes; the counts at p = 6 (56, 84 and 84) leave a
+// last pass with 20 to 24 of 32 lanes, and the sparse rows of D_x, D_y, D_z
+// differ in length, so lanes wait for the longest row of their warp.  Here a
+// block takes 32 elements at a time and lane e of every warp works on element e:
+// warps split the rows (and the (face, mode) pairs), and every lane of a warp
+// runs the same row, so each multiply-add instruction has all 32 lanes busy and
+// the table entries it reads are the same for the whole warp.  Fields, flux and
+// traces of the group are staged in shared memory (per-element strides odd, so
+// the 32 lanes hit distinct banks), and read from and written to global memory
+// in whole contiguous rows.  The sums are those of the kernels above, in the
+// same order.
+
+namespace {
+
+constexpr int kEG = 32;        // elements per group: one per lane
+constexpr int kEGMaxWarps = 16;   // warps per block: chosen per degree, 8 to 16
+
+struct EGLayout {
+    int sIn, sF, sOut;         // per-element strides (reals)
+    int oF, oOut, total;       // offsets and size of the block's region (reals)
+};
+
+__host__ __device__ inline EGLayout eg_layout(int Nin, int Nout, int G) {
+    EGLayout L;
+    L.sIn = (3 * Nin) | 1;
+    L.sF = (8 * G) | 1;
+    L.sOut = (3 * Nout) | 1;
+    L.oF = kEG * L.sIn;
+    L.oOut = L.oF + kEG * L.sF;
+    L.total = L.oOut + kEG * L.sOut;
+    return L;
+}
+
+__device__ void block_energy_store_w(double v, double* out) {
+    __shared__ double red[kEGMaxWarps];
+    const int W = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < W; ++i) s += red[i];
+        out[blockIdx.x] = s;
+    }
+}
+
+// contiguous rows [t0, t0 + ne) of X ([nt][n] reals) <-> padded shared rows
+template <typename real>
+__device__ void eg_stage_in(const real* __restrict__ X, int64_t t0, int ne, int n, real* s, int stride) {
+    const real* src = X + t0 * n;
+    for (int i = threadIdx.x; i < ne * n; i += blockDim.x) {
+        const int e = i / n;
+        s[e * stride + (i - e * n)] = src[i];
+    }
+}
+
+template <typename real>
+__device__ void eg_stage_out(real* X, int64_t t0, int ne, int n, const real* s, int stride) {
+    real* dst = X + t0 * n;
+    for (int i = threadIdx.x; i < ne * n; i += blockDim.x) {
+        const int e = i / n;
+        dst[i] = s[e * stride + (i - e * n)];
+    }
+}
+
+// flux values of the group's faces from the trace buffer tr (jump for the
+// H-phase, average for the E-phase, PEC ghost state on boundary faces) into
+// sF [e][f][2][G]; warps over (element, face) pairs, lanes over the 2G values
+template <typename real, bool JUMP>
+__device__ void eg_flux(const KParams<real>& P, const real* __restrict__ tr, int64_t t0, int ne, real* sF,
+                        int stride) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5, G2 = 2 * P.N2H;
+    for (int pair = w; pair < 4 * ne; pair += W) {
+        const int e = pair >> 2, f = pair & 3;
+        const int64_t t = t0 + e;
+        const int32_t nb = P.nbr[t * 4 + f];
+        const double sig = P.geo[t * kGeoStride + kGeoSign] * c_sigma_hat[f];
+        const real* own = tr + (t * 4 + f) * G2;
+        const real* nbt = nb >= 0 ? tr + ((int64_t)(nb >> 2) * 4 + (nb & 3)) * G2 : own;
+        for (int k = lane; k < G2; k += 32) {
+            const real J = own[k];
+            real a;
+            if (nb >= 0) {
+                const real K = nbt[k];
+                a = (real)(0.5 * sig) * (JUMP ? J - K : J + K);
+            } else {
+                a = (real)sig * J;
+            }
+            sF[e * stride + f * G2 + k] = a;
+        }
+    }
+}
+
+// tangential traces of the staged field sX [e][3][N] into sT [e][f][2][G];
+// warps over (face, mode) pairs, lane = element
+template <typename real>
+__device__ void eg_traces(const real* sX, int N, int sx, const real* __restrict__ TT, int G, real* sT, int st) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const real* x = sX + lane * sx;
+    for (int item = w; item < 4 * G; item += W) {
+        const int f = item / G, gm = item - f * G;
+        const real* T = TT + (size_t)f * N * G + gm;
+        real t0 = 0, t1 = 0, t2 = 0;
+        for (int a = 0; a < N; ++a) {
+            const real v = ld(T + (size_t)a * G);
+            t0 += v * x[a];
+            t1 += v * x[N + a];
+            t2 += v * x[2 * N + a];
+        }
+        real* o = sT + lane * st + f * 2 * G + gm;
+        o[0] = (real)c_that[f][0][0] * t0 + (real)c_that[f][0][1] * t1 + (real)c_that[f][0][2] * t2;
+        o[G] = (real)c_that[f][1][0] * t0 + (real)c_that[f][1][1] * t1 + (real)c_that[f][1][2] * t2;
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kEGMaxWarps * 32, 1)
+k_phase_H3(KParams<real> P, double dt, double a_lo, double c_out, double* __restrict__ partials) {
+    extern __shared__ unsigned char smem_raw[];
+    real* s = reinterpret_cast<real*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int NE = P.NE, NH = P.NH, G = P.N2H;
+    const EGLayout L = eg_layout(NE, NH, G);
+    real* sE = s;
+    real* sF = s + L.oF;
+    real* sH = s + L.oOut;
+    double eacc = 0.0;
+    const int64_t ngroups = (P.nt + kEG - 1) / kEG;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t t0 = grp * kEG;
+        const int ne = (int)(P.nt - t0 < kEG ? P.nt - t0 : kEG);
+        eg_stage_in(P.E, t0, ne, 3 * NE, sE, L.sIn);
+        eg_stage_in(P.H, t0, ne, 3 * NH, sH, L.sOut);
+        eg_flux<real, true>(P, P.trE, t0, ne, sF, L.sF);
+        __syncthreads();
+        const bool valid = lane < ne;
+        const double* g = P.geo + (t0 + (valid ? lane : 0)) * kGeoStride;
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double gm6[6] = {g[6], g[7], g[8], g[9], g[10], g[11]};
+        const double sT = g[kGeoSign], inv_mu = g[kGeoInvMu], mu = g[kGeoMu];
+        const real* ex = sE + lane * L.sIn;
+        const real* fl = sF + lane * L.sF;
+        real* hx = sH + lane * L.sOut;
+        for (int b = w; b < NH; b += W) {
+            real cx = 0, cy = 0, cz = 0;
+            for (int k = ld(P.ptrH + b), k1 = ld(P.ptrH + b + 1); k < k1; ++k) {
+                const int a = ld(P.idxH + k);
+                const real v = ld(P.valH + k);
+                cy -= v * ex[2 * NE + a];
+                cz += v * ex[NE + a];
+            }
+            for (int k = ld(P.ptrH + (NH + 1) + b), k1 = ld(P.ptrH + (NH + 1) + b + 1); k < k1; ++k) {
+                const int a = ld(P.idxH + k);
+                const real v = ld(P.valH + k);
+                cx += v * ex[2 * NE + a];
+                cz -= v * ex[a];
+            }
+            for (int k = ld(P.ptrH + 2 * (NH + 1) + b), k1 = ld(P.ptrH + 2 * (NH + 1) + b + 1); k < k1; ++k) {
+                const int a = ld(P.idxH + k);
+                const real v = ld(P.valH + k);
+                cx -= v * ex[NE + a];
+                cy += v * ex[a];
+            }
+            real r0 = -(real)sT * cx, r1 = -(real)sT * cy, r2 = -(real)sT * cz;
+            for (int f = 0; f < 4; ++f) {
+                const real* Lf = P.TrH + (size_t)f * G * NH + b;
+                const real* A0 = fl + f * 2 * G;
+                const real* A1 = A0 + G;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < G; ++gm) {
+                    const real l = ld(Lf + (size_t)gm * NH);
+                    u0 += l * A0[gm];
+                    u1 += l * A1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real sc = (real)(dt * inv_mu);
+            const real d0 = sc * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real d1 = sc * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real d2 = sc * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            const real h0 = hx[b], h1 = hx[NH + b], h2 = hx[2 * NH + b];
+            if (partials && valid) {
+                const double l0 = (double)h0 - a_lo * (double)d0, l1 = (double)h1 - a_lo * (double)d1,
+                             l2 = (double)h2 - a_lo * (double)d2;
+                const double u0 = l0 + (double)d0, u1 = l1 + (double)d1, u2 = l2 + (double)d2;
+                eacc += 0.5 * mu *
+                        (l0 * (gm6[0] * u0 + gm6[1] * u1 + gm6[2] * u2) + l1 * (gm6[1] * u0 + gm6[3] * u1 + gm6[4] * u2) +
+                         l2 * (gm6[2] * u0 + gm6[4] * u1 + gm6[5] * u2));
+            }
+            hx[b] = h0 + (real)c_out * d0;
+            hx[NH + b] = h1 + (real)c_out * d1;
+            hx[2 * NH + b] = h2 + (real)c_out * d2;
+        }
+        if (partials && valid) {
+            const double eps = g[kGeoEps];
+            for (int a = w; a < NE; a += W) {
+                const double e0 = ex[a], e1 = ex[NE + a], e2 = ex[2 * NE + a];
+                eacc += 0.5 * eps *
+                        (e0 * (gm6[0] * e0 + gm6[1] * e1 + gm6[2] * e2) + e1 * (gm6[1] * e0 + gm6[3] * e1 + gm6[4] * e2) +
+                         e2 * (gm6[2] * e0 + gm6[4] * e1 + gm6[5] * e2));
+            }
+        }
+        __syncthreads();
+        eg_stage_out(P.H, t0, ne, 3 * NH, sH, L.sOut);
+        eg_traces(sH, NH, L.sOut, P.TrHT, G, sF, L.sF);
+        __syncthreads();
+        eg_stage_out(P.trH, t0, ne, 8 * G, sF, L.sF);
+        __syncthreads();
+    }
+    if (partials) block_energy_store_w(eacc, partials);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kEGMaxWarps * 32, 1) k_phase_E3(KParams<real> P, double dt) {
+    extern __shared__ unsigned char smem_raw[];
+    real* s = reinterpret_cast<real*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int NE = P.NE, NH = P.NH, G = P.N2H;
+    const EGLayout L = eg_layout(NH, NE, G);
+    real* sH = s;
+    real* sF = s + L.oF;
+    real* sE = s + L.oOut;
+    const int64_t ngroups = (P.nt + kEG - 1) / kEG;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t t0 = grp * kEG;
+        const int ne = (int)(P.nt - t0 < kEG ? P.nt - t0 : kEG);
+        eg_stage_in(P.H, t0, ne, 3 * NH, sH, L.sIn);
+        eg_stage_in(P.E, t0, ne, 3 * NE, sE, L.sOut);
+        eg_flux<real, false>(P, P.trH, t0, ne, sF, L.sF);
+        __syncthreads();
+        const bool valid = lane < ne;
+        const double* g = P.geo + (t0 + (valid ? lane : 0)) * kGeoStride;
+        const double ginv[6] = {g[0], g[1], g[2], g[3], g[4], g[5]};
+        const double sT = g[kGeoSign], inv_eps = g[kGeoInvEps];
+        const real* hx = sH + lane * L.sIn;
+        const real* fl = sF + lane * L.sF;
+        real* ex = sE + lane * L.sOut;
+        for (int a = w; a < NE; a += W) {
+            real rx = 0, ry = 0, rz = 0;
+            for (int k = ld(P.ptrE + a), k1 = ld(P.ptrE + a + 1); k < k1; ++k) {
+                const int b = ld(P.idxE + k);
+                const real v = ld(P.valE + k);
+                ry += v * hx[2 * NH + b];
+                rz -= v * hx[NH + b];
+            }
+            for (int k = ld(P.ptrE + (NE + 1) + a), k1 = ld(P.ptrE + (NE + 1) + a + 1); k < k1; ++k) {
+                const int b = ld(P.idxE + k);
+                const real v = ld(P.valE + k);
+                rx -= v * hx[2 * NH + b];
+                rz += v * hx[b];
+            }
+            for (int k = ld(P.ptrE + 2 * (NE + 1) + a), k1 = ld(P.ptrE + 2 * (NE + 1) + a + 1); k < k1; ++k) {
+                const int b = ld(P.idxE + k);
+                const real v = ld(P.valE + k);
+                rx += v * hx[NH + b];
+                ry -= v * hx[b];
+            }
+            real r0 = (real)sT * rx, r1 = (real)sT * ry, r2 = (real)sT * rz;
+            for (int f = 0; f < 4; ++f) {
+                const real* Lf = P.TrEq + (size_t)f * G * NE + a;
+                const real* B0 = fl + f * 2 * G;
+                const real* B1 = B0 + G;
+                real u0 = 0, u1 = 0;
+                for (int gm = 0; gm < G; ++gm) {
+                    const real l = ld(Lf + (size_t)gm * NE);
+                    u0 += l * B0[gm];
+                    u1 += l * B1[gm];
+                }
+                r0 += (real)c_that[f][1][0] * u0 - (real)c_that[f][0][0] * u1;
+                r1 += (real)c_that[f][1][1] * u0 - (real)c_that[f][0][1] * u1;
+                r2 += (real)c_that[f][1][2] * u0 - (real)c_that[f][0][2] * u1;
+            }
+            const real sc = (real)(dt * inv_eps);
+            const real d0 = sc * ((real)ginv[0] * r0 + (real)ginv[1] * r1 + (real)ginv[2] * r2);
+            const real d1 = sc * ((real)ginv[1] * r0 + (real)ginv[3] * r1 + (real)ginv[4] * r2);
+            const real d2 = sc * ((real)ginv[2] * r0 + (real)ginv[4] * r1 + (real)ginv[5] * r2);
+            ex[a] += d0;
+            ex[NE + a] += d1;
+            ex[2 * NE + a] += d2;
+        }
+        __syncthreads();
+        eg_stage_out(P.E, t0, ne, 3 * NE, sE, L.sOut);
+        eg_traces(sE, NE, L.sOut, P.TrEqT, G, sF, L.sF);
+        __syncthreads();
+        eg_stage_out(P.trE, t0, ne, 8 * G, sF, L.sF);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <typename real>
+size_t phase_eg_smem_bytes(const KParams<real>& P) {
+    const EGLayout a = eg_layout(P.NE, P.NH, P.N2H), b = eg_layout(P.NH, P.NE, P.N2H);
+    return (size_t)(a.total > b.total ? a.total : b.total) * sizeof(real);
+}
+
+// warps per block: the one from 8 to 16 that leaves the fewest idle warps over
+// the rows of H, the rows of E and the (face, mode) pairs (ties: more warps)
+int phase_eg_warps(int NE, int NH, int G) {
+    int best = 8;
+    double best_eff = 0.0;
+    for (int W = 8; W <= kEGMaxWarps; ++W) {
+        const int c[3] = {NH, NE, 4 * G};
+        double used = 0.0, slots = 0.0;
+        for (int n : c) {
+            used += n;
+            slots += (double)W * ((n + W - 1) / W);
+        }
+        const double eff = used / slots;
+        if (eff >= best_eff - 1e-12) {
+            best_eff = eff;
+            best = W;
+        }
+    }
+    return best;
+}
+
+template <typename real>
+int launch_phase_H3(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
+                    cudaStream_t s) {
+    const size_t smem = phase_eg_smem_bytes(P);
+    if (cudaFuncSetAttribute(k_phase_H3<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    k_phase_H3<real><<<grid, phase_eg_warps(P.NE, P.NH, P.N2H) * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int launch_phase_E3(const KParams<real>& P, int grid, double dt, cudaStream_t s) {
+    const size_t smem = phase_eg_smem_bytes(P);
+    if (cudaFuncSetAttribute(k_phase_E3<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    k_phase_E3<real><<<grid, phase_eg_warps(P.NE, P.NH, P.N2H) * 32, smem, s>>>(P, dt);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template size_t phase_eg_smem_bytes<double>(const KParams<double>&);
+template size_t phase_eg_smem_bytes<float>(const KParams<float>&);
+template int launch_phase_H3<double>(const KParams<double>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_H3<float>(const KParams<float>&, int, double, double, double, double*, cudaStream_t);
+template int launch_phase_E3<double>(const KParams<double>&, int, double, cudaStream_t);
+template int launch_phase_E3<float>(const KParams<float>&, int, double, cudaStream_t);
+
 }  // namespace dgm

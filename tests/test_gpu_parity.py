@@ -36,8 +36,8 @@ pytestmark = pytest.mark.gpu
 # fp16; the 100-step cavity trajectory deviates 0.32 (max-coefficient measure),
 # bounded by 0.4.  "tc16x2": fp16 field operands with two-term (hi + lo) fp16 tables:
 # the field rounding, and so the per-kick bound, stays that of fp16
-TOL = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-5, "fp32s": 2e-5, "fp32k": 2e-5, "tc32": 3e-3, "tc16": 3e-3, "tc16d": 3e-3, "tcbf16": 2.4e-2, "tc16x2": 3e-3}
-TOL_TRAJ = {"fp64": 1e-12, "fp64s": 1e-12, "fp32": 2e-4, "fp32s": 2e-4, "fp32k": 2e-4, "tc32": 3e-2, "tc16": 3e-2, "tc16d": 3e-2, "tcbf16": 0.4, "tc16x2": 3e-2}
+TOL = {"fp64": 1e-12, "fp64s": 1e-12, "fp64g": 1e-12, "fp32": 2e-5, "fp32s": 2e-5, "fp32g": 2e-5, "fp32k": 2e-5, "tc32": 3e-3, "tc16": 3e-3, "tc16d": 3e-3, "tcbf16": 2.4e-2, "tc16x2": 3e-3}
+TOL_TRAJ = {"fp64": 1e-12, "fp64s": 1e-12, "fp64g": 1e-12, "fp32": 2e-4, "fp32s": 2e-4, "fp32g": 2e-4, "fp32k": 2e-4, "tc32": 3e-2, "tc16": 3e-2, "tc16d": 3e-2, "tcbf16": 0.4, "tc16x2": 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -58,10 +58,13 @@ def _rel(a, b):
 def _solver(capi, m, p, eps, mu=1.0, precision="fp64", flux="central"):
     """precision names as the Solver's, plus: "tc16d" = TC16 on the dense-operator
     kernels (variant 1), "fp64s"/"fp32s" = the sparse-curl CUDA-core kernels (variant 2),
+    "fp64g"/"fp32g" = the element-group CUDA-core kernels (variant 3),
     "fp32k" = FP32 with the compensated (Kahan) update."""
     from paper_1104_4208_gb300.solver import Solver
-    variant = 1 if precision == "tc16d" else 2 if precision in ("fp64s", "fp32s") else 0
-    base = {"tc16d": "tc16", "fp64s": "fp64", "fp32s": "fp32", "fp32k": "fp32"}.get(precision, precision)
+    variant = (1 if precision == "tc16d" else 2 if precision in ("fp64s", "fp32s") else
+               3 if precision in ("fp64g", "fp32g") else 0)
+    base = {"tc16d": "tc16", "fp64s": "fp64", "fp32s": "fp32", "fp64g": "fp64", "fp32g": "fp32",
+            "fp32k": "fp32"}.get(precision, precision)
     return Solver(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key, precision=base, flux=flux, variant=variant,
                   compensated=precision == "fp32k")
 
@@ -87,7 +90,7 @@ def _mesh(name):
     return kuhn_cube_mesh(1, jitter=0.0, seed=1, shuffle_local=True)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32s", "fp32k"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32s", "fp64g", "fp32g", "fp32k"])
 @pytest.mark.parametrize("name,p", _cases())
 def test_kick_parity(capi, name, p, precision):
     """One H-kick and one E-kick (Sec. 3 symplectic Euler halves) vs the oracle."""
@@ -96,6 +99,12 @@ def test_kick_parity(capi, name, p, precision):
     rng = np.random.default_rng(100 + p)
     eps = rng.uniform(1, 4, m.nt)
     mu = rng.uniform(1, 2, m.nt)
+    if precision == "fp64g" and p == 8:
+        # 32 elements of FP64 at p = 8 need 293 KB of shared memory: refused at creation
+        with pytest.raises(capi.DgmError) as e:
+            _solver(capi, m, p, eps, mu, precision)
+        assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+        return
     dg = OracleDG(m.xyz, m.tets, p, eps, mu, vertex_key=m.vertex_key)
     A = dg.assemble()
     S = _solver(capi, m, p, eps, mu, precision)
@@ -115,7 +124,7 @@ def test_kick_parity(capi, name, p, precision):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp32k"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp64s", "fp64g", "fp32g", "fp32k"])
 def test_cavity_trajectory_parity(capi, precision):
     """Workload cavity_n4_p3 (384 tets, p=3, TE110, dt = 0.2h/p^2, 100 steps):
     fields and the per-step discrete energy vs the oracle; energy conserved."""
@@ -190,7 +199,7 @@ def test_sampled_parity_full_pulse_workload(capi, precision):
     S.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp64s", "fp32", "tc32", "tc16", "tc16d", "tcbf16", "tc16x2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64s", "fp64g", "fp32", "tc32", "tc16", "tc16d", "tcbf16", "tc16x2"])
 def test_sampled_parity_full_planewave_workload(capi, precision):
     """Workload planewave_n32_p6 at full size (196,608 tets, periodic, p=6) in the
     launch configuration the benchmark times (autotuned first): one H-kick and
@@ -291,6 +300,13 @@ def test_invalid_arguments(capi):
         with pytest.raises(capi.DgmError) as e:
             Solver(m.xyz, m.tets, 2, 1.0, 1.0, compensated=True, **kw)
         assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+    # ... and not in the element-group kernels; those need the central flux
+    with pytest.raises(capi.DgmError) as e:
+        Solver(m.xyz, m.tets, 2, 1.0, 1.0, precision="fp32", compensated=True, variant=3)
+    assert e.value.code == capi.DGM_ERR_UNSUPPORTED
+    with pytest.raises(capi.DgmError) as e:
+        Solver(m.xyz, m.tets, 2, 1.0, 1.0, precision="fp64", flux="stabilized", variant=3)
+    assert e.value.code == -1
     # autotune needs at least one timed step
     S = Solver(m.xyz, m.tets, 2, 1.0, 1.0, precision="tc16")
     with pytest.raises(capi.DgmError) as e:
@@ -709,8 +725,8 @@ def test_autotune_leaves_results_unchanged(capi, precision):
         assert cfg == [1, 2]        # CTAs per SM of the dense-operator kernels
     elif precision.startswith("tc"):
         assert cfg == [1]           # resident-table kernels: one CTA per SM
-    else:                           # blocks per SM, dense then sparse curl (+1000)
-        assert cfg == [4, 8, 16, 24, 1004, 1008, 1016, 1024]
+    else:                           # blocks per SM: dense, sparse curl (+1000), element groups (+2000)
+        assert cfg == [4, 8, 16, 24, 1004, 1008, 1016, 1024, 2001, 2002]
     E2, H2 = A.get_fields()[:2]
     assert np.array_equal(E1, E2) and np.array_equal(H1, H2)          # dt = 0: fields untouched
     WA = A.run(dt, 20, energies=True)
