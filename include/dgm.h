@@ -129,6 +129,12 @@ typedef struct dgm_options {
                            last update, which is fed back into the next one, so the state
                            accumulates increments to about twice float precision; 8 extra
                            bytes of traffic per coefficient and step.  Default 0 */
+    int equal_order;    /* FP64 and FP32 only (else DGM_ERR_UNSUPPORTED if set): H of degree p
+                           like E (E, H in V^k x V^k) instead of p - 1 (Sec. 2: V^{k+1} x V^k).
+                           The same scheme of Sec. 2.1 and Sec. 3 on the other pair of spaces:
+                           N3(p) coefficients per component for both fields, face traces of
+                           degree p on both sides.  Use it with the stabilized flux: with the
+                           central flux this pair keeps spurious modes.  Default 0 */
 } dgm_options;
 
 typedef struct dgm_ctx dgm_ctx;

@@ -37,7 +37,8 @@ class DgmError(RuntimeError):
 
 class dgm_options(C.Structure):
     _fields_ = [("flux", C.c_int), ("alpha0", C.c_double), ("precision", C.c_int),
-                ("variant", C.c_int), ("checks", C.c_int), ("compensated", C.c_int)]
+                ("variant", C.c_int), ("checks", C.c_int), ("compensated", C.c_int),
+                ("equal_order", C.c_int)]
 
 
 class dgm_run_stats(C.Structure):

@@ -357,6 +357,7 @@ void dgm_default_options(dgm_options* opt) {
     opt->variant = 0;
     opt->checks = 1;
     opt->compensated = 0;
+    opt->equal_order = 0;
 }
 
 int dgm_create(dgm_ctx** ctx, int device) {
@@ -459,6 +460,10 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
             return DGM_ERR_UNSUPPORTED;
         }
     }
+    if (o.equal_order && o.precision != DGM_PREC_FP64 && o.precision != DGM_PREC_FP32) {
+        set_error("dgm_problem_create: the equal-order pair exists for FP64 and FP32");
+        return DGM_ERR_UNSUPPORTED;
+    }
     if (o.compensated && !(o.precision == DGM_PREC_FP32 && o.flux == DGM_FLUX_CENTRAL)) {
         set_error("dgm_problem_create: the compensated update exists for FP32 with the central flux");
         return DGM_ERR_UNSUPPORTED;
@@ -474,7 +479,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     P->ctx = ctx;
     P->p = p;
     P->opt = o;
-    int rc = dgm::build_ref_tables(p, P->tab);
+    int rc = dgm::build_ref_tables(p, P->tab, o.equal_order != 0);
     if (rc) {
         delete P;
         return rc;
@@ -653,7 +658,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
     {
         std::vector<double> nrmE(P->NE), nrmH(P->NH);
         std::vector<int> iH;
-        dgm::index3(p - 1, iH);
+        dgm::index3(P->tab.ph, iH);
         for (int a = 0; a < P->NE; ++a) nrmE[a] = std::sqrt(P->tab.norm2E[a]);
         for (int b = 0; b < P->NH; ++b) nrmH[b] = std::sqrt(dgm::dubiner3_norm2(iH[3 * b], iH[3 * b + 1], iH[3 * b + 2]));
         if ((e = cudaMalloc(&P->dNrmE, P->NE * sizeof(double))) != cudaSuccess) return fail(cuda_fail(e, "alloc nrm"));
@@ -679,6 +684,7 @@ int dgm_problem_create(dgm_ctx* ctx, const dgm_mesh* mesh, int p, const double* 
             return fail(DGM_ERR_UNSUPPORTED);
         }
         P->grid = std::min(P->grid_cap, ctx->num_sms);
+        P->kd.eg_warps = P->kf.eg_warps = dgm::phase_eg_warps(P->NE, P->NH, P->N2H, 16);
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(cuda_fail(e, "setup"));
     *out = P;
@@ -1200,10 +1206,12 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
             P->grid = std::min(P->grid_cap, sms * (c % 1000));
             P->kd.sparse = P->kf.sparse = c >= 1000 ? 1 : 0;
             P->kd.eg = P->kf.eg = c >= 2000 ? 1 : 0;
+            if (c >= 2000)   // one block per SM: up to 16 warps; two: 8 each (the SM's registers)
+                P->kd.eg_warps = P->kf.eg_warps = dgm::phase_eg_warps(P->NE, P->NH, P->N2H, 16 / (c - 2000));
         }
     };
     const int keep_grid = P->grid, keep_tc = P->tc_grid, keep_sparse = P->kd.sparse | P->kf.sparse,
-              keep_eg = P->kd.eg | P->kf.eg;
+              keep_eg = P->kd.eg | P->kf.eg, keep_egw = P->kd.eg_warps | P->kf.eg_warps;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DGM_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1234,6 +1242,7 @@ int dgm_autotune(dgm_problem* P, int steps, int* ncand_out, int* cand_config, do
         P->tc_grid = keep_tc;
         P->kd.sparse = P->kf.sparse = keep_sparse;
         P->kd.eg = P->kf.eg = keep_eg;
+        P->kd.eg_warps = P->kf.eg_warps = keep_egw;
         if (P->tc) P->tca.partH = P->tca.partE + P->tc_grid;
         return rc;
     }
@@ -1937,7 +1946,7 @@ static int ensure_rule(dgm_problem* P, int q1d) {
     std::vector<double> x, w, col, phE, phH;
     dgm::collapsed_rule(q1d, x, w, col);
     dgm::phi_table(P->p, q1d, phE);
-    dgm::phi_table(P->p - 1, q1d, phH);
+    dgm::phi_table(P->tab.ph, q1d, phH);
     const int nq = (int)w.size();
     std::vector<double> wE(phE.size()), wH(phH.size());
     for (int q = 0; q < nq; ++q) {

@@ -18,21 +18,22 @@ void set_error(const std::string& msg);
 // Reference operators of the orthonormalised Dubiner basis phi_a / ||phi_a||
 // (Sec. 3.2.2 gradients, Sec. 3.2.3 traces), FP64.
 struct RefTables {
-    int p = 0, NE = 0, NH = 0, N2E = 0, N2H = 0;
+    int p = 0, ph = 0, NE = 0, NH = 0, N2E = 0, N2H = 0;   // ph: degree of H (p - 1, or p)
     std::vector<double> norm2E;          // [NE] ||phi_a||^2 (unnormalised basis)
-    std::vector<double> D[3];            // [NH][NE]  (d_d phi'_a, phi'_b)
+    std::vector<double> D[3];            // [NH][NE]  (d_d phi'_a, phi'_b), b over H's basis
     std::vector<double> TrE[4];          // [N2E][NE] (phi'_a|_f, psi'_g) over degree-p face modes
-    std::vector<double> TrH[4];          // [N2H][NH] (phi'_b|_f, psi'_g) for the degree p-1 basis
+    std::vector<double> TrH[4];          // [N2H][NH] (phi'_b|_f, psi'_g) for H's basis (degree ph)
     // Face-frame tangents of local face f in reference coordinates:
     // that[f][i][m], i = 0,1 (t_1 = v_b - v_a, t_2 = v_c - v_a).
     double that[4][2][3];
     // sign of nu_hat . (t_1 x t_2) for the outward reference normal of face f
     double sigma_hat[4];
-    // position of each degree-(p-1) face index (i,j) inside the degree-p list
+    // position of each degree-ph face index (i,j) inside the degree-p list
     std::vector<int> pos2H;              // [N2H]
 };
 
-int build_ref_tables(int p, RefTables& t);
+// equal_order: H of degree p like E (else p - 1)
+int build_ref_tables(int p, RefTables& t, bool equal_order = false);
 // Squared norm of the unnormalised 3D Dubiner function (closed form).
 double dubiner3_norm2(int i, int j, int k);
 double dubiner2_norm2(int i, int j);

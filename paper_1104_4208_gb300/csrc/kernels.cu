@@ -1210,12 +1210,15 @@ size_t phase_eg_smem_bytes(const KParams<real>& P) {
     return (size_t)(a.total > b.total ? a.total : b.total) * sizeof(real);
 }
 
-// warps per block: the one from 8 to 16 that leaves the fewest idle warps over
-// the rows of H, the rows of E and the (face, mode) pairs (ties: more warps)
-int phase_eg_warps(int NE, int NH, int G) {
+// warps per block: the one from 8 to wmax (<= 16) that leaves the fewest idle
+// warps over the rows of H, the rows of E and the (face, mode) pairs (ties: more
+// warps); wmax = 8 when two blocks share an SM, whose registers hold 16 warps
+int phase_eg_warps(int NE, int NH, int G, int wmax) {
+    if (wmax > kEGMaxWarps) wmax = kEGMaxWarps;
+    if (wmax < 8) wmax = 8;
     int best = 8;
     double best_eff = 0.0;
-    for (int W = 8; W <= kEGMaxWarps; ++W) {
+    for (int W = 8; W <= wmax; ++W) {
         const int c[3] = {NH, NE, 4 * G};
         double used = 0.0, slots = 0.0;
         for (int n : c) {
@@ -1235,18 +1238,20 @@ template <typename real>
 int launch_phase_H3(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
                     cudaStream_t s) {
     const size_t smem = phase_eg_smem_bytes(P);
+    if (P.eg_warps < 1 || P.eg_warps > kEGMaxWarps) return -1;
     if (cudaFuncSetAttribute(k_phase_H3<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    k_phase_H3<real><<<grid, phase_eg_warps(P.NE, P.NH, P.N2H) * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
+    k_phase_H3<real><<<grid, P.eg_warps * 32, smem, s>>>(P, dt, a_lo, c_out, partials);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename real>
 int launch_phase_E3(const KParams<real>& P, int grid, double dt, cudaStream_t s) {
     const size_t smem = phase_eg_smem_bytes(P);
+    if (P.eg_warps < 1 || P.eg_warps > kEGMaxWarps) return -1;
     if (cudaFuncSetAttribute(k_phase_E3<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    k_phase_E3<real><<<grid, phase_eg_warps(P.NE, P.NH, P.N2H) * 32, smem, s>>>(P, dt);
+    k_phase_E3<real><<<grid, P.eg_warps * 32, smem, s>>>(P, dt);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

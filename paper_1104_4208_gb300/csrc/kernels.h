@@ -50,6 +50,7 @@ struct KParams {
     real* cH;
     int sparse;                 // 1: the trace-buffer kernels apply the curl in sparse form
     int eg;                     // 1: element-group kernels (32 elements per block, lane = element)
+    int eg_warps;               // their warps per block (phase_eg_warps)
     const int32_t* ptrH;        // [3][NH+1]
     const int32_t* idxH;
     const real* valH;
@@ -94,12 +95,12 @@ int launch_phase_E2(const KParams<real>& P, int grid, double dt, cudaStream_t s)
 template <typename real>
 int launch_traces2(const KParams<real>& P, int grid, int which, int64_t e0, int64_t e1, cudaStream_t s);
 // element-group phase kernels (central flux, trace buffers, sparse curl): `grid`
-// blocks of 32 phase_eg_warps(NE, NH, N2H) threads and phase_eg_smem_bytes(P)
-// bytes of shared memory, each taking groups of 32 elements in turn; the H-phase
-// writes one energy partial per block
+// blocks of 32 P.eg_warps threads and phase_eg_smem_bytes(P) bytes of shared
+// memory, each taking groups of 32 elements in turn; the H-phase writes one
+// energy partial per block
 template <typename real>
 size_t phase_eg_smem_bytes(const KParams<real>& P);
-int phase_eg_warps(int NE, int NH, int G);
+int phase_eg_warps(int NE, int NH, int G, int wmax);
 template <typename real>
 int launch_phase_H3(const KParams<real>& P, int grid, double dt, double a_lo, double c_out, double* partials,
                     cudaStream_t s);

@@ -279,17 +279,20 @@ void phi_at_points(int p, const double* xh, int n, std::vector<double>& out) {
     }
 }
 
-int build_ref_tables(int p, RefTables& t) {
+int build_ref_tables(int p, RefTables& t, bool equal_order) {
     if (p < 1 || p > DGM_PMAX) {
         set_error("p must be in [1, DGM_PMAX]");
         return DGM_ERR_INVALID_ARG;
     }
+    // degree of H: p - 1 (V^{k+1} x V^k, Sec. 2) or p (the equal-order pair)
+    const int ph = equal_order ? p : p - 1;
     std::vector<int> iE, iH, i2E, i2H;
     index3(p, iE);
-    index3(p - 1, iH);
+    index3(ph, iH);
     index2(p, i2E);
-    index2(p - 1, i2H);
+    index2(ph, i2H);
     t.p = p;
+    t.ph = ph;
     t.NE = (int)iE.size() / 3;
     t.NH = (int)iH.size() / 3;
     t.N2E = (int)i2E.size() / 2;
@@ -297,7 +300,7 @@ int build_ref_tables(int p, RefTables& t) {
     t.norm2E.resize(t.NE);
     for (int a = 0; a < t.NE; ++a) t.norm2E[a] = dubiner3_norm2(iE[3 * a], iE[3 * a + 1], iE[3 * a + 2]);
 
-    // derivative tables: (d_d phi'_a, phi'_b), b over the degree p-1 basis
+    // derivative tables: (d_d phi'_a, phi'_b), b over the basis of H's degree
     const int nq = p + 2;
     std::vector<double> gx, gw;
     gauss_legendre01(nq, gx, gw);
@@ -309,7 +312,7 @@ int build_ref_tables(int p, RefTables& t) {
                 const double xi = gx[a], eta = gx[b], zeta = gx[c];
                 const double w = gw[a] * gw[b] * gw[c] * (1.0 - xi) * (1.0 - xi) * (1.0 - eta);
                 phi3_at(p, iE, xi, eta, zeta, v.data(), dx.data(), dy.data(), dz.data());
-                phi3_at(p - 1, iH, xi, eta, zeta, vh.data(), nullptr, nullptr, nullptr);
+                phi3_at(ph, iH, xi, eta, zeta, vh.data(), nullptr, nullptr, nullptr);
                 for (int bb = 0; bb < t.NH; ++bb) {
                     const double wb = w * vh[bb];
                     double* Dx = &t.D[0][(size_t)bb * t.NE];
@@ -344,7 +347,7 @@ int build_ref_tables(int p, RefTables& t) {
     }
     for (int f = 0; f < 4; ++f) {
         face_trace(p, f, t.TrE[f]);
-        face_trace(p - 1, f, t.TrH[f]);
+        face_trace(ph, f, t.TrH[f]);
     }
     // face frames and reference orientation signs
     const double nhat[4][3] = {{1, 1, 1}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}};

@@ -12,7 +12,7 @@ class Solver:
     """mesh + p + eps + mu -> device-resident DG Maxwell problem (include/dgm.h)."""
 
     def __init__(self, xyz, tets, p, eps, mu, vertex_key=None, precision="fp64",
-                 flux="central", alpha0=1.0, device=0, variant=0, compensated=False):
+                 flux="central", alpha0=1.0, device=0, variant=0, compensated=False, equal_order=False):
         self.ctx = capi.dgm_create(device)
         self.mesh = capi.dgm_mesh_create(self.ctx, xyz, tets, vertex_key)
         self.nt, self.nfaces, self.nboundary = capi.dgm_mesh_info(self.mesh)
@@ -22,6 +22,7 @@ class Solver:
                          "tcbf16": capi.DGM_PREC_TCBF16, "tc16x2": capi.DGM_PREC_TC16X2}[precision]
         opt.variant = variant
         opt.compensated = 1 if compensated else 0
+        opt.equal_order = 1 if equal_order else 0
         opt.flux = {"central": capi.DGM_FLUX_CENTRAL, "stabilized": capi.DGM_FLUX_STABILIZED}[flux]
         opt.alpha0 = alpha0
         eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.nt,))
