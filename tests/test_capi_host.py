@@ -41,6 +41,31 @@ def test_version_and_defaults(capi):
     assert capi.dgm_version() >= 100
     o = capi.dgm_default_options()
     assert o.flux == capi.DGM_FLUX_CENTRAL and o.precision == capi.DGM_PREC_FP64 and o.alpha0 == 1.0
+    assert o.variant == 0 and o.compensated == 0 and o.equal_order == 0
+
+
+def test_options_struct_layout_matches_header(capi, tmp_path):
+    """The binding's dgm_options has the C struct's size and field offsets."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in capi.dgm_options._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("{f} %zu\\n", offsetof(dgm_options, {f}));\n' for f in fields)
+    src.write_text('#include "dgm.h"\n#include <stddef.h>\n#include <stdio.h>\nint main(void) {\n'
+                   '    printf("size %zu\\n", sizeof(dgm_options));\n' + body + '    return 0;\n}\n')
+    exe = tmp_path / "layout.out"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         timeout=60).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(capi.dgm_options)
+    for f in fields:
+        assert int(out[f]) == getattr(capi.dgm_options, f).offset, f
 
 
 def _oracle_tables(p):
