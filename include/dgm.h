@@ -12,7 +12,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - p is the polynomial degree of E; H has degree p-1 (Sec. 2: E in V^{k+1},
- *    H in V^k).  1 <= p <= DGM_PMAX.
+ *    H in V^k), or p with the equal_order option.  1 <= p <= DGM_PMAX.
  *  - Element map: the four vertices of each tetrahedron are re-ordered by
  *    ascending vertex key (vertex_key[v] if given, else the vertex id v);
  *    Phi(xh) = X0 + F xh, F = [X1-X0, X2-X0, X3-X0] (Sec. 3.2.1).
@@ -21,7 +21,8 @@
  *    printed (unnormalised), multi-indices a = (i,j,k), i+j+k <= p, ordered
  *    lexicographically with i outermost and k innermost.
  *  - Canonical field layout (host and device arrays, FP64):
- *      E [nt][3][N3(p)],  H [nt][3][N3(p-1)],  N3(q) = (q+1)(q+2)(q+3)/6.
+ *      E [nt][3][N3(p)],  H [nt][3][N3(p-1)] (N3(p) with equal_order),
+ *      N3(q) = (q+1)(q+2)(q+3)/6.
  *  - Face unknowns H^F (stabilized flux only): H^F = sum_g psi_g (K_1g t^1 +
  *    K_2g t^2) with psi the 2D Dubiner basis of Eq. (4) in the face
  *    parametrisation x = X_a + s t_1 + u t_2, t_1 = X_b - X_a, t_2 = X_c - X_a

@@ -26,7 +26,7 @@ struct KParams {
     const int32_t* nbr;         // [nt][4] = 4*neighbour + neighbour's local face, or -1 (PEC)
     const real* DT;             // [3][NE][NH]   D_d transposed
     const real* D;              // [3][NH][NE]
-    const real* TrEqT;          // [4][NE][N2H]  E trace onto degree <= p-1 face modes, transposed
+    const real* TrEqT;          // [4][NE][N2H]  E trace onto the face modes up to H's degree, transposed
     const real* TrEq;           // [4][N2H][NE]
     const real* TrHT;           // [4][NH][N2H]  H trace, transposed
     const real* TrH;            // [4][N2H][NH]
@@ -37,7 +37,7 @@ struct KParams {
     const real* TrEfT;          // [4][NE][N2E]  E trace onto all degree <= p face modes, transposed
     const real* TrEf;           // [4][N2E][NE]
     // central flux, trace-buffer kernels: tangential face traces of E and H on the
-    // degree <= p-1 face modes, [nt][4 faces][2 tangents][N2H], written by the phase
+    // face modes up to H's degree, [nt][4 faces][2 tangents][N2H], written by the phase
     // that updates the field and read (own and neighbour side) by the other phase
     real* trE;
     real* trH;
