@@ -17,7 +17,9 @@ What it computes is the plain definition of the method:
     evaluated at the same physical point through the neighbour's own inverse
     map -- no reference-element identities, no recurrences, no face frames;
   * block mass matrices assembled by quadrature and inverted by Cholesky;
-  * symplectic Euler / leapfrog of Sec. 3 and the discrete energy of Sec. 2.1.
+  * symplectic Euler / leapfrog of Sec. 3 and the discrete energy of Sec. 2.1;
+  * the same scheme for 2D TE fields on triangles (``dg2d``: E in the plane,
+    H along z, the Eq. (4) basis), the oracle of a 2D triangle solver.
 
 Readings of the paper taken here (the same as the CUDA path's):
   * p is the degree of E; H has degree p-1 (Sec. 2, spaces V^{k+1}, V^k).
