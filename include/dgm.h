@@ -459,6 +459,24 @@ int dgm_grad_sweep(int p, int dir, const double* a, double* b, int* swept);
  * returned in *needed. */
 int dgm_reference_table(int p, int which, double* out, int64_t count, int64_t* needed);
 
+/* Reference tables of the 2D triangle solver (host, FP64, orthonormalised
+ * Dubiner basis psi_a / ||psi_a|| of Eq. (4) on the reference triangle with
+ * vertices (0,0), (1,0), (0,1)).  The 2D TE fields: E in the plane of degree p,
+ * H along z of degree p - 1 (Sec. 2's pair of spaces in two dimensions); the
+ * derivative tables are those whose sparsity the printed 2D relations of
+ * Sec. 4.2.1 describe, the traces those of Sec. 3.2.3 on edges:
+ *   which = 0,1  : D_x, D_y  [N2(p-1)][N2(p)], entry (b,a) = (d psi_a, psi_b)
+ *   which = 2..4 : E trace on edge which-2  [p+1][N2(p)], entry (g,a) =
+ *                  int_0^1 psi_a(edge point at s) L_g(s) ds
+ *   which = 5..7 : H trace on edge which-5  [p][N2(p-1)], the same
+ *   which = 8    : squared norms ||psi_a||^2 [N2(p)]
+ * Edge f is opposite reference vertex f, parametrised from its lower-numbered
+ * vertex to its higher one; L_g = sqrt(2g+1) P_g(2s-1), orthonormal on [0,1].
+ * Needs no GPU.  `count` = capacity of `out` in doubles; the required size is
+ * returned in *needed.  Errors: DGM_ERR_INVALID_ARG for p outside [1, DGM_PMAX],
+ * `which` out of range or `out` too small. */
+int dgm_reference_table_2d(int p, int which, double* out, int64_t count, int64_t* needed);
+
 #ifdef __cplusplus
 }
 #endif

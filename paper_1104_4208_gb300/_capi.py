@@ -89,6 +89,7 @@ _SIGS = {
     "dgm_inject_wait_timeout": ([_vp, C.c_int], C.c_int),
     "dgm_measure_fp64_peak": ([C.c_int, C.c_int, _pd], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
+    "dgm_reference_table_2d": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
     "dgm_batch_create": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)], C.c_int),
     "dgm_batch_destroy": ([_vp], C.c_int),
@@ -318,6 +319,14 @@ def dgm_reference_table(p, which):
     _check(_lib.dgm_reference_table(int(p), int(which), None, 0, C.byref(need)))
     out = np.empty(need.value)
     _check(_lib.dgm_reference_table(int(p), int(which), _dptr(out), need.value, C.byref(need)))
+    return out
+
+
+def dgm_reference_table_2d(p, which):
+    need = _i64()
+    _check(_lib.dgm_reference_table_2d(int(p), int(which), None, 0, C.byref(need)))
+    out = np.empty(need.value)
+    _check(_lib.dgm_reference_table_2d(int(p), int(which), _dptr(out), need.value, C.byref(need)))
     return out
 
 

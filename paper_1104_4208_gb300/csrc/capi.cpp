@@ -2054,6 +2054,30 @@ int dgm_reference_table(int p, int which, double* out, int64_t count, int64_t* n
     return DGM_OK;
 }
 
+int dgm_reference_table_2d(int p, int which, double* out, int64_t count, int64_t* needed) {
+    dgm::RefTables2D t;
+    int rc = dgm::build_ref_tables_2d(p, t);
+    if (rc) return rc;
+    const std::vector<double>* v = nullptr;
+    if (which >= 0 && which <= 1) v = &t.D[which];
+    else if (which >= 2 && which <= 4) v = &t.TrE[which - 2];
+    else if (which >= 5 && which <= 7) v = &t.TrH[which - 5];
+    else if (which == 8) v = &t.norm2E;
+    else {
+        set_error("dgm_reference_table_2d: which out of range");
+        return DGM_ERR_INVALID_ARG;
+    }
+    if (needed) *needed = (int64_t)v->size();
+    if (out) {
+        if (count < (int64_t)v->size()) {
+            set_error("dgm_reference_table_2d: output too small");
+            return DGM_ERR_INVALID_ARG;
+        }
+        std::memcpy(out, v->data(), v->size() * sizeof(double));
+    }
+    return DGM_OK;
+}
+
 int dgm_quad_points(dgm_problem* P, int q1d, int64_t* count, double* xyz) {
     if (!P || !count || q1d < 1 || q1d > 32) {
         set_error("dgm_quad_points: bad argument");

@@ -34,6 +34,23 @@ struct RefTables {
 
 // equal_order: H of degree p like E (else p - 1)
 int build_ref_tables(int p, RefTables& t, bool equal_order = false);
+
+// Reference operators of the 2D triangle solver (TE fields: E in the plane of
+// degree p, H along z of degree p - 1), orthonormalised Dubiner basis psi_a of
+// Eq. (4) on the reference triangle (0,0), (1,0), (0,1):
+//   D[d]  [N2(p-1)][N2(p)]   (d_d psi'_a, psi'_b), d = x, y
+//   TrE[f] [p+1][N2(p)]      int_0^1 psi'_a(edge f at s) L'_g(s) ds, g <= p
+//   TrH[f] [p][N2(p-1)]      the same for the degree p - 1 basis, g <= p - 1
+// Edge f is opposite reference vertex f, parametrised from its lower-numbered
+// vertex to its higher one; L'_g = sqrt(2g+1) P_g(2s-1), orthonormal on [0,1].
+struct RefTables2D {
+    int p = 0, NE = 0, NH = 0;
+    std::vector<double> norm2E;          // [NE] ||psi_a||^2 (unnormalised basis)
+    std::vector<double> D[2];
+    std::vector<double> TrE[3];
+    std::vector<double> TrH[3];
+};
+int build_ref_tables_2d(int p, RefTables2D& t);
 // Squared norm of the unnormalised 3D Dubiner function (closed form).
 double dubiner3_norm2(int i, int j, int k);
 double dubiner2_norm2(int i, int j);

@@ -387,4 +387,118 @@ void phi3_grad(int p, const std::vector<int>& idx, double xi, double eta, double
     }
 }
 
+namespace {
+
+// psi_ij (Eq. (4)) and its Cartesian derivatives at the collapsed point (a, b):
+// s = a, u = (1-a) b, psi = P_i(2b-1) (1-a)^i P_j^(2i+1,0)(2a-1);
+// d/ds = d/da + b/(1-a) d/db, d/du = 1/(1-a) d/db.
+void psi2_grad_at(int p, const std::vector<int>& idx, double a, double b, double* val, double* ds, double* du) {
+    const int N = (int)idx.size() / 2;
+    std::vector<double> L(p + 1), Ld(p + 1), J(p + 1), Jd(p + 1);
+    jacobi_d(p, 0.0, 2.0 * b - 1.0, L.data(), Ld.data());
+    const double om = 1.0 - a;
+    int lasti = -1;
+    for (int r = 0; r < N; ++r) {
+        const int i = idx[2 * r], j = idx[2 * r + 1];
+        if (i != lasti) {
+            jacobi_d(p - i, 2.0 * i + 1.0, 2.0 * a - 1.0, J.data(), Jd.data());
+            lasti = i;
+        }
+        const double A = L[i], Ab = 2.0 * Ld[i];
+        const double B = ipow(om, i) * J[j];
+        const double Ba = (i > 0 ? -i * ipow(om, i - 1) * J[j] : 0.0) + ipow(om, i) * 2.0 * Jd[j];
+        val[r] = A * B;
+        if (ds) {
+            ds[r] = A * Ba + b / om * Ab * B;
+            du[r] = Ab * B / om;
+        }
+    }
+}
+
+const double kVert2[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+
+// T[g][a] = int_0^1 psi'_a(edge f at s) L'_g(s) ds, g <= p
+void edge_trace(int p, int f, std::vector<double>& T) {
+    std::vector<int> i2;
+    index2(p, i2);
+    const int N = (int)i2.size() / 2, NG = p + 1;
+    int v[2], c = 0;
+    for (int q = 0; q < 3; ++q)
+        if (q != f) v[c++] = q;
+    std::vector<double> xs, ws;
+    gauss_legendre01(p + 2, xs, ws);
+    std::vector<double> psi(N), leg(NG);
+    T.assign((size_t)NG * N, 0.0);
+    for (size_t q = 0; q < xs.size(); ++q) {
+        const double s = xs[q];
+        const double x = kVert2[v[0]][0] + s * (kVert2[v[1]][0] - kVert2[v[0]][0]);
+        const double y = kVert2[v[0]][1] + s * (kVert2[v[1]][1] - kVert2[v[0]][1]);
+        // collapsed coordinates of (x, y); the vertex (1, 0) itself is never a Gauss point
+        const double a = x, b = x < 1.0 ? y / (1.0 - x) : 0.0;
+        psi2_at(p, i2, a, b, psi.data());
+        jacobi_all(p, 0.0, 0.0, 2.0 * s - 1.0, leg.data());
+        for (int g = 0; g < NG; ++g)
+            for (int r = 0; r < N; ++r)
+                T[(size_t)g * N + r] += ws[q] * std::sqrt(2.0 * g + 1.0) * leg[g] * psi[r];
+    }
+    for (int r = 0; r < N; ++r) {
+        const double nr = std::sqrt(dubiner2_norm2(i2[2 * r], i2[2 * r + 1]));
+        for (int g = 0; g < NG; ++g) T[(size_t)g * N + r] /= nr;
+    }
+}
+
+}  // namespace
+
+int build_ref_tables_2d(int p, RefTables2D& t) {
+    if (p < 1 || p > DGM_PMAX) {
+        set_error("p must be in [1, DGM_PMAX]");
+        return DGM_ERR_INVALID_ARG;
+    }
+    std::vector<int> iE, iH;
+    index2(p, iE);
+    index2(p - 1, iH);
+    t.p = p;
+    t.NE = (int)iE.size() / 2;
+    t.NH = (int)iH.size() / 2;
+    t.norm2E.resize(t.NE);
+    for (int a = 0; a < t.NE; ++a) t.norm2E[a] = dubiner2_norm2(iE[2 * a], iE[2 * a + 1]);
+    // (d_d psi'_a, psi'_b) by collapsed Gauss quadrature (exact: degree <= 2p - 1)
+    const int nq = p + 2;
+    std::vector<double> ga, wa;
+    gauss_legendre01(nq, ga, wa);
+    for (int d = 0; d < 2; ++d) t.D[d].assign((size_t)t.NH * t.NE, 0.0);
+    std::vector<double> v(t.NE), ds(t.NE), du(t.NE), vh(t.NH);
+    for (int qa = 0; qa < nq; ++qa)
+        for (int qb = 0; qb < nq; ++qb) {
+            const double a = ga[qa], b = ga[qb];
+            const double w = wa[qa] * wa[qb] * (1.0 - a);
+            psi2_grad_at(p, iE, a, b, v.data(), ds.data(), du.data());
+            psi2_at(p - 1, iH, a, b, vh.data());
+            for (int r = 0; r < t.NH; ++r)
+                for (int c = 0; c < t.NE; ++c) {
+                    t.D[0][(size_t)r * t.NE + c] += w * vh[r] * ds[c];
+                    t.D[1][(size_t)r * t.NE + c] += w * vh[r] * du[c];
+                }
+        }
+    for (int r = 0; r < t.NH; ++r) {
+        const double nb = std::sqrt(dubiner2_norm2(iH[2 * r], iH[2 * r + 1]));
+        for (int c = 0; c < t.NE; ++c) {
+            const double na = std::sqrt(t.norm2E[c]);
+            for (int d = 0; d < 2; ++d) t.D[d][(size_t)r * t.NE + c] /= (na * nb);
+        }
+    }
+    // exact zeros left at quadrature round-off, as for the 3D tables
+    double mx = 0.0;
+    for (int d = 0; d < 2; ++d)
+        for (double x : t.D[d]) mx = std::max(mx, std::fabs(x));
+    for (int d = 0; d < 2; ++d)
+        for (double& x : t.D[d])
+            if (std::fabs(x) < 1e-12 * mx) x = 0.0;
+    for (int f = 0; f < 3; ++f) {
+        edge_trace(p, f, t.TrE[f]);
+        edge_trace(p - 1, f, t.TrH[f]);
+    }
+    return DGM_OK;
+}
+
 }  // namespace dgm
