@@ -477,6 +477,43 @@ int dgm_reference_table(int p, int which, double* out, int64_t count, int64_t* n
  * `which` out of range or `out` too small. */
 int dgm_reference_table_2d(int p, int which, double* out, int64_t count, int64_t* needed);
 
+/* 2D triangle solver (TE fields).  E = (E_x, E_y) in the plane, covariant of
+ * degree p: E|_T(x) = F^{-T} sum_a c_{m,a} e_m psi_a(Phi^{-1} x), m = 0, 1, with
+ * psi the printed (unnormalised) Dubiner basis of Eq. (4), multi-indices (i,j),
+ * i+j <= p, lexicographic with i outermost; H = H_z scalar of degree p - 1:
+ * H|_T(x) = sum_b d_b psi_b(Phi^{-1} x).  The triangle's vertices are ordered by
+ * ascending key (vertex_key[v] if given, else v), Phi(xh) = X0 + F xh,
+ * F = [X1-X0, X2-X0].  The scheme is the central-flux system of Sec. 2.1 for
+ * these fields (eps dE/dt = curl H, mu dH/dt = -curl E, curl E = d_x E_y - d_y E_x,
+ * curl H = (d_y H, -d_x H)), with the leapfrog of Sec. 3:
+ *   d/dt (eps E, e)_T = (H, curl e)_T - ({{H}}, n x e)_dT
+ *   d/dt (mu H, h)_T  = -(curl E, h)_T + (1/2 n x [[E]], h)_dT
+ * n x v = n_x v_y - n_y v_x, [[E]] = E_T - E_nbr, {{H}} = (H_T + H_nbr)/2; edges
+ * without a partner are PEC walls (ghost E_nbr = -E_T tangentially, H_nbr = H_T);
+ * two edges whose two keys coincide are glued (periodic).  FP64 or FP32
+ * (`precision` DGM_PREC_FP64 / DGM_PREC_FP32; else DGM_ERR_UNSUPPORTED).
+ * Layouts (host arrays, FP64): E [nt][2][N2(p)], H [nt][N2(p-1)].
+ * Errors of create: DGM_ERR_INVALID_ARG for ids out of range, repeated keys in
+ * one triangle, degenerate triangles (|det F| <= 1e-12 (max edge component)^2),
+ * edges shared by more than two triangles, a triangle glued to itself,
+ * non-positive eps or mu, p outside [1, DGM_PMAX]. */
+typedef struct dgm_problem2d dgm_problem2d;
+int dgm_problem2d_create(dgm_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tris,
+                         const int32_t* vertex_key, int p, const double* eps, const double* mu, int precision,
+                         dgm_problem2d** out);
+int dgm_problem2d_destroy(dgm_problem2d* prob);
+/* Lengths (in doubles) of the canonical E and H arrays. */
+int dgm_problem2d_sizes(const dgm_problem2d* prob, int64_t* nE, int64_t* nH);
+int dgm_set_fields2d(dgm_problem2d* prob, const double* E, const double* H);
+int dgm_get_fields2d(dgm_problem2d* prob, double* E, double* H);
+/* One half of the symplectic Euler step: which = 0 advances H by dt from the
+ * current E, which = 1 advances E by dt from the current H. */
+int dgm_kick2d(dgm_problem2d* prob, int which, double dt);
+/* nsteps leapfrog steps with the opening and closing half kicks of H, as
+ * dgm_run; energy_out (nullable, nsteps + 1 values) receives the modified energy
+ * W^n = 1/2 (eps E^n, E^n) + 1/2 (mu H^{n-1/2}, H^{n+1/2}), n = 0..nsteps. */
+int dgm_run2d(dgm_problem2d* prob, double dt, int64_t nsteps, void* stream, double* energy_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,14 @@ _SIGS = {
     "dgm_measure_fp64_peak": ([C.c_int, C.c_int, _pd], C.c_int),
     "dgm_reference_table": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_reference_table_2d": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
+    "dgm_problem2d_create": ([_vp, _i64, _pd, _i64, _pi32, _pi32, C.c_int, _pd, _pd, C.c_int, C.POINTER(_vp)],
+                             C.c_int),
+    "dgm_problem2d_destroy": ([_vp], C.c_int),
+    "dgm_problem2d_sizes": ([_vp, _pi64, _pi64], C.c_int),
+    "dgm_set_fields2d": ([_vp, _pd, _pd], C.c_int),
+    "dgm_get_fields2d": ([_vp, _pd, _pd], C.c_int),
+    "dgm_kick2d": ([_vp, C.c_int, C.c_double], C.c_int),
+    "dgm_run2d": ([_vp, C.c_double, _i64, _vp, _pd], C.c_int),
     "dgm_quad_rule": ([C.c_int, C.POINTER(C.c_int), _pd, _pd], C.c_int),
     "dgm_batch_create": ([_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)], C.c_int),
     "dgm_batch_destroy": ([_vp], C.c_int),
@@ -328,6 +336,51 @@ def dgm_reference_table_2d(p, which):
     out = np.empty(need.value)
     _check(_lib.dgm_reference_table_2d(int(p), int(which), _dptr(out), need.value, C.byref(need)))
     return out
+
+
+def dgm_problem2d_create(ctx, xy, tris, p, eps, mu, vertex_key=None, precision=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    key = None if vertex_key is None else np.ascontiguousarray(vertex_key, dtype=np.int32)
+    nt = tris.shape[0]
+    eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (nt,)))
+    mu = np.ascontiguousarray(np.broadcast_to(np.asarray(mu, dtype=np.float64), (nt,)))
+    h = _vp()
+    _check(_lib.dgm_problem2d_create(ctx, xy.shape[0], _dptr(xy), nt, tris.ctypes.data_as(_pi32),
+                                     None if key is None else key.ctypes.data_as(_pi32), int(p), _dptr(eps),
+                                     _dptr(mu), DGM_PREC_FP64 if precision is None else int(precision),
+                                     C.byref(h)))
+    return h
+
+
+def dgm_problem2d_destroy(prob):
+    _check(_lib.dgm_problem2d_destroy(prob))
+
+
+def dgm_problem2d_sizes(prob):
+    a, b = _i64(), _i64()
+    _check(_lib.dgm_problem2d_sizes(prob, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def dgm_set_fields2d(prob, E=None, H=None):
+    E = None if E is None else np.ascontiguousarray(E, dtype=np.float64)
+    H = None if H is None else np.ascontiguousarray(H, dtype=np.float64)
+    _check(_lib.dgm_set_fields2d(prob, _dptr(E), _dptr(H)))
+
+
+def dgm_get_fields2d(prob, E, H):
+    _check(_lib.dgm_get_fields2d(prob, _dptr(E), _dptr(H)))
+
+
+def dgm_kick2d(prob, which, dt):
+    _check(_lib.dgm_kick2d(prob, int(which), float(dt)))
+
+
+def dgm_run2d(prob, dt, nsteps, stream=None, energies=False):
+    W = np.empty(int(nsteps) + 1) if energies else None
+    _check(_lib.dgm_run2d(prob, float(dt), int(nsteps), stream, _dptr(W)))
+    return W
 
 
 def dgm_quad_rule(q1d):

@@ -92,3 +92,39 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Solver2D:
+    """2D triangle mesh + p + eps + mu -> device-resident TE problem (include/dgm.h:
+    E in the plane of degree p, H along z of degree p - 1)."""
+
+    def __init__(self, xy, tris, p, eps, mu, vertex_key=None, precision="fp64", device=0):
+        self.ctx = capi.dgm_create(device)
+        prec = {"fp64": capi.DGM_PREC_FP64, "fp32": capi.DGM_PREC_FP32}.get(precision, -1)
+        self.prob = capi.dgm_problem2d_create(self.ctx, xy, tris, p, eps, mu, vertex_key, prec)
+        self.p = p
+        self.nE, self.nH = capi.dgm_problem2d_sizes(self.prob)
+
+    def set_fields(self, E, H):
+        capi.dgm_set_fields2d(self.prob, E, H)
+
+    def get_fields(self):
+        E = np.empty(self.nE)
+        H = np.empty(self.nH)
+        capi.dgm_get_fields2d(self.prob, E, H)
+        return E, H
+
+    def kick(self, which, dt):
+        capi.dgm_kick2d(self.prob, which, dt)
+
+    def run(self, dt, nsteps, energies=False):
+        return capi.dgm_run2d(self.prob, dt, nsteps, None, energies)
+
+    def close(self):
+        if getattr(self, "prob", None):
+            capi.dgm_problem2d_destroy(self.prob)
+            self.prob = None
+        if getattr(self, "ctx", None):
+            capi.dgm_destroy(self.ctx)
+            self.ctx = None
+
