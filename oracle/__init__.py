@@ -20,8 +20,9 @@ What it computes is the plain definition of the method:
   * symplectic Euler / leapfrog of Sec. 3 and the discrete energy of Sec. 2.1;
   * the same scheme for 2D TE fields on triangles (``dg2d``: E in the plane,
     H along z, the Eq. (4) basis), the oracle of a 2D triangle solver;
-  * material parameters varying inside flat elements (``varcoef``): the exact
-    mass and the approximate inverse mass of Sec. 3.3.2.
+  * material parameters varying inside flat elements (``varcoef``) and curved
+    elements from a smooth global map (``curved``): the exact mass and the
+    approximate inverse mass of Sec. 3.3.2.
 
 Readings of the paper taken here (the same as the CUDA path's):
   * p is the degree of E; H has degree p-1 (Sec. 2, spaces V^{k+1}, V^k).
