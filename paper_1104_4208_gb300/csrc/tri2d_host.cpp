@@ -243,14 +243,15 @@ int dgm_problem2d_create(dgm_ctx* ctx, int64_t nv, const double* xy, int64_t nt,
     const int64_t nE = nt * 2 * P->NE, nH = nt * P->NH;
     if ((e = cudaMalloc(&P->dE, nE * rs)) != cudaSuccess) return fail(fail2(e, "alloc E"));
     if ((e = cudaMalloc(&P->dH, nH * rs)) != cudaSuccess) return fail(fail2(e, "alloc H"));
-    cudaMemset(P->dE, 0, nE * rs);
-    cudaMemset(P->dH, 0, nH * rs);
+    if ((e = cudaMemset(P->dE, 0, nE * rs)) != cudaSuccess || (e = cudaMemset(P->dH, 0, nH * rs)) != cudaSuccess)
+        return fail(fail2(e, "clear fields"));
     if ((e = cudaMalloc(&P->dGeo, M.geo.size() * sizeof(double))) != cudaSuccess) return fail(fail2(e, "alloc geo"));
     if ((e = cudaMalloc(&P->dNbr, M.nbr.size() * sizeof(int32_t))) != cudaSuccess) return fail(fail2(e, "alloc nbr"));
     if ((e = cudaMalloc(&P->dSig, M.sig.size())) != cudaSuccess) return fail(fail2(e, "alloc sig"));
-    cudaMemcpy(P->dGeo, M.geo.data(), M.geo.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(P->dNbr, M.nbr.data(), M.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(P->dSig, M.sig.data(), M.sig.size(), cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(P->dGeo, M.geo.data(), M.geo.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(P->dNbr, M.nbr.data(), M.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(P->dSig, M.sig.data(), M.sig.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(fail2(e, "upload geometry"));
     {
         std::vector<int> iE, iH;
         dgm::index2(p, iE);
@@ -260,8 +261,9 @@ int dgm_problem2d_create(dgm_ctx* ctx, int64_t nv, const double* xy, int64_t nt,
         for (int b = 0; b < P->NH; ++b) nrmH[b] = std::sqrt(dgm::dubiner2_norm2(iH[2 * b], iH[2 * b + 1]));
         if ((e = cudaMalloc(&P->dNrmE, P->NE * sizeof(double))) != cudaSuccess) return fail(fail2(e, "alloc nrm"));
         if ((e = cudaMalloc(&P->dNrmH, P->NH * sizeof(double))) != cudaSuccess) return fail(fail2(e, "alloc nrm"));
-        cudaMemcpy(P->dNrmE, nrmE.data(), P->NE * sizeof(double), cudaMemcpyHostToDevice);
-        cudaMemcpy(P->dNrmH, nrmH.data(), P->NH * sizeof(double), cudaMemcpyHostToDevice);
+        if ((e = cudaMemcpy(P->dNrmE, nrmE.data(), P->NE * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(P->dNrmH, nrmH.data(), P->NH * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(fail2(e, "upload norms"));
     }
     if ((e = cudaMalloc(&P->dStage, std::max(nE, nH) * sizeof(double))) != cudaSuccess)
         return fail(fail2(e, "alloc stage"));
