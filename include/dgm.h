@@ -498,6 +498,12 @@ int dgm_reference_table_2d(int p, int which, double* out, int64_t count, int64_t
  * edges shared by more than two triangles, a triangle glued to itself,
  * non-positive eps or mu, p outside [1, DGM_PMAX]. */
 typedef struct dgm_problem2d dgm_problem2d;
+/* Edge counts of a 2D triangle mesh with the adjacency dgm_problem2d_create
+ * builds (keys, periodic gluing, PEC boundary): *nedges distinct edges, of which
+ * *nboundary have no partner.  Host only, no GPU; the same argument checks and
+ * errors as dgm_problem2d_create (eps = mu = 1). */
+int dgm_mesh2d_info(int64_t nv, const double* xy, int64_t nt, const int32_t* tris, const int32_t* vertex_key,
+                    int64_t* nedges, int64_t* nboundary);
 int dgm_problem2d_create(dgm_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tris,
                          const int32_t* vertex_key, int p, const double* eps, const double* mu, int precision,
                          dgm_problem2d** out);

@@ -92,6 +92,7 @@ _SIGS = {
     "dgm_reference_table_2d": ([C.c_int, C.c_int, _pd, _i64, _pi64], C.c_int),
     "dgm_problem2d_create": ([_vp, _i64, _pd, _i64, _pi32, _pi32, C.c_int, _pd, _pd, C.c_int, C.POINTER(_vp)],
                              C.c_int),
+    "dgm_mesh2d_info": ([_i64, _pd, _i64, _pi32, _pi32, _pi64, _pi64], C.c_int),
     "dgm_problem2d_destroy": ([_vp], C.c_int),
     "dgm_problem2d_sizes": ([_vp, _pi64, _pi64], C.c_int),
     "dgm_set_fields2d": ([_vp, _pd, _pd], C.c_int),
@@ -351,6 +352,16 @@ def dgm_problem2d_create(ctx, xy, tris, p, eps, mu, vertex_key=None, precision=N
                                      _dptr(mu), DGM_PREC_FP64 if precision is None else int(precision),
                                      C.byref(h)))
     return h
+
+
+def dgm_mesh2d_info(xy, tris, vertex_key=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    key = None if vertex_key is None else np.ascontiguousarray(vertex_key, dtype=np.int32)
+    a, b = _i64(), _i64()
+    _check(_lib.dgm_mesh2d_info(xy.shape[0], _dptr(xy), tris.shape[0], tris.ctypes.data_as(_pi32),
+                                None if key is None else key.ctypes.data_as(_pi32), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def dgm_problem2d_destroy(prob):

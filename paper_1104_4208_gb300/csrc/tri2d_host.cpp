@@ -201,6 +201,23 @@ int phase_E2d(dgm_problem2d* P, double dt, cudaStream_t s) {
 
 }  // namespace
 
+int dgm_mesh2d_info(int64_t nv, const double* xy, int64_t nt, const int32_t* tris, const int32_t* vertex_key,
+                    int64_t* nedges, int64_t* nboundary) {
+    if (!xy || !tris || nv < 3 || nt < 1) {
+        set_error("dgm_mesh2d_info: bad argument");
+        return DGM_ERR_INVALID_ARG;
+    }
+    std::vector<double> one((size_t)nt, 1.0);
+    Mesh2 M;
+    const int rc = build_mesh2(nv, xy, nt, tris, vertex_key, one.data(), one.data(), M);
+    if (rc) return rc;
+    int64_t interior_sides = 0, boundary = 0;
+    for (int32_t nb : M.nbr) (nb >= 0 ? interior_sides : boundary) += 1;
+    if (nedges) *nedges = interior_sides / 2 + boundary;
+    if (nboundary) *nboundary = boundary;
+    return DGM_OK;
+}
+
 int dgm_problem2d_create(dgm_ctx* ctx, int64_t nv, const double* xy, int64_t nt, const int32_t* tris,
                          const int32_t* vertex_key, int p, const double* eps, const double* mu, int precision,
                          dgm_problem2d** out) {

@@ -105,3 +105,30 @@ def test_2d_table_arguments(capi):
         capi.dgm_reference_table_2d(0, 0)
     with pytest.raises(capi.DgmError):
         capi.dgm_reference_table_2d(3, 9)
+
+
+def test_2d_mesh_adjacency(capi):
+    """The adjacency the 2D solver builds: an n x n square split into 2 n^2
+    triangles has 3 n^2 + 2 n edges, 4 n on the boundary; with periodic keys
+    3 n^2 edges and none on the boundary; refusals as for the solver."""
+    from workloads.mesh2d import square_tri_mesh
+    for n in (1, 3, 5):
+        m = square_tri_mesh(n, jitter=0.1 if n > 1 else 0.0, seed=2, shuffle_local=True)
+        assert capi.dgm_mesh2d_info(m.xy, m.tris) == (3 * n * n + 2 * n, 4 * n)
+        if n > 1:
+            mp = square_tri_mesh(n, periodic=True, shuffle_local=True, seed=3)
+            assert capi.dgm_mesh2d_info(mp.xy, mp.tris, mp.vertex_key) == (3 * n * n, 0)
+    m = square_tri_mesh(2)
+    bad = m.xy.copy()
+    bad[m.tris[0, 1]] = bad[m.tris[0, 0]]
+    with pytest.raises(capi.DgmError) as e:
+        capi.dgm_mesh2d_info(bad, m.tris)
+    assert e.value.code == capi.DGM_ERR_INVALID_ARG
+    tris = m.tris.copy()
+    tris[0, 2] = m.nv
+    with pytest.raises(capi.DgmError):
+        capi.dgm_mesh2d_info(m.xy, tris)
+    dup = np.concatenate([m.tris, m.tris[:1]])        # one edge shared by three triangles
+    with pytest.raises(capi.DgmError):
+        capi.dgm_mesh2d_info(m.xy, dup)
+
