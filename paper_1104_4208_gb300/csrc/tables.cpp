@@ -187,40 +187,132 @@ void psi2_at(int p, const std::vector<int>& idx, double a, double b, double* val
 
 const double kVert[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 
-void face_trace(int p, int f, std::vector<double>& T) {
-    // T[g][a] = int psi'_g(s,u) phi'_a(xh_f(s,u)) ds du, face modes of degree <= p
+// Face traces T[g][a] = int psi'_g(s,u) phi'_a(face point) ds du of the
+// orthonormal bases, built sum-factorised (Sec. 3.2.3, Sec. 4.2.2).
+// On each reference face the restriction of phi_ijk factors in the face's
+// collapsed coordinates (s, b = u / (1 - s)):
+//   face 1 (x = 0):  (-1)^k psi_ij                                   (diagonal)
+//   face 2 (y = 0):  (-1)^j P_i(2b-1) (1-s)^i [(1-s)^j P_k^(2i+2j+2,0)(2s-1)]
+//   face 3 (z = 0):  (-1)^i [(1-b)^i P_j^(2i+1,0)(2b-1)] (1-s)^(i+j) P_k^(2i+2j+2,0)(2s-1)
+//   face 0 (x+y+z = 1): the face-3 form without the sign, in the face's rotated
+//     parametrisation (s~, u~) = (1 - s - u, s); a dense rotation block, the same
+//     for every element and block diagonal in the face degree, maps it back.
+// The brackets are expanded by 1D connection coefficients: in b against the
+// Legendre P_m(2b-1) (weight 1), in s against P_n^(2m+1,0)(2s-1) (weight
+// (1-s)^(2m+1)), each an exact Gauss-Legendre sum of a polynomial.
+
+// int_0^1 w(s) p(s) q(s) ds for polynomials, by nq-point Gauss-Legendre
+struct Line {
+    std::vector<double> x, w;
+    explicit Line(int nq) { gauss_legendre01(nq, x, w); }
+};
+
+// c_n = <g, P_n^(a,0)(2s-1)>_(1-s)^a / <P_n, P_n>_(1-s)^a, n = 0..nmax, for g given
+// at the line's nodes
+void jacobi_coeffs(const Line& L, double a, const std::vector<double>& g, int nmax, double* c) {
+    std::vector<double> P(nmax + 1);
+    std::vector<double> num(nmax + 1, 0.0), den(nmax + 1, 0.0);
+    for (size_t q = 0; q < L.x.size(); ++q) {
+        jacobi_all(nmax, a, 0.0, 2.0 * L.x[q] - 1.0, P.data());
+        const double wq = L.w[q] * std::pow(1.0 - L.x[q], a);
+        for (int n = 0; n <= nmax; ++n) {
+            num[n] += wq * g[q] * P[n];
+            den[n] += wq * P[n] * P[n];
+        }
+    }
+    for (int n = 0; n <= nmax; ++n) c[n] = num[n] / den[n];
+}
+
+// unnormalised face-3 form (without sign) of phi_ijk: coefficients q[(m,n)] on psi_mn
+void face3_form(int p, int i, int j, int k, const Line& L, const std::vector<int>& pos2, std::vector<double>& q) {
+    const int N2 = (p + 1) * (p + 2) / 2;
+    q.assign(N2, 0.0);
+    const int nq = (int)L.x.size();
+    std::vector<double> g(nq), P(p + 1), d(i + j + 1), e(p + 1);
+    // (1-b)^i P_j^(2i+1,0)(2b-1) in Legendre P_m(2b-1)
+    for (int r = 0; r < nq; ++r) {
+        jacobi_all(j, 2.0 * i + 1.0, 0.0, 2.0 * L.x[r] - 1.0, P.data());
+        g[r] = ipow(1.0 - L.x[r], i) * P[j];
+    }
+    jacobi_coeffs(L, 0.0, g, i + j, d.data());
+    for (int m = 0; m <= i + j; ++m) {
+        if (d[m] == 0.0) continue;
+        // (1-s)^(i+j-m) P_k^(2i+2j+2,0)(2s-1) in P_n^(2m+1,0)(2s-1)
+        for (int r = 0; r < nq; ++r) {
+            jacobi_all(k, 2.0 * i + 2.0 * j + 2.0, 0.0, 2.0 * L.x[r] - 1.0, P.data());
+            g[r] = ipow(1.0 - L.x[r], i + j - m) * P[k];
+        }
+        const int nmax = i + j - m + k;
+        jacobi_coeffs(L, 2.0 * m + 1.0, g, nmax, e.data());
+        for (int n = 0; n <= nmax; ++n) q[pos2[m * (p + 1) + n]] += d[m] * e[n];
+    }
+}
+
+void face_trace_sf(int p, int f, std::vector<double>& T) {
     std::vector<int> i3, i2;
     index3(p, i3);
     index2(p, i2);
-    const int NE = (int)i3.size() / 3, N2 = (int)i2.size() / 2;
-    int v[3], c = 0;
-    for (int q = 0; q < 4; ++q)
-        if (q != f) v[c++] = q;
-    std::vector<double> xa, wa, xb, wb;
-    const int nq = p + 2;
-    gauss_legendre01(nq, xa, wa);
-    gauss_legendre01(nq, xb, wb);
-    std::vector<double> phi(NE), psi(N2);
-    T.assign((size_t)N2 * NE, 0.0);
-    for (int qa = 0; qa < nq; ++qa)
-        for (int qb = 0; qb < nq; ++qb) {
-            const double s = xa[qa], u = (1.0 - xa[qa]) * xb[qb];
-            const double w = wa[qa] * wb[qb] * (1.0 - xa[qa]);
-            double xh[3];
-            for (int d = 0; d < 3; ++d)
-                xh[d] = kVert[v[0]][d] + s * (kVert[v[1]][d] - kVert[v[0]][d])
-                        + u * (kVert[v[2]][d] - kVert[v[0]][d]);
-            phi3_cart(p, i3, xh, phi.data());
-            psi2_at(p, i2, xa[qa], xb[qb], psi.data());
-            for (int g = 0; g < N2; ++g)
-                for (int a = 0; a < NE; ++a) T[(size_t)g * NE + a] += w * psi[g] * phi[a];
+    const int N3 = (int)i3.size() / 3, N2 = (int)i2.size() / 2;
+    std::vector<int> pos2((p + 1) * (p + 1), -1);
+    for (int g = 0; g < N2; ++g) pos2[i2[2 * g] * (p + 1) + i2[2 * g + 1]] = g;
+    std::vector<double> n2(N2);
+    for (int g = 0; g < N2; ++g) n2[g] = dubiner2_norm2(i2[2 * g], i2[2 * g + 1]);
+    const Line L(2 * p + 4);
+    // face 0: R[g][h] = int psi_g(s,u) psi_h(1-s-u, s) ds du / ||psi_g||^2
+    std::vector<double> R;
+    if (f == 0) {
+        R.assign((size_t)N2 * N2, 0.0);
+        const int nq = p + 2;
+        std::vector<double> xa, wa;
+        gauss_legendre01(nq, xa, wa);
+        std::vector<double> pg(N2), ph(N2);
+        for (int qa = 0; qa < nq; ++qa)
+            for (int qb = 0; qb < nq; ++qb) {
+                const double s = xa[qa], u = (1.0 - xa[qa]) * xa[qb];
+                const double w = wa[qa] * wa[qb] * (1.0 - xa[qa]);
+                psi2_at(p, i2, xa[qa], xa[qb], pg.data());
+                const double st = 1.0 - s - u;
+                psi2_at(p, i2, st, s / (1.0 - st), ph.data());
+                for (int g = 0; g < N2; ++g)
+                    for (int h = 0; h < N2; ++h) R[(size_t)g * N2 + h] += w * pg[g] * ph[h];
+            }
+        for (int g = 0; g < N2; ++g)
+            for (int h = 0; h < N2; ++h) R[(size_t)g * N2 + h] /= n2[g];
+    }
+    T.assign((size_t)N2 * N3, 0.0);
+    std::vector<double> q, e(p + 1);
+    for (int a = 0; a < N3; ++a) {
+        const int i = i3[3 * a], j = i3[3 * a + 1], k = i3[3 * a + 2];
+        // c[g]: coefficient of psi_g in the restriction of phi_ijk
+        std::vector<double> c(N2, 0.0);
+        if (f == 1) {
+            c[pos2[i * (p + 1) + j]] = (k % 2) ? -1.0 : 1.0;
+        } else if (f == 2) {
+            const int nq = (int)L.x.size();
+            std::vector<double> g(nq), P(p + 1);
+            for (int r = 0; r < nq; ++r) {
+                jacobi_all(k, 2.0 * i + 2.0 * j + 2.0, 0.0, 2.0 * L.x[r] - 1.0, P.data());
+                g[r] = ipow(1.0 - L.x[r], j) * P[k];
+            }
+            jacobi_coeffs(L, 2.0 * i + 1.0, g, j + k, e.data());
+            const double sg = (j % 2) ? -1.0 : 1.0;
+            for (int n = 0; n <= j + k; ++n) c[pos2[i * (p + 1) + n]] = sg * e[n];
+        } else {
+            face3_form(p, i, j, k, L, pos2, q);
+            if (f == 3) {
+                const double sg = (i % 2) ? -1.0 : 1.0;
+                for (int g = 0; g < N2; ++g) c[g] = sg * q[g];
+            } else {
+                for (int g = 0; g < N2; ++g) {
+                    double acc = 0.0;
+                    for (int h = 0; h < N2; ++h) acc += R[(size_t)g * N2 + h] * q[h];
+                    c[g] = acc;
+                }
+            }
         }
-    for (int g = 0; g < N2; ++g) {
-        const double ng = std::sqrt(dubiner2_norm2(i2[2 * g], i2[2 * g + 1]));
-        for (int a = 0; a < NE; ++a) {
-            const double na = std::sqrt(dubiner3_norm2(i3[3 * a], i3[3 * a + 1], i3[3 * a + 2]));
-            T[(size_t)g * NE + a] /= (ng * na);
-        }
+        const double na = std::sqrt(dubiner3_norm2(i, j, k));
+        // orthonormal table: (int psi_g phi_a) / (||psi_g|| ||phi_a||) = c_g ||psi_g|| / ||phi_a||
+        for (int g = 0; g < N2; ++g) T[(size_t)g * N3 + a] = c[g] * std::sqrt(n2[g]) / na;
     }
 }
 
@@ -346,8 +438,8 @@ int build_ref_tables(int p, RefTables& t, bool equal_order) {
                 if (std::fabs(x) < 1e-12 * mx) x = 0.0;
     }
     for (int f = 0; f < 4; ++f) {
-        face_trace(p, f, t.TrE[f]);
-        face_trace(ph, f, t.TrH[f]);
+        face_trace_sf(p, f, t.TrE[f]);
+        face_trace_sf(ph, f, t.TrH[f]);
     }
     // face frames and reference orientation signs
     const double nhat[4][3] = {{1, 1, 1}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}};
